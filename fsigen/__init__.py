@@ -1,0 +1,285 @@
+"""Seeded input generator for the monolithic FSI linear solve.
+
+Builds the linearised ALE fluid-structure Jacobian A_h (Eq. mat:small, Sec. 3.4)
+of the semilinear form Eq. (fsi:all) at a seeded smooth state, plus a seeded
+right-hand side, on structured box meshes that stand in for the paper's 2D
+channel (Sec. 6.1) and 3D obstacle (Sec. 6.2) cases.  The C++ part
+(``assemble.cpp``) does the finite-element work; this module compiles it, draws
+the seeded state and right-hand side, and hands out plain numpy arrays.
+
+Both the CPU oracle and the CUDA library take what this module returns as input.
+It holds none of the solver's arithmetic (no Krylov, AMG or preconditioner step).
+
+Input recipe (seeded, synthetic):
+  * state: for each scalar field in the order v_0..v_{d-1}, u_0..u_{d-1}, p, with
+    ``rng = numpy.random.default_rng(state_seed)`` shared across fields, draw
+    ``modes = rng.integers(1, 5, size=(4, d))`` and ``a = rng.uniform(-1, 1, 4)``;
+    the field is ``A * sum_k a_k prod_j sin(pi m_kj x_j / L_j) / sum_k |a_k|``
+    evaluated at the DOF's node (zero on the whole outer boundary, |f| <= A);
+  * previous time step: U^{n-1} = U ("rest", the default: the mesh velocity
+    (u - u^{n-1})/dt vanishes) or U^{n-1} = 0 ("zero");
+  * right-hand side: ``numpy.random.default_rng(rhs_seed).standard_normal(n)``,
+    zeroed on fixed (identity) rows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "assemble.cpp")
+_SO = os.path.join(_HERE, "libfsigen.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``assemble.cpp`` into ``libfsigen.so`` (g++, OpenMP, no FMA contraction
+    so x86 and Arm hosts produce the same bits)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O3", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3),
+                ("solid_h", ctypes.c_double), ("rho_f", ctypes.c_double), ("nu_f", ctypes.c_double),
+                ("mu_s", ctypes.c_double), ("lambda_s", ctypes.c_double), ("rho_s", ctypes.c_double),
+                ("dt", ctypes.c_double), ("theta", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            vp, i64p, i32p, f64p, u8p = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_uint8))
+            lib.fsigen_create.restype = vp
+            lib.fsigen_create.argtypes = [ctypes.POINTER(_Params)]
+            lib.fsigen_free.argtypes = [vp]
+            lib.fsigen_sizes.argtypes = [vp, i64p]
+            lib.fsigen_pattern.argtypes = [vp, i64p, i32p]
+            lib.fsigen_dof_info.argtypes = [vp, f64p, i32p, i32p, u8p]
+            lib.fsigen_jacobian.argtypes = [vp, f64p, f64p, f64p, f64p]
+            lib.fsigen_jacobian.restype = ctypes.c_int
+            lib.fsigen_residual.argtypes = [vp, f64p, f64p, f64p, f64p]
+            lib.fsigen_residual.restype = ctypes.c_int
+            lib.fsigen_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None else None
+
+
+@dataclass(frozen=True)
+class FSIConfig:
+    """Mesh, material and seed parameters of one synthetic Jacobian.
+
+    Material values are the FSI-2 set of Sec. 6.1 (fluid density 1e3, viscosity
+    1e-3, solid density 1e4, Lame mu 0.5e6, lambda 2e6); backward Euler, dt = 0.01.
+    """
+    name: str
+    dim: int
+    n: tuple
+    L: tuple = (2.0, 1.0, 1.0)
+    solid_h: float = 0.25
+    amplitude: float = 1e-2
+    state_seed: int = 0
+    rhs_seed: int = 0
+    rho_f: float = 1e3
+    nu_f: float = 1e-3
+    mu_s: float = 5e5
+    lambda_s: float = 2e6
+    rho_s: float = 1e4
+    dt: float = 0.01
+    theta: float = 1.0
+    prev_state: str = "rest"      # U^{n-1} = U ("rest") or 0 ("zero")
+
+    def with_(self, **kw) -> "FSIConfig":
+        return replace(self, **kw)
+
+
+CONFIGS = {
+    # 16x16 cells on [0,2]x[0,1], solid strip y < 0.25: n = 4,645
+    "2d_tiny": FSIConfig("2d_tiny", 2, (16, 16)),
+    # 256x128 cells: n = 560,517
+    "2d_mid": FSIConfig("2d_mid", 2, (256, 128)),
+    # 32x16x16 hex cells on [0,2]x[0,1]^2, solid slab z < 0.25: n = 434,247
+    "3d": FSIConfig("3d", 3, (32, 16, 16)),
+    # 1024x512 cells, amplitude 5e-2: n = 8,926,725
+    "2d_large": FSIConfig("2d_large", 2, (1024, 512), amplitude=5e-2),
+}
+
+
+class Problem:
+    """Mesh, DOF classes and sparsity pattern of one configuration."""
+
+    def __init__(self, cfg: FSIConfig):
+        lib = _load()
+        self.cfg = cfg
+        p = _Params()
+        p.dim = cfg.dim
+        for d in range(3):
+            p.n[d] = cfg.n[d] if d < cfg.dim else 1
+            p.L[d] = cfg.L[d]
+        p.solid_h, p.rho_f, p.nu_f = cfg.solid_h, cfg.rho_f, cfg.nu_f
+        p.mu_s, p.lambda_s, p.rho_s, p.dt, p.theta = cfg.mu_s, cfg.lambda_s, cfg.rho_s, cfg.dt, cfg.theta
+        self._h = lib.fsigen_create(ctypes.byref(p))
+        if not self._h:
+            raise ValueError(f"fsigen: invalid configuration {cfg}")
+        sizes = np.zeros(9, np.int64)
+        lib.fsigen_sizes(self._h, _ptr(sizes, ctypes.c_int64))
+        self.offsets = sizes[:6].copy()
+        self.n = int(sizes[5])
+        self.nnz = int(sizes[6])
+        self.n_q2, self.n_q1 = int(sizes[7]), int(sizes[8])
+        self.dim = cfg.dim
+        self.rowptr = np.empty(self.n + 1, np.int64)
+        self.colind = np.empty(self.nnz, np.int32)
+        lib.fsigen_pattern(self._h, _ptr(self.rowptr, ctypes.c_int64), _ptr(self.colind, ctypes.c_int32))
+        self.coords = np.empty((self.n, self.dim), np.float64)
+        self.field = np.empty(self.n, np.int32)
+        self.comp = np.empty(self.n, np.int32)
+        self.fixed = np.empty(self.n, np.uint8)
+        lib.fsigen_dof_info(self._h, _ptr(self.coords, ctypes.c_double), _ptr(self.field, ctypes.c_int32),
+                            _ptr(self.comp, ctypes.c_int32), _ptr(self.fixed, ctypes.c_uint8))
+        self.fixed = self.fixed.astype(bool)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _load().fsigen_free(self._h)
+            self._h = None
+
+    # ------------------------------------------------------------ seeded data
+    def seeded_state(self, seed: int | None = None, amplitude: float | None = None) -> np.ndarray:
+        """Smooth state U: per scalar field a normalised sum of 4 random sine modes."""
+        cfg = self.cfg
+        seed = cfg.state_seed if seed is None else seed
+        A = cfg.amplitude if amplitude is None else amplitude
+        d = self.dim
+        rng = np.random.default_rng(seed)
+        U = np.zeros(self.n)
+        L = np.asarray(cfg.L[:d])
+        for fld, ncomp in ((0, d), (1, d), (2, 1)):
+            for c in range(ncomp):
+                modes = rng.integers(1, 5, size=(4, d))
+                a = rng.uniform(-1.0, 1.0, size=4)
+                sel = (self.field == fld) & (self.comp == c)
+                x = self.coords[sel]
+                val = np.zeros(x.shape[0])
+                for k in range(4):
+                    term = np.full(x.shape[0], a[k])
+                    for j in range(d):
+                        term = term * np.sin(np.pi * modes[k, j] * x[:, j] / L[j])
+                    val += term
+                U[sel] = A * val / np.sum(np.abs(a))
+        U[self.fixed] = 0.0
+        return U
+
+    def rhs(self, seed: int | None = None) -> np.ndarray:
+        seed = self.cfg.rhs_seed if seed is None else seed
+        b = np.random.default_rng(seed).standard_normal(self.n)
+        b[self.fixed] = 0.0
+        return b
+
+    # --------------------------------------------------------------- assembly
+    def jacobian(self, U: np.ndarray, Uold: np.ndarray | None = None) -> np.ndarray:
+        """Values of dR/dU on the pattern (rowptr, colind)."""
+        U = np.ascontiguousarray(U, np.float64)
+        vals = np.empty(self.nnz, np.float64)
+        minJ = ctypes.c_double(0.0)
+        uo = None if Uold is None else np.ascontiguousarray(Uold, np.float64)
+        rc = _load().fsigen_jacobian(self._h, _ptr(U, ctypes.c_double), _ptr(uo, ctypes.c_double),
+                                     _ptr(vals, ctypes.c_double), ctypes.byref(minJ))
+        self.min_J = minJ.value
+        if rc == 1:
+            raise RuntimeError("fsigen: Jacobian entry outside the sparsity pattern")
+        if rc == 2:
+            raise RuntimeError(f"fsigen: state folds the mesh (min J = {minJ.value})")
+        return vals
+
+    def residual(self, U: np.ndarray, Uold: np.ndarray | None = None) -> np.ndarray:
+        U = np.ascontiguousarray(U, np.float64)
+        R = np.empty(self.n, np.float64)
+        minJ = ctypes.c_double(0.0)
+        uo = None if Uold is None else np.ascontiguousarray(Uold, np.float64)
+        rc = _load().fsigen_residual(self._h, _ptr(U, ctypes.c_double), _ptr(uo, ctypes.c_double),
+                                     _ptr(R, ctypes.c_double), ctypes.byref(minJ))
+        if rc == 2:
+            raise RuntimeError(f"fsigen: state folds the mesh (min J = {minJ.value})")
+        return R
+
+    def solid_node_coords(self) -> np.ndarray:
+        """Coordinates of the s_v nodes (one row per node, s_v node order)."""
+        lo, hi = self.offsets[1], self.offsets[2]
+        return np.ascontiguousarray(self.coords[lo:hi:self.dim])
+
+
+@dataclass
+class System:
+    """One linear system A x = b in monolithic CSR with its class offsets."""
+    cfg: FSIConfig
+    dim: int
+    rowptr: np.ndarray
+    colind: np.ndarray
+    vals: np.ndarray
+    offsets: np.ndarray
+    rhs: np.ndarray
+    solid_coords: np.ndarray
+    fixed: np.ndarray
+    state: np.ndarray = field(repr=False, default=None)
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets[5])
+
+    def scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.vals, self.colind, self.rowptr), shape=(self.n, self.n))
+
+
+_problem_cache: dict = {}
+
+
+def get_problem(cfg: FSIConfig) -> Problem:
+    key = (cfg.dim, tuple(cfg.n), tuple(cfg.L), cfg.solid_h, cfg.rho_f, cfg.nu_f, cfg.mu_s,
+           cfg.lambda_s, cfg.rho_s, cfg.dt, cfg.theta)
+    if key not in _problem_cache:
+        _problem_cache[key] = Problem(cfg)
+    return _problem_cache[key]
+
+
+def make_system(cfg: FSIConfig | str, state_seed: int | None = None, rhs_seed: int | None = None) -> System:
+    """Assemble the seeded Jacobian and right-hand side of a configuration."""
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    if state_seed is not None:
+        cfg = cfg.with_(state_seed=state_seed)
+    if rhs_seed is not None:
+        cfg = cfg.with_(rhs_seed=rhs_seed)
+    pb = get_problem(cfg)
+    U = pb.seeded_state(cfg.state_seed, cfg.amplitude)
+    if cfg.prev_state == "rest":
+        Uold = U.copy()
+    elif cfg.prev_state == "zero":
+        Uold = None
+    else:
+        raise ValueError(f"unknown prev_state {cfg.prev_state!r}")
+    vals = pb.jacobian(U, Uold)
+    return System(cfg=cfg, dim=pb.dim, rowptr=pb.rowptr, colind=pb.colind, vals=vals,
+                  offsets=pb.offsets.copy(), rhs=pb.rhs(cfg.rhs_seed), solid_coords=pb.solid_node_coords(),
+                  fixed=pb.fixed, state=U)

@@ -1,0 +1,214 @@
+"""Pins of the seeded problem generator (input of the solve, Eq. mat:small).
+
+The Jacobian is checked against its own residual by central differences, and
+the residual/Jacobian against closed forms that the physics of Sec. 2-3 fixes:
+Q2 mass integrals, Laplace stiffness annihilating linear fields, linear
+elasticity annihilating rigid motions, frame invariance of the St. Venant-
+Kirchhoff stress under a finite rotation, the discrete pressure gradient being
+minus the transposed divergence, and the solid kinematic rows A_uv = -dt A_uu.
+"""
+from fractions import Fraction
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fsigen
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small(dim, n, **kw):
+    base = fsigen.CONFIGS["2d_tiny"] if dim == 2 else fsigen.CONFIGS["3d"]
+    return base.with_(name=f"t{dim}", n=n, **kw)
+
+
+def A_of(pb, vals):
+    return sp.csr_matrix((vals, pb.colind, pb.rowptr), shape=(pb.n, pb.n))
+
+
+@pytest.mark.parametrize("name,expect", [
+    ("2d_tiny", [0, 1584, 2178, 2772, 4356, 4645]),
+    ("2d_mid", [0, 196992, 263682, 330372, 527364, 560517]),
+    ("3d", [0, 154440, 212355, 270270, 424710, 434247]),
+])
+def test_dof_counts(name, expect):
+    pb = fsigen.get_problem(fsigen.CONFIGS[name])
+    assert pb.offsets.tolist() == expect
+
+
+@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(2, (6, 4), prev_state="zero"), small(3, (4, 2, 4))])
+def test_jacobian_matches_central_differences(cfg):
+    pb = fsigen.get_problem(cfg)
+    U = pb.seeded_state(3, 3e-2)
+    Uold = U.copy() if cfg.prev_state == "rest" else None
+    if Uold is not None:
+        Uold = Uold * 0.5   # a previous step that differs from U exercises every term
+    A = A_of(pb, pb.jacobian(U, Uold))
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        d = rng.standard_normal(pb.n)
+        d[pb.fixed] = 0.0
+        eps = 1e-6
+        fd = (pb.residual(U + eps * d, Uold) - pb.residual(U - eps * d, Uold)) / (2 * eps)
+        ad = A @ d
+        ad[pb.fixed] = 0.0
+        assert np.linalg.norm(fd - ad) <= 1e-6 * np.linalg.norm(ad)
+
+
+def test_q2_mass_integrals_solid_block():
+    cfg = small(2, (8, 16))
+    pb = fsigen.get_problem(cfg)
+    A = A_of(pb, pb.jacobian(pb.seeded_state(), None))
+    o = pb.offsets
+    Auu = A[o[2]:o[3], o[2]:o[3]].tocsr()
+    hx, hy = 2.0 / 8, 1.0 / 16
+    gold = {}
+    for line in open(os.path.join(GOLD, "q2_basis_integrals.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()
+        gold[k] = float(Fraction(v))
+    coords = pb.coords[o[2]:o[3]]
+    comp = pb.comp[o[2]:o[3]]
+    fixed = pb.fixed[o[2]:o[3]]
+    ones = np.ones(Auu.shape[0])
+    m1 = Auu @ ones
+    checked = 0
+    for i in range(Auu.shape[0]):
+        x, y = coords[i]
+        ix, iy = round(x / (hx / 2)), round(y / (hy / 2))
+        # strictly inside the solid strip (y < 0.25) and away from fixed neighbours
+        if fixed[i] or iy < 3 or iy > 5 or ix < 3 or ix > 13:
+            continue
+        kind = "vertex" if (ix % 2 == 0 and iy % 2 == 0) else ("center" if (ix % 2 and iy % 2) else "edge")
+        assert m1[i] == pytest.approx(gold[kind] * hx * hy, rel=1e-12), (i, kind)
+        checked += 1
+    assert checked > 20
+
+
+def test_mesh_block_annihilates_linear_fields_at_zero_state():
+    cfg = small(2, (8, 8))
+    pb = fsigen.get_problem(cfg)
+    A = A_of(pb, pb.jacobian(np.zeros(pb.n), None))
+    o = pb.offsets
+    M = A[o[0]:o[1], o[0]:o[1]].tocsr()
+    X = pb.coords[o[0]:o[1]]
+    comp = pb.comp[o[0]:o[1]]
+    field = 0.3 * X[:, 0] - 0.7 * X[:, 1] + 0.2     # affine, same for each component
+    Mf = M @ field
+    # rows whose whole Q2 neighbourhood is free and outside the solid closure
+    hx, hy = 2.0 / 8, 1.0 / 8
+    ix = np.rint(X[:, 0] / (hx / 2)).astype(int)
+    iy = np.rint(X[:, 1] / (hy / 2)).astype(int)
+    inner = (ix >= 3) & (ix <= 13) & (iy >= 7) & (iy <= 13)
+    assert inner.sum() > 50
+    scale = np.abs(M).max()
+    assert np.max(np.abs(Mf[inner])) <= 1e-12 * scale
+
+
+def test_linear_elasticity_kernel_rigid_modes_at_zero_state():
+    cfg = small(2, (8, 16))
+    pb = fsigen.get_problem(cfg)
+    A = A_of(pb, pb.jacobian(np.zeros(pb.n), None))
+    o = pb.offsets
+    Avu = A[o[1]:o[2], o[2]:o[3]].tocsr()
+    X = pb.coords[o[2]:o[3]]
+    comp = pb.comp[o[2]:o[3]]
+    hx, hy = 2.0 / 8, 1.0 / 16
+    ix = np.rint(X[:, 0] / (hx / 2)).astype(int)
+    iy = np.rint(X[:, 1] / (hy / 2)).astype(int)
+    inner = (ix >= 3) & (ix <= 13) & (iy >= 3) & (iy <= 4)   # solid strip interior: y in (0, 0.25)
+    assert inner.sum() > 20
+    scale = np.abs(Avu).max()
+    for mode in ("tx", "ty", "rot"):
+        if mode == "tx":
+            f = (comp == 0).astype(float)
+        elif mode == "ty":
+            f = (comp == 1).astype(float)
+        else:
+            f = np.where(comp == 0, -X[:, 1], X[:, 0])
+        r = Avu @ f
+        assert np.max(np.abs(r[inner])) <= 1e-11 * scale, mode
+
+
+def test_stvk_frame_invariance_under_finite_rotation():
+    """A rigid finite rotation u = (R - I) x has E = 0, so the solid stress rows and
+    the mesh-motion rows (constant gradient, J = 1) see no force."""
+    cfg = small(2, (8, 16))
+    pb = fsigen.get_problem(cfg)
+    ang = 0.3
+    R = np.array([[np.cos(ang), -np.sin(ang)], [np.sin(ang), np.cos(ang)]])
+    U = np.zeros(pb.n)
+    u_rows = pb.field == 1
+    X = pb.coords[u_rows]
+    disp = X @ (R - np.eye(2)).T
+    U[u_rows] = disp[np.arange(X.shape[0]), pb.comp[u_rows]]
+    res = pb.residual(U, U.copy())
+    o = pb.offsets
+    hx, hy = 2.0 / 8, 1.0 / 16
+    X = pb.coords
+    ix = np.rint(X[:, 0] / (hx / 2)).astype(int)
+    iy = np.rint(X[:, 1] / (hy / 2)).astype(int)
+    sv = np.zeros(pb.n, bool)
+    sv[o[1]:o[2]] = True
+    inner_solid = sv & (ix >= 2) & (ix <= 14) & (iy >= 1) & (iy <= 6) & ~pb.fixed
+    assert inner_solid.sum() > 20
+    # the stress scale: dt * lambda * h ~ 2e6 * 0.01 * 0.06
+    assert np.max(np.abs(res[inner_solid])) <= 1e-9 * (0.01 * 2e6 * hx)
+    m = np.zeros(pb.n, bool)
+    m[o[0]:o[1]] = True
+    assert np.max(np.abs(res[m & ~pb.fixed])) <= 1e-12
+
+
+@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(3, (4, 2, 4))])
+def test_pressure_gradient_is_minus_divergence_transpose(cfg):
+    pb = fsigen.get_problem(cfg)
+    U = pb.seeded_state(1, 3e-2)
+    A = A_of(pb, pb.jacobian(U, U.copy()))
+    o = pb.offsets
+    Bvp = A[o[3]:o[4], o[4]:o[5]]
+    Bpv = A[o[4]:o[5], o[3]:o[4]]
+    D = (Bvp + Bpv.T)
+    assert abs(D).max() <= 1e-13 * abs(Bvp).max()
+    Bsp = A[o[1]:o[2], o[4]:o[5]]
+    Bps = A[o[4]:o[5], o[1]:o[2]]
+    assert abs(Bsp + Bps.T).max() <= 1e-13 * abs(Bsp).max()
+
+
+@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(3, (4, 2, 4))])
+def test_solid_kinematic_rows(cfg):
+    """A_uv = -dt*theta*A_uu on the free kinematic rows (Sec. 4.3 mass identity)."""
+    pb = fsigen.get_problem(cfg)
+    U = pb.seeded_state(2, 3e-2)
+    A = A_of(pb, pb.jacobian(U, U.copy()))
+    o = pb.offsets
+    Auv = A[o[2]:o[3], o[1]:o[2]]
+    Auu = A[o[2]:o[3], o[2]:o[3]]
+    free = ~pb.fixed[o[2]:o[3]]
+    D = (Auv + cfg.dt * cfg.theta * Auu).tocsr()[free]
+    assert abs(D).max() <= 1e-15 * abs(Auu).max()
+
+
+@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(3, (4, 2, 4))])
+def test_amg_blocks_structurally_symmetric(cfg):
+    pb = fsigen.get_problem(cfg)
+    o = pb.offsets
+    P = sp.csr_matrix((np.ones(pb.nnz), pb.colind, pb.rowptr), shape=(pb.n, pb.n))
+    for lo, hi in ((o[0], o[1]), (o[3], o[4])):
+        B = P[lo:hi, lo:hi]
+        assert (B != B.T).nnz == 0
+    Svv = P[o[1]:o[2], o[1]:o[2]] + P[o[1]:o[2], o[2]:o[3]]
+    assert (Svv != Svv.T).nnz == 0
+
+
+def test_seeded_state_bounds_and_boundary():
+    pb = fsigen.get_problem(small(2, (8, 8)))
+    U = pb.seeded_state(0, 1e-2)
+    assert np.max(np.abs(U)) <= 1e-2 + 1e-15
+    X = pb.coords
+    on = (X[:, 0] == 0) | (X[:, 1] == 0) | np.isclose(X[:, 0], 2.0) | np.isclose(X[:, 1], 1.0)
+    assert np.max(np.abs(U[on])) <= 1e-15
+    b1, b2 = pb.rhs(0), pb.rhs(0)
+    assert np.array_equal(b1, b2) and np.all(b1[pb.fixed] == 0)

@@ -1,0 +1,159 @@
+"""Pins of the oracle's Alg. 2 preconditioner and FGMRES on tiny seeded FSI
+systems: dense LU brute force, the exact-sub-solve identity
+P = (D + L) D^-1 (D + U), the <= 3-iteration bound for exact block-triangular
+preconditioning, exact LDU = 1 iteration, monotone residuals, and the Givens
+least-squares estimate equal to the true residual and to lstsq."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import fsigen
+import oracle
+from oracle.fgmres import fgmres
+
+
+def tiny(dim):
+    if dim == 2:
+        return fsigen.make_system(fsigen.CONFIGS["2d_tiny"].with_(name="o2", n=(8, 8)))
+    return fsigen.make_system(fsigen.CONFIGS["3d"].with_(name="o3", n=(4, 2, 4)))
+
+
+def params(dim):
+    return oracle.PrecondParams(mass_ratio=8.0 if dim == 2 else 20.0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fgmres_alg2_matches_dense_lu(dim):
+    s = tiny(dim)
+    A = s.scipy()
+    xd = sla.solve(A.toarray(), s.rhs)
+    o = oracle.OracleSolver.from_system(s, params(dim))
+    r = o.solve(s.rhs, tol=1e-8)
+    assert r.converged and r.true_relres <= 1e-8
+    kappa_bound = np.linalg.cond(A.toarray(), 1)
+    err = np.linalg.norm(r.x - xd) / np.linalg.norm(xd)
+    assert err <= kappa_bound * 1e-8
+    r12 = o.solve(s.rhs, tol=1e-12, restart=200)
+    assert np.linalg.norm(r12.x - xd) / np.linalg.norm(xd) <= 1e-9
+    # within a cycle the residual estimate never increases (nested Krylov spaces)
+    bounds = list(r.cycle_starts) + [len(r.history)]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        h = np.array(r.history[a:b])
+        assert np.all(np.diff(h) <= 1e-14)
+
+
+def _dense_blocks(s):
+    A = s.scipy().toarray()
+    o = s.offsets
+    I = [slice(o[0], o[1]), slice(o[1], o[3]), slice(o[3], o[5])]
+    return A, I
+
+
+def test_exact_alg2_is_block_symmetric_gauss_seidel():
+    s = tiny(2)
+    A, I = _dense_blocks(s)
+    D = np.zeros_like(A)
+    L = np.zeros_like(A)
+    U = np.zeros_like(A)
+    for a in range(3):
+        for b in range(3):
+            blk = A[I[a], I[b]]
+            if a == b:
+                D[I[a], I[b]] = blk
+            elif a > b and not (a == 1 and b == 0):     # C_sm dropped
+                L[I[a], I[b]] = blk
+            elif a < b:
+                U[I[a], I[b]] = blk
+    P = (D + L) @ np.linalg.solve(D, D + U)
+    pre = oracle.BlockLDU(s.scipy(), s.offsets, 2, exact=True)
+    r = np.random.default_rng(5).standard_normal(A.shape[0])
+    assert np.allclose(pre(r), np.linalg.solve(P, r), rtol=1e-9, atol=1e-9 * np.abs(np.linalg.solve(P, r)).max())
+
+
+def test_exact_block_triangular_converges_in_three_iterations():
+    """T = L D = [[M,0,0],[C_sm,S1,0],[C_fm,C~_fs,X]] of the exact LDU (Sec. 4.1) with
+    the true Schur complements: T^-1 A = U is unit block upper triangular, so
+    (T^-1 A - I)^3 = 0 and GMRES stops within 3 iterations.  The system is first
+    equilibrated by diagonal row and column scalings (which keep the block
+    structure and the theorem) so that rounding stays far below the tolerance."""
+    s = tiny(2)
+    A, I = _dense_blocks(s)
+    rs = 1.0 / np.abs(A).max(axis=1)
+    A = rs[:, None] * A
+    cs = 1.0 / np.abs(A).max(axis=0)
+    A = A * cs[None, :]
+    rhs = rs * s.rhs
+    M, Cms = A[I[0], I[0]], A[I[0], I[1]]
+    Csm, S, Csf = A[I[1], I[0]], A[I[1], I[1]], A[I[1], I[2]]
+    Cfm, Cfs, F = A[I[2], I[0]], A[I[2], I[1]], A[I[2], I[2]]
+    S1 = S - Csm @ np.linalg.solve(M, Cms)
+    Cfs_t = Cfs - Cfm @ np.linalg.solve(M, Cms)
+    X = F - Cfs_t @ np.linalg.solve(S1, Csf)
+    T = np.zeros_like(A)
+    T[I[0], I[0]] = M
+    T[I[1], I[0]], T[I[1], I[1]] = Csm, S1
+    T[I[2], I[0]], T[I[2], I[1]], T[I[2], I[2]] = Cfm, Cfs_t, X
+    lu = sla.lu_factor(T)
+    res = fgmres(lambda v: A @ v, lambda r: sla.lu_solve(lu, r), rhs, tol=1e-10, restart=20, maxit=20)
+    assert res.converged and res.iters <= 3
+    # full LDU with those factors reproduces A exactly: one iteration
+    Lf = np.eye(A.shape[0])
+    Lf[I[1], I[0]] = Csm @ np.linalg.inv(M)
+    Lf[I[2], I[0]] = Cfm @ np.linalg.inv(M)
+    Lf[I[2], I[1]] = Cfs_t @ np.linalg.inv(S1)
+    Df = np.zeros_like(A)
+    Df[I[0], I[0]], Df[I[1], I[1]], Df[I[2], I[2]] = M, S1, X
+    Uf = np.eye(A.shape[0])
+    Uf[I[0], I[1]] = np.linalg.solve(M, Cms)
+    Uf[I[1], I[2]] = np.linalg.solve(S1, Csf)
+    P = Lf @ Df @ Uf
+    assert np.allclose(P, A, atol=1e-8 * np.abs(A).max())
+    lu = sla.lu_factor(P)
+    res = fgmres(lambda v: A @ v, lambda r: sla.lu_solve(lu, r), rhs, tol=1e-10, restart=20, maxit=20)
+    assert res.converged and res.iters == 1
+
+
+def test_solid_schur_alg3_with_exact_inverses_is_exact():
+    s = tiny(2)
+    pre = oracle.BlockLDU(s.scipy(), s.offsets, 2)
+    B = pre.B
+    from oracle.precond import _ExactInverse
+    pre.Shat_inv = _ExactInverse(pre.S_hat)
+    pre.Ms_inv = _ExactInverse(B.A_uu)
+    r = np.random.default_rng(2).standard_normal(B.S.shape[0])
+    x = pre.S_inv(r)
+    x_direct = np.linalg.solve(B.S.toarray(), r)
+    # an algebra slip shows as an O(1) difference; rounding (cond(S) ~ 1e9) stays << 1e-6
+    assert np.linalg.norm(x - x_direct) <= 1e-6 * np.linalg.norm(x_direct)
+
+
+def test_fluid_schur_elimination_with_exact_schur_is_exact():
+    s = tiny(2)
+    pre = oracle.BlockLDU(s.scipy(), s.offsets, 2)
+    B = pre.B
+    from oracle.precond import _ExactInverse
+    Aff = B.A_ff.toarray()
+    Sp_exact = B.C_pp.toarray() - B.B_pv.toarray() @ np.linalg.solve(Aff, B.B_vp.toarray())
+    pre.Aff_inv = _ExactInverse(B.A_ff)
+    pre.Sp_inv = lambda r: np.linalg.solve(Sp_exact, r)
+    r = np.random.default_rng(4).standard_normal(B.F.shape[0])
+    x = pre.F_inv(r)
+    x_direct = np.linalg.solve(B.F.toarray(), r)
+    assert np.linalg.norm(x - x_direct) <= 1e-6 * np.linalg.norm(x_direct)
+
+
+def test_givens_estimate_equals_true_residual_and_lstsq():
+    s = tiny(2)
+    A = s.scipy()
+    pre = oracle.BlockLDU(A, s.offsets, 2, params=params(2))
+    Zs = []
+    rec = lambda r: (Zs.append(pre(r)), Zs[-1])[1]
+    k = 6          # residual still far above the rounding floor of this ill-scaled system
+    res = fgmres(lambda v: A @ v, rec, s.rhs, tol=1e-30, restart=k, maxit=k)
+    est = res.history[-1] * np.linalg.norm(s.rhs)
+    true = np.linalg.norm(s.rhs - A @ res.x)
+    assert est == pytest.approx(true, rel=1e-6)
+    Z = np.column_stack(Zs)
+    y, *_ = np.linalg.lstsq((A @ Z), s.rhs, rcond=None)
+    assert np.linalg.norm(s.rhs - A @ (Z @ y)) == pytest.approx(true, rel=1e-6)
