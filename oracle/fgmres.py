@@ -1,6 +1,9 @@
 """Right-preconditioned flexible GMRES (Saad, Iterative Methods for Sparse Linear
-Systems, 2nd ed., Alg. 9.6) with modified Gram-Schmidt Arnoldi and Givens
-rotations for the Hessenberg least-squares problem.  The paper solves each
+Systems, 2nd ed., Alg. 9.6) with Givens rotations for the Hessenberg
+least-squares problem.  The Arnoldi step orthogonalises by classical
+Gram-Schmidt applied twice (Giraud, Langou & Rozloznik, Comput. Math. Appl. 50,
+2005: "twice is enough"): on these badly scaled Jacobians (condition numbers
+near 1e14) single-pass modified Gram-Schmidt loses orthogonality and stalls.  The paper solves each
 Newton step's system A_h dU = F_h with GMRES preconditioned by Alg. 2 (Sec. 4,
 Sec. 6 solver settings); the stopping rule here is the relative residual
 ||b - A x|| / ||b|| <= tol, checked on the Givens estimate and confirmed on the
@@ -59,9 +62,10 @@ def fgmres(A, M, b, tol=1e-8, restart=100, maxit=1000, x0=None) -> FGMRESResult:
             Z[j] = M(V[j])
             w = A(Z[j])
             wnorm0 = np.sqrt(np.dot(w, w))
-            for i in range(j + 1):
-                H[i, j] = np.dot(V[i], w)
-                w = w - H[i, j] * V[i]
+            for _ in range(2):                      # classical Gram-Schmidt, twice
+                h = V[:j + 1] @ w
+                w = w - V[:j + 1].T @ h
+                H[:j + 1, j] += h
             H[j + 1, j] = np.sqrt(np.dot(w, w))
             # apply the previous rotations to column j, then form the new one
             for i in range(j):
