@@ -1,0 +1,198 @@
+/*
+ * fsi.h - C ABI of the GB300 (sm_103a) solver for one linearised monolithic
+ * ALE fluid-structure Jacobian.
+ *
+ * The operation is the linear solve A_h dU = F_h of one Newton step (Alg. 1,
+ * Sec. 3.3) for the block system of Eq. (mat:small), Sec. 3.4:
+ *
+ *       [ M     C_ms  0    ]   m : mesh displacement u outside the solid
+ *   A = [ C_sm  S     C_sf ]   s : solid velocity v and displacement u (closed solid region)
+ *       [ C_fm  C_fs  F    ]   f : fluid velocity v and pressure p
+ *
+ * solved by right-preconditioned FGMRES whose preconditioner is the approximate
+ * block-LDU factorisation of Sec. 4.1 (Alg. 2) with the solid Schur solve of
+ * Sec. 4.3 (Alg. 3), a pressure Schur-complement fluid solve (Sec. 4.4) and
+ * smoothed-aggregation AMG V-cycles for the sub-block inverses (Sec. 4.2-4.4).
+ *
+ * Conventions shared by all calls
+ *   - Unknowns are ordered by class: m | s_v | s_u | f_v | f_p.  The vector
+ *     classes (m, s_v, s_u, f_v) are node-major, component-minor (dim values per
+ *     node); s_v and s_u list the same nodes in the same order.
+ *   - Matrix input is CSR with 64-bit row pointers, 32-bit column indices sorted
+ *     within each row, FP64 values.  Fixed (Dirichlet) DOFs are identity rows
+ *     with their columns removed.
+ *   - Device pointers (`*_dev`) are CUDA device memory the caller owns (e.g.
+ *     PyTorch tensors) and must stay valid during the call; the library works on
+ *     the stream given to fsi_setup and returns after that stream has finished
+ *     the call's work.
+ *   - Every call returns FSI_OK (0) or a negative FSI_E* code; fsi_last_error()
+ *     gives the message of the last failure on that context.  No call aborts the
+ *     process.  Device memory the library allocates is released by fsi_free().
+ */
+#ifndef FSI_H_
+#define FSI_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FSI_OK = 0,
+  FSI_EINVAL = -1,       /* bad argument, malformed CSR or offsets, call out of order */
+  FSI_ENOMEM = -2,       /* device allocation failed */
+  FSI_ECUDA = -3,        /* CUDA runtime error */
+  FSI_ENOTCONV = -4,     /* maxit reached: x holds the last iterate, stats are filled */
+  FSI_EBREAKDOWN = -5,   /* Arnoldi breakdown before the tolerance was met */
+  FSI_ENONFINITE = -6    /* non-finite right-hand side or iterate */
+};
+
+enum { FSI_FP64 = 0, FSI_FP32_AMG = 1 };
+
+enum {
+  FSI_X0_GIVEN = 1,        /* fsi_solve starts from the x passed in (else from 0) */
+  FSI_USE_GRAPHS = 2,      /* replay each FGMRES iteration as one captured CUDA graph */
+  FSI_NO_RIGID_MODES = 4   /* solid AMG with translations only, even when coordinates are given */
+};
+
+typedef struct fsi_params {
+  int restart;              /* FGMRES restart length m (default 100) */
+  int maxit;                /* maximum FGMRES iterations (default 1000) */
+  int flags;                /* FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES */
+  double dt_theta;          /* c = dt*theta of the solid Schur complement S_hat = A_vv + c A_vu (0.01) */
+  /* smoothed-aggregation AMG */
+  double strength_theta;    /* strength threshold on node-block Frobenius norms (0.08) */
+  int coarse_max;           /* coarsen until <= this many scalar rows (500) */
+  int max_levels;           /* (10) */
+  int cheb_degree;          /* Chebyshev smoother degree (4) */
+  double cheb_ratio;        /* smoothing interval [lambda/ratio, upper*lambda] (30) */
+  double cheb_upper;        /* (1.3) */
+  int power_iters;          /* power iterations for lambda_max(D^-1 A) (15) */
+  double drop_tol;          /* near-nullspace column drop in the tentative prolongator (1e-10) */
+  int presmooth, postsmooth;/* Chebyshev sweeps before/after the coarse correction (1, 1) */
+  /* V-cycles per application of each block inverse */
+  int vcycles_mesh, vcycles_solid, vcycles_fluid, vcycles_pressure;   /* (1, 2, 1, 1) */
+  /* solid mass solve: Chebyshev polynomial on D^-1 A_uu */
+  int mass_degree;          /* (12) */
+  double mass_ratio;        /* interval [lambda/ratio, upper*lambda] (8 in 2D, 20 in 3D) */
+} fsi_params;
+
+typedef struct fsi_stats {
+  int iters;                /* FGMRES iterations of the last solve */
+  int cycles;               /* restart cycles */
+  int status;               /* FSI_OK / FSI_ENOTCONV / ... */
+  double true_relres;       /* ||b - A x|| / ||b|| of the returned x (FP64 on the device) */
+  double setup_s;           /* fsi_setup wall seconds */
+  double precond_build_s;   /* fsi_precond_build wall seconds */
+  double solve_s;           /* fsi_solve wall seconds (stream synchronised) */
+  double operator_bytes;    /* algorithmic bytes of one outer SpMV */
+  double precond_bytes;     /* algorithmic bytes of one application of Alg. 2 */
+  const double* relres_hist;/* |g_{j+1}|/||b|| per iteration; owned by the context, valid until the next solve */
+  int hist_len;
+  int64_t kernel_launches;  /* CUDA kernels the solve executed (graph replays counted per kernel node) */
+} fsi_stats;
+
+typedef struct fsi_ctx fsi_ctx;
+
+/* Defaults for dim = 2 or 3 (mass_ratio depends on dim). */
+void fsi_default_params(fsi_params* p, int dim);
+
+/*
+ * fsi_setup - copy one monolithic Jacobian to the device and split it into the
+ * class blocks of Eq. (mat:small).
+ *   out            receives the new context (NULL on failure; then only the
+ *                  return code reports the error)
+ *   dim            2 or 3
+ *   n              number of unknowns (= block_offsets[5])
+ *   rowptr/colind/vals   host CSR, n+1 / nnz / nnz entries (deep-copied; the
+ *                  caller may free them after return)
+ *   block_offsets  host, 6 entries: start of m, s_v, s_u, f_v, f_p, and n;
+ *                  non-decreasing, vector classes multiples of dim, |s_v| = |s_u|
+ *   node_coords    host, nullable: dim coordinates per s_v node (rigid-body
+ *                  near-nullspace of the solid AMG); copied
+ *   p              nullable (defaults)
+ *   cuda_stream    cudaStream_t to run on (NULL = a stream the context creates)
+ * Errors: FSI_EINVAL on inconsistent sizes, unsorted or out-of-range columns,
+ * non-finite values; FSI_ENOMEM / FSI_ECUDA from the device.
+ */
+int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+              const int64_t* block_offsets, const double* node_coords, const fsi_params* p, void* cuda_stream);
+
+/*
+ * fsi_precond_build - build the preconditioner of Alg. 2 on the device: the
+ * Schur approximations S_hat = A_vv + c A_vu (Alg. 3) and
+ * S_p = C_pp - B_pv diag(A_ff)^-1 B_vp (Sec. 4.4), and smoothed-aggregation
+ * hierarchies for M, S_hat, A_ff and S_p (set-up timed apart from the solve).
+ *   precision   FSI_FP64, or FSI_FP32_AMG: hierarchies, smoothers and the
+ *               couplings inside P^-1 stored and run in FP32 (FP32 accumulation)
+ *               while the outer SpMV, Gram-Schmidt and Givens stay FP64.
+ *               May be called again to switch precision (the FP64 hierarchy is
+ *               built once).
+ *   learned_weights  must be NULL (reserved).
+ */
+int fsi_precond_build(fsi_ctx* ctx, int precision, const char* learned_weights);
+
+/*
+ * fsi_solve - FGMRES (right preconditioned, restart m) until
+ * ||b - A x||_2 / ||b||_2 <= rtol, confirmed on the true residual.
+ *   rhs_dev  device, n doubles (not modified)
+ *   x_dev    device, n doubles: initial guess when FSI_X0_GIVEN is set, else
+ *            overwritten from 0; receives the solution (best iterate on
+ *            FSI_ENOTCONV)
+ *   out      nullable; filled on FSI_OK, FSI_ENOTCONV and FSI_EBREAKDOWN
+ */
+int fsi_solve(fsi_ctx* ctx, const double* rhs_dev, double* x_dev, double rtol, fsi_stats* out);
+
+/* Release every device and host resource of the context (NULL is ignored). */
+void fsi_free(fsi_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none; static text for NULL). */
+const char* fsi_last_error(const fsi_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Component entry points (same context, after fsi_precond_build).  They expose
+ * the pieces of the solve for parity checks and per-kernel timing.
+ */
+
+/* y = A x, the monolithic operator (Eq. mat:small), FP64; x_dev, y_dev: n doubles.
+ * Like fsi_apply_block, this call only enqueues its kernels on the context's
+ * stream and returns; synchronise that stream before reading y. */
+int fsi_apply_operator(fsi_ctx* ctx, const double* x_dev, double* y_dev);
+
+/*
+ * out = B^-1 in for one block inverse of Alg. 2, in the built precision (FP64
+ * inputs/outputs; converted internally in the FP32 form):
+ *   which 0  M^-1      (mesh,   m DOFs):   vcycles_mesh V-cycles
+ *         1  S_hat^-1  (solid velocity Schur, s_v DOFs)
+ *         2  A_ff^-1   (fluid velocity, f_v DOFs)
+ *         3  S_p^-1    (pressure Schur, f_p DOFs)
+ *         4  A_uu^-1   (solid mass Chebyshev, s_u DOFs)
+ *         5  S^-1      (Alg. 3 on s_v,s_u DOFs)
+ *         6  F^-1      (fluid Schur solve on f_v,f_p DOFs)
+ *         7  P^-1      (Alg. 2, all n DOFs)
+ * Enqueued on the context's stream without waiting (see fsi_apply_operator).
+ */
+int fsi_apply_block(fsi_ctx* ctx, int which, const double* in_dev, double* out_dev);
+
+/*
+ * AMG hierarchy inspection (which 0..3 as above, level >= 0).
+ *   info[0] levels, [1] block rows of this level, [2] block size, [3] nnz blocks,
+ *   [4] aggregates formed from this level (0 on the coarsest), [5] scalar rows of
+ *   the coarsest level;  *lambda = lambda_max(D^-1 A) estimate of the level.
+ */
+int fsi_amg_info(fsi_ctx* ctx, int which, int level, int64_t info[6], double* lambda);
+/*
+ * Copy one array of a level to host memory `dst` (caller sizes it from
+ * fsi_amg_info): what 0 aggregate id per node (int32, -1 = unaggregated),
+ * 1 A row pointers (int32, rows+1), 2 A block columns (int32), 3 A values
+ * (double, nnzb*b*b, row-major blocks), 4 P row pointers, 5 P block columns,
+ * 6 P values (b x k blocks), 7 P block columns count as int64 in dst[0].
+ */
+int fsi_amg_export(fsi_ctx* ctx, int which, int level, int what, void* dst);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSI_H_ */

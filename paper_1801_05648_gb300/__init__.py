@@ -1,0 +1,11 @@
+"""GB300-native block-preconditioned FGMRES for monolithic ALE fluid-structure
+Jacobians (Jodlbauer, Langer & Wick, arXiv:1801.05648, Sec. 4).
+
+The solver lives in ``libfsi.so`` (CUDA, sm_103a) behind the C ABI of
+``include/fsi.h``; ``fsi.py`` is its ctypes binding.
+"""
+from .fsi import (FSISolver, FSIError, Params, SolveStats, default_params, load_library, BLOCKS, EXPORTED,
+                  FSI_FP64, FSI_FP32_AMG, FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, LIB_PATH)
+
+__all__ = ["FSISolver", "FSIError", "Params", "SolveStats", "default_params", "load_library", "BLOCKS", "EXPORTED",
+           "FSI_FP64", "FSI_FP32_AMG", "FSI_X0_GIVEN", "FSI_USE_GRAPHS", "FSI_NO_RIGID_MODES", "LIB_PATH"]

@@ -1,0 +1,98 @@
+// Smoothed-aggregation AMG (Vanek, Mandel & Brezina 1996) on the GPU: set-up
+// (strength, distance-2 MIS aggregation, tentative prolongator by per-aggregate
+// modified Gram-Schmidt, Jacobi-smoothed prolongator, Galerkin triple product)
+// and the V-cycle apply with Chebyshev smoothing, in FP64 or FP32.
+//
+// Set-up per level:
+//   strength   j != i strong iff max(f_ij, f_ji) > 0 and >= theta*sqrt(f_ii f_jj),
+//              f = Frobenius norm of the node block (squares summed in row-major
+//              order without fused multiply-add)
+//   aggregate  distance-2 maximal independent set with keys
+//              (state << 59 | priority << 27 | index), priorities
+//              splitmix64(i + level*2^32) >> 32 (Bell, Dalton & Olson 2012);
+//              roots seed aggregates, neighbours of roots join them, every other
+//              non-isolated node joins its aggregated neighbour of largest
+//              (priority, index); isolated nodes stay out
+//   P_tent     per aggregate MGS QR of the near-nullspace rows (members in
+//              increasing node order), dropped columns below drop_tol
+//   P          (I - omega D^-1 A) P_tent, omega = 4/(3 lambda),
+//              lambda = |lambda_max(D^-1 A)| by power iteration from
+//              x_i = 1 + u_i (splitmix64 stream 256 + level)
+//   A_c        R (A P),  R = P^T
+// Coarsest level: dense inverse (all-zero rows replaced by identity rows).
+#pragma once
+#include "common.cuh"
+
+namespace fsi {
+
+struct AmgParams {
+  double theta = 0.08;
+  int coarse_max = 500;
+  int max_levels = 10;
+  int cheb_degree = 4;
+  double cheb_ratio = 30.0;
+  double cheb_upper = 1.3;
+  int power_iters = 15;
+  double drop_tol = 1e-10;
+  int presmooth = 1;
+  int postsmooth = 1;
+};
+
+template <class T>
+struct LevelWork {
+  DBuf<T> b, x, xb, r, d;   // rhs, iterate, ping-pong iterate, residual, Chebyshev direction
+};
+
+struct AmgLevel {
+  Bsr A;
+  DBuf<double> dinv64;
+  DBuf<float> dinv32;
+  double lam = 0.0;
+  Bsr P, R;
+  int nagg = 0;
+  DBuf<int> agg;              // aggregate of each node (-1 = none), for inspection
+  LevelWork<double> w64;
+  LevelWork<float> w32;
+  int64_t n() const { return A.rows(); }
+};
+
+struct Hierarchy {
+  std::vector<AmgLevel> levels;
+  int ncoarse = 0;
+  DBuf<double> cinv64;
+  DBuf<float> cinv32;
+  AmgParams prm;
+  bool has_fp32 = false;
+  double operator_complexity() const;
+  // algorithmic bytes of one V-cycle (value size vb)
+  double vcycle_bytes(int vb) const;
+};
+
+// Build the hierarchy of A (FP64 values, square, br == bc) with near-nullspace B
+// (device, (A.rows()) x k, node-major rows, row-major k columns).
+void amg_setup(Hierarchy& H, Bsr&& A, const double* B, int k, const AmgParams& prm, cudaStream_t s);
+// FP32 copies of every level's matrices, diagonal and coarse inverse.
+void amg_make_fp32(Hierarchy& H, cudaStream_t s);
+// x = V(b): one V-cycle from x = 0 (x, b: level-0 sized, distinct)
+template <class T> void amg_vcycle(Hierarchy& H, const T* b, T* x, cudaStream_t s);
+
+// Chebyshev polynomial smoother/solver on D^-1 A from x = 0 (used for the solid
+// mass matrix): x = p(D^-1 A) D^-1 b with `degree` steps over [lam/ratio, upper*lam].
+struct ChebSolver {
+  Bsr A;
+  DBuf<double> dinv64;
+  DBuf<float> dinv32;
+  double lam = 0.0;
+  int degree = 12;
+  double ratio = 8.0, upper = 1.3;
+  LevelWork<double> w64;
+  LevelWork<float> w32;
+};
+void cheb_setup(ChebSolver& C, Bsr&& A, int degree, double ratio, double upper, int power_iters, cudaStream_t s);
+void cheb_make_fp32(ChebSolver& C, cudaStream_t s);
+template <class T> void cheb_apply(ChebSolver& C, const T* b, T* x, cudaStream_t s);
+
+// |lambda_max(D^-1 A)| estimate by power iteration (see above), FP64.
+double power_lambda(const Bsr& A, const double* dinv, int iters, int stream_id, cudaStream_t s);
+
+}  // namespace fsi

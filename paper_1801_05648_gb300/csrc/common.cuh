@@ -1,0 +1,110 @@
+// Shared device-side definitions of the FSI solver library: error handling,
+// device buffers, the block-sparse-row (BSR) matrix type and small helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+#include <stdexcept>
+
+namespace fsi {
+
+// Error raised inside the library; converted to a status code at the C ABI.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+enum Status { OK = 0, EINVAL_ = -1, ENOMEM_ = -2, ECUDA_ = -3, ENOTCONV_ = -4, EBREAKDOWN_ = -5, ENONFINITE_ = -6 };
+
+#define FSI_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) {                                                                    \
+      if (e_ == cudaErrorMemoryAllocation)                                                      \
+        throw ::fsi::Error(::fsi::ENOMEM_, std::string("out of device memory at ") + #call);    \
+      throw ::fsi::Error(::fsi::ECUDA_, std::string(cudaGetErrorString(e_)) + " at " + #call);  \
+    }                                                                                           \
+  } while (0)
+
+// Kernel launches issued by the library (captured launches are re-counted per
+// graph replay by the solver).
+inline int64_t g_kernel_launches = 0;
+
+#define FSI_CHECK_LAUNCH()        \
+  do {                            \
+    ++::fsi::g_kernel_launches;   \
+    FSI_CUDA(cudaGetLastError()); \
+  } while (0)
+
+inline void require(bool ok, const std::string& msg) {
+  if (!ok) throw Error(EINVAL_, msg);
+}
+
+// Owning device buffer.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  explicit DBuf(size_t count) { alloc(count); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    n = count;
+    if (count) FSI_CUDA(cudaMalloc(&p, count * sizeof(T)));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr; n = 0;
+  }
+  T* get() const { return p; }
+};
+
+// Block sparse row matrix on the device: nbr x nbc blocks of br x bc values,
+// block values row-major, blocks of a row stored consecutively with sorted
+// block-column indices.  Values may exist in FP64, FP32 or both.
+struct Bsr {
+  int nbr = 0, nbc = 0, br = 1, bc = 1;
+  int64_t nnzb = 0;
+  DBuf<int> rowptr;     // nbr + 1
+  DBuf<int> colind;     // nnzb
+  DBuf<double> v64;     // nnzb * br * bc
+  DBuf<float> v32;      // optional FP32 copy
+  int tpr = 32;         // threads per block row for the SpMV, from the mean row length
+  int64_t rows() const { return (int64_t)nbr * br; }
+  int64_t cols() const { return (int64_t)nbc * bc; }
+  template <class T> const T* vals() const;
+  // algorithmic bytes of one SpMV: values + column indices + row pointers + x + y
+  double spmv_bytes(int value_bytes) const {
+    return (double)nnzb * (br * bc * value_bytes + 4) + 4.0 * (nbr + 1) + (double)value_bytes * (cols() + rows());
+  }
+};
+template <> inline const double* Bsr::vals<double>() const { return v64.p; }
+template <> inline const float* Bsr::vals<float>() const { return v32.p; }
+
+inline int choose_tpr(int64_t nnzb, int nbr) {
+  double mean = nbr ? (double)nnzb / nbr : 0.0;
+  if (mean >= 24) return 32;
+  if (mean >= 12) return 16;
+  if (mean >= 6) return 8;
+  return 4;
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Streams and scratch shared by one context.
+struct Exec {
+  cudaStream_t stream = nullptr;
+  int num_sms = 152;
+};
+
+}  // namespace fsi

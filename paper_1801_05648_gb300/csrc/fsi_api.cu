@@ -1,0 +1,283 @@
+// C ABI of the solver (declarations and contract in include/fsi.h).
+#include "../../include/fsi.h"
+#include "solver.cuh"
+#include "vec.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+struct fsi_ctx {
+  fsi::Context C;
+};
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+template <class F>
+int guarded(fsi_ctx* ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->C.err.clear();
+    return FSI_OK;
+  } catch (const fsi::Error& e) {
+    if (ctx) ctx->C.err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->C.err = "host allocation failed";
+    return FSI_ENOMEM;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->C.err = e.what();
+    return FSI_ECUDA;
+  }
+}
+
+void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
+  s.restart = p.restart;
+  s.maxit = p.maxit;
+  s.flags = p.flags;
+  s.dt_theta = p.dt_theta;
+  s.amg.theta = p.strength_theta;
+  s.amg.coarse_max = p.coarse_max;
+  s.amg.max_levels = p.max_levels;
+  s.amg.cheb_degree = p.cheb_degree;
+  s.amg.cheb_ratio = p.cheb_ratio;
+  s.amg.cheb_upper = p.cheb_upper;
+  s.amg.power_iters = p.power_iters;
+  s.amg.drop_tol = p.drop_tol;
+  s.amg.presmooth = p.presmooth;
+  s.amg.postsmooth = p.postsmooth;
+  s.vc_mesh = p.vcycles_mesh;
+  s.vc_solid = p.vcycles_solid;
+  s.vc_fluid = p.vcycles_fluid;
+  s.vc_pressure = p.vcycles_pressure;
+  s.mass_degree = p.mass_degree;
+  s.mass_ratio = p.mass_ratio;
+}
+
+void validate_params(const fsi::SolverParams& s) {
+  using fsi::require;
+  require(s.restart >= 1 && s.restart <= 1000, "restart must be in [1, 1000]");
+  require(s.maxit >= 1, "maxit must be >= 1");
+  require(s.amg.cheb_degree >= 1 && s.amg.presmooth >= 1 && s.amg.postsmooth >= 0, "smoother settings");
+  require(s.amg.cheb_ratio > 1.0 && s.amg.cheb_upper >= 1.0, "Chebyshev interval settings");
+  require(s.amg.coarse_max >= 1 && s.amg.max_levels >= 1 && s.amg.power_iters >= 1, "AMG level settings");
+  require(s.vc_mesh >= 1 && s.vc_solid >= 1 && s.vc_fluid >= 1 && s.vc_pressure >= 1, "V-cycle counts");
+  require(s.mass_degree >= 1 && s.mass_ratio > 1.0, "mass solve settings");
+  require(std::isfinite(s.dt_theta), "dt_theta");
+}
+
+void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                  const int64_t* off) {
+  using fsi::require;
+  require(dim == 2 || dim == 3, "dim must be 2 or 3");
+  require(n > 0 && n < (int64_t)1 << 31, "n out of range");
+  require(rowptr && colind && vals && off, "null CSR or offsets");
+  require(off[0] == 0 && off[5] == n, "block_offsets must start at 0 and end at n");
+  for (int k = 0; k < 5; ++k) require(off[k] <= off[k + 1], "block_offsets must be non-decreasing");
+  for (int k = 0; k < 4; ++k) require((off[k + 1] - off[k]) % dim == 0, "vector classes must be multiples of dim");
+  require(off[2] - off[1] == off[3] - off[2], "s_v and s_u must have the same size");
+  require(rowptr[0] == 0, "rowptr[0] must be 0");
+  for (int64_t r = 0; r < n; ++r) {
+    require(rowptr[r + 1] >= rowptr[r], "rowptr must be non-decreasing");
+    for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+      require(colind[k] >= 0 && colind[k] < n, "column index out of range");
+      require(k == rowptr[r] || colind[k] > colind[k - 1], "columns must be strictly increasing within a row");
+      require(std::isfinite(vals[k]), "non-finite matrix value");
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void fsi_default_params(fsi_params* p, int dim) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->restart = 100;
+  p->maxit = 1000;
+  p->flags = 0;
+  p->dt_theta = 0.01;
+  p->strength_theta = 0.08;
+  p->coarse_max = 500;
+  p->max_levels = 10;
+  p->cheb_degree = 4;
+  p->cheb_ratio = 30.0;
+  p->cheb_upper = 1.3;
+  p->power_iters = 15;
+  p->drop_tol = 1e-10;
+  p->presmooth = 1;
+  p->postsmooth = 1;
+  p->vcycles_mesh = 1;
+  p->vcycles_solid = 2;
+  p->vcycles_fluid = 1;
+  p->vcycles_pressure = 1;
+  p->mass_degree = 12;
+  p->mass_ratio = dim == 3 ? 20.0 : 8.0;
+}
+
+int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+              const int64_t* block_offsets, const double* node_coords, const fsi_params* p, void* cuda_stream) {
+  if (!out) return FSI_EINVAL;
+  *out = nullptr;
+  fsi_ctx* ctx = nullptr;
+  try {
+    ctx = new fsi_ctx();
+  } catch (...) {
+    return FSI_ENOMEM;
+  }
+  int rc = guarded(ctx, [&] {
+    validate_csr(dim, n, rowptr, colind, vals, block_offsets);
+    fsi_params def;
+    fsi_default_params(&def, dim);
+    to_solver_params(p ? *p : def, ctx->C.prm);
+    validate_params(ctx->C.prm);
+    ctx->C.dim = dim;
+    ctx->C.n = n;
+    for (int k = 0; k < 6; ++k) ctx->C.off[k] = block_offsets[k];
+    if (cuda_stream) {
+      ctx->C.s = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      FSI_CUDA(cudaStreamCreateWithFlags(&ctx->C.s, cudaStreamNonBlocking));
+      ctx->C.own_stream = true;
+    }
+    fsi::context_setup(ctx->C, rowptr, colind, vals, node_coords);
+  });
+  if (rc != FSI_OK) {
+    g_setup_error = ctx->C.err;
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return FSI_OK;
+}
+
+int fsi_precond_build(fsi_ctx* ctx, int precision, const char* learned_weights) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(precision == FSI_FP64 || precision == FSI_FP32_AMG, "precision must be FSI_FP64 or FSI_FP32_AMG");
+    fsi::require(learned_weights == nullptr, "learned_weights must be NULL");
+    fsi::precond_build(ctx->C, precision);
+  });
+}
+
+int fsi_solve(fsi_ctx* ctx, const double* rhs_dev, double* x_dev, double rtol, fsi_stats* out) {
+  if (!ctx) return FSI_EINVAL;
+  int status = FSI_OK;
+  int rc = guarded(ctx, [&] {
+    fsi::require(rhs_dev && x_dev, "null rhs or x");
+    fsi::require(rtol > 0.0 && std::isfinite(rtol), "rtol must be positive");
+    status = fsi::fgmres_solve(ctx->C, rhs_dev, x_dev, rtol);
+  });
+  fsi::Context& C = ctx->C;
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->iters = C.last_iters;
+    out->cycles = C.last_cycles;
+    out->status = rc != FSI_OK ? rc : status;
+    out->true_relres = C.last_true_relres;
+    out->setup_s = C.setup_s;
+    out->precond_build_s = C.build_s;
+    out->solve_s = C.solve_s;
+    if (C.built) {
+      out->operator_bytes = fsi::operator_bytes(C);
+      out->precond_bytes = fsi::precond_bytes(C, C.precision == 1 ? 4 : 8);
+    }
+    out->relres_hist = C.hist.empty() ? nullptr : C.hist.data();
+    out->hist_len = (int)C.hist.size();
+    out->kernel_launches = C.last_launches;
+  }
+  if (rc != FSI_OK) return rc;
+  if (status == fsi::ENOTCONV_) C.err = "FGMRES reached maxit before rtol";
+  if (status == fsi::EBREAKDOWN_) C.err = "Arnoldi breakdown before rtol";
+  if (status == fsi::ENONFINITE_) C.err = "non-finite iterate";
+  return status;
+}
+
+void fsi_free(fsi_ctx* ctx) { delete ctx; }
+
+const char* fsi_last_error(const fsi_ctx* ctx) {
+  if (!ctx) return g_setup_error.c_str();
+  return ctx->C.err.c_str();
+}
+
+int fsi_apply_operator(fsi_ctx* ctx, const double* x_dev, double* y_dev) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(x_dev && y_dev, "null vector");
+    fsi::apply_operator(ctx->C, x_dev, y_dev);
+  });
+}
+
+int fsi_apply_block(fsi_ctx* ctx, int which, const double* in_dev, double* out_dev) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::Context& C = ctx->C;
+    fsi::require(C.built, "fsi_apply_block before fsi_precond_build");
+    fsi::require(in_dev && out_dev, "null vector");
+    fsi::require(which >= 0 && which <= 7, "unknown block");
+    const int64_t* o = C.off;
+    const int64_t len[8] = {o[1] - o[0], o[2] - o[1], o[4] - o[3], o[5] - o[4], o[3] - o[2], o[3] - o[1],
+                            o[5] - o[3], C.n};
+    if (C.precision == 1) {
+      auto& W = C.pw32;
+      fsi::cast<double, float>(len[which], in_dev, W.in.p, C.s);
+      fsi::apply_block<float>(C, which, W.in.p, W.out.p);
+      fsi::cast<float, double>(len[which], W.out.p, out_dev, C.s);
+    } else {
+      fsi::apply_block<double>(C, which, in_dev, out_dev);
+    }
+  });
+}
+
+int fsi_amg_info(fsi_ctx* ctx, int which, int level, int64_t info[6], double* lambda) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::Context& C = ctx->C;
+    fsi::require(C.built, "fsi_amg_info before fsi_precond_build");
+    fsi::require(which >= 0 && which <= 3 && info, "bad arguments");
+    fsi::Hierarchy& H = C.H[which];
+    fsi::require(level >= 0 && level < (int)H.levels.size(), "level out of range");
+    const fsi::AmgLevel& L = H.levels[level];
+    info[0] = (int64_t)H.levels.size();
+    info[1] = L.A.nbr;
+    info[2] = L.A.br;
+    info[3] = L.A.nnzb;
+    info[4] = (level + 1 < (int)H.levels.size()) ? L.nagg : 0;
+    info[5] = H.ncoarse;
+    if (lambda) *lambda = L.lam;
+  });
+}
+
+int fsi_amg_export(fsi_ctx* ctx, int which, int level, int what, void* dst) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::Context& C = ctx->C;
+    fsi::require(C.built, "fsi_amg_export before fsi_precond_build");
+    fsi::require(which >= 0 && which <= 3 && dst, "bad arguments");
+    fsi::Hierarchy& H = C.H[which];
+    fsi::require(level >= 0 && level < (int)H.levels.size(), "level out of range");
+    const fsi::AmgLevel& L = H.levels[level];
+    const bool has_p = level + 1 < (int)H.levels.size();
+    auto cp = [&](const void* src, size_t bytes) {
+      if (bytes) FSI_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, C.s));
+    };
+    switch (what) {
+      case 0: fsi::require(has_p, "no aggregates on the coarsest level"); cp(L.agg.p, sizeof(int) * L.A.nbr); break;
+      case 1: cp(L.A.rowptr.p, sizeof(int) * (L.A.nbr + 1)); break;
+      case 2: cp(L.A.colind.p, sizeof(int) * L.A.nnzb); break;
+      case 3: cp(L.A.v64.p, sizeof(double) * L.A.nnzb * L.A.br * L.A.bc); break;
+      case 4: fsi::require(has_p, "no P on the coarsest level"); cp(L.P.rowptr.p, sizeof(int) * (L.P.nbr + 1)); break;
+      case 5: fsi::require(has_p, "no P on the coarsest level"); cp(L.P.colind.p, sizeof(int) * L.P.nnzb); break;
+      case 6: fsi::require(has_p, "no P on the coarsest level");
+              cp(L.P.v64.p, sizeof(double) * L.P.nnzb * L.P.br * L.P.bc); break;
+      case 7: fsi::require(has_p, "no P on the coarsest level"); *static_cast<int64_t*>(dst) = L.P.nnzb; break;
+      default: throw fsi::Error(fsi::EINVAL_, "unknown export");
+    }
+    FSI_CUDA(cudaStreamSynchronize(C.s));
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,572 @@
+// Block-LDU preconditioned FGMRES for the monolithic FSI Jacobian.
+//
+// Block structure (Eq. mat:small): DOFs in the class order m | s_v | s_u | f_v | f_p,
+//   A = [[M, C_ms, 0], [C_sm, S, C_sf], [C_fm, C_fs, F]],  s = (s_v, s_u), f = (f_v, f_p).
+// P^-1 r (Alg. 2, Sec. 4.1):
+//   x_m = M^-1 r_m;  x_s = S^-1 r_s;  x_f = F^-1 (r_f - C_fm x_m - C_fs x_s);
+//   x_s -= S^-1 C_sf x_f;  x_m -= M^-1 C_ms x_s.
+// S^-1 (Alg. 3, Sec. 4.3): x_v = S_hat^-1 (r_v - A_vu A_uu^-1 r_u), S_hat = A_vv + dt*theta*A_vu;
+//   x_u = A_uu^-1 (r_u - A_uv x_v).
+// F^-1 (Sec. 4.4, pressure Schur complement S_p = C_pp - B_pv diag(A_ff)^-1 B_vp):
+//   y = A_ff^-1 r_v;  x_p = S_p^-1 (r_p - B_pv y);  x_v = A_ff^-1 (r_v - B_vp x_p).
+// Inverses: smoothed-aggregation V-cycles (M, S_hat, A_ff, S_p) and a Chebyshev
+// polynomial for the solid mass matrix A_uu.  The outer iteration is
+// right-preconditioned FGMRES (Saad Alg. 9.6) with classical Gram-Schmidt applied
+// twice and Givens rotations kept on the device.
+#include "solver.cuh"
+#include "spmv.cuh"
+#include "vec.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+namespace fsi {
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+inline double secs(clk::time_point a, clk::time_point b) { return std::chrono::duration<double>(b - a).count(); }
+
+template <class T> PrecWork<T>& pwork(Context& C);
+template <> PrecWork<double>& pwork<double>(Context& C) { return C.pw64; }
+template <> PrecWork<float>& pwork<float>(Context& C) { return C.pw32; }
+
+template <class T>
+void alloc_pw(PrecWork<T>& W, int64_t n) {
+  if (W.ready) return;
+  W.in.alloc(n); W.out.alloc(n); W.a2_t.alloc(n); W.a2_u.alloc(n);
+  W.s3_y.alloc(n); W.s3_t.alloc(n); W.mv_res.alloc(n); W.mv_cor.alloc(n);
+  W.ready = true;
+}
+
+void bsr_clone(const Bsr& A, Bsr& B, cudaStream_t s) {
+  B = Bsr();
+  B.nbr = A.nbr; B.nbc = A.nbc; B.br = A.br; B.bc = A.bc; B.nnzb = A.nnzb; B.tpr = A.tpr;
+  B.rowptr.alloc(A.nbr + 1);
+  B.colind.alloc(A.nnzb > 0 ? A.nnzb : 1);
+  B.v64.alloc(A.nnzb > 0 ? A.nnzb * A.br * A.bc : 1);
+  FSI_CUDA(cudaMemcpyAsync(B.rowptr.p, A.rowptr.p, sizeof(int) * (A.nbr + 1), cudaMemcpyDeviceToDevice, s));
+  if (A.nnzb) {
+    FSI_CUDA(cudaMemcpyAsync(B.colind.p, A.colind.p, sizeof(int) * A.nnzb, cudaMemcpyDeviceToDevice, s));
+    FSI_CUDA(cudaMemcpyAsync(B.v64.p, A.v64.p, sizeof(double) * A.nnzb * A.br * A.bc, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+template <class Ti, class To>
+__global__ void k_col_in(int64_t n, const Ti* __restrict__ V, int64_t ldv, const int* __restrict__ jdev, int joff,
+                         To* __restrict__ out) {
+  const int j = *jdev + joff;
+  const Ti* src = V + (size_t)j * ldv;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (To)src[i];
+}
+// zfix = (double) in; Z_j = zfix
+template <class T>
+__global__ void k_col_out(int64_t n, const T* __restrict__ in, double* __restrict__ zfix, double* __restrict__ Z,
+                          int64_t ldz, const int* __restrict__ jdev) {
+  double* dst = Z + (size_t)(*jdev) * ldz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)in[i];
+    zfix[i] = v;
+    dst[i] = v;
+  }
+}
+// V_{j+1} = w / h  (left zero when h == 0)
+__global__ void k_scale_col(int64_t n, const double* __restrict__ w, const double* __restrict__ h,
+                            double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev) {
+  const double hv = *h;
+  double* dst = V + (size_t)(*jdev + 1) * ldv;
+  const double inv = hv > 0.0 ? 1.0 / hv : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = w[i] * inv;
+}
+
+// Hessenberg column j = h1 + h2 (CGS2), h_{j+1,j} = ||w||; apply the previous
+// rotations, form the new one, update g.  Writes |g_{j+1}|/||b|| and a
+// breakdown flag to host-mapped memory.  One thread.
+__global__ void k_givens(int ldh, const int* __restrict__ jdev, const double* __restrict__ h1,
+                         const double* __restrict__ h2, const double* __restrict__ hnorm, double* __restrict__ H,
+                         double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                         const double* __restrict__ inv_bnorm_p, double* __restrict__ out) {
+  const double inv_bnorm = *inv_bnorm_p;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = *jdev;
+  double* col = H + (size_t)j * ldh;
+  double w0 = 0.0;
+  for (int i = 0; i <= j; ++i) {
+    col[i] = h1[i] + h2[i];
+    w0 += col[i] * col[i];
+  }
+  const double hn = *hnorm;
+  col[j + 1] = hn;
+  w0 = sqrt(w0 + hn * hn);
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  double c = 1.0, sv = 0.0;
+  if (den > 0.0) { c = col[j] / den; sv = col[j + 1] / den; }
+  cs[j] = c; sn[j] = sv;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sv * g[j];
+  g[j] = c * g[j];
+  out[0] = fabs(g[j + 1]) * inv_bnorm;
+  out[1] = (hn <= 1e-14 * w0) ? 1.0 : 0.0;
+  out[2] = hn;
+  out[3] = (isfinite(g[j + 1]) && isfinite(hn)) ? 0.0 : 1.0;
+}
+
+// H y = g, k x k upper triangular (column-major, leading dimension ldh); one thread
+__global__ void k_backsolve(int ldh, const int* __restrict__ kdev, const double* __restrict__ H,
+                            const double* __restrict__ g, double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = *kdev;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * ldh + i] * y[l];
+    y[i] = s / H[(size_t)i * ldh + i];
+  }
+}
+
+__global__ void k_set_first(double* __restrict__ g, int len, double beta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) g[i] = (i == 0) ? beta : 0.0;
+}
+
+inline int grid_n(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// near-nullspaces (host-built, node-major rows, row-major columns)
+std::vector<double> translations(int64_t nodes, int d) {
+  std::vector<double> B((size_t)nodes * d * d, 0.0);
+  for (int64_t i = 0; i < nodes; ++i)
+    for (int r = 0; r < d; ++r) B[((size_t)i * d + r) * d + r] = 1.0;
+  return B;
+}
+
+std::vector<double> rigid_modes(const double* X, int64_t nodes, int d) {
+  const int k = d == 2 ? 3 : 6;
+  std::vector<double> B((size_t)nodes * d * k, 0.0);
+  for (int64_t i = 0; i < nodes; ++i) {
+    auto at = [&](int r, int c) -> double& { return B[((size_t)i * d + r) * k + c]; };
+    for (int r = 0; r < d; ++r) at(r, r) = 1.0;
+    const double x = X[i * d], y = X[i * d + 1];
+    if (d == 2) {
+      at(0, 2) = -y; at(1, 2) = x;
+    } else {
+      const double z = X[i * d + 2];
+      at(0, 3) = -y; at(1, 3) = x;
+      at(1, 4) = -z; at(2, 4) = y;
+      at(2, 5) = -x; at(0, 5) = z;
+    }
+  }
+  return B;
+}
+
+void upload(DBuf<double>& dst, const std::vector<double>& src, cudaStream_t s) {
+  dst.alloc(src.size() > 0 ? src.size() : 1);
+  if (!src.empty())
+    FSI_CUDA(cudaMemcpyAsync(dst.p, src.data(), sizeof(double) * src.size(), cudaMemcpyHostToDevice, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ sub-solves
+// x = inverse of hierarchy h applied with `nc` V-cycles: x = V(b); x += V(b - A x) ...
+template <class T>
+void amg_solve(Context& C, int h, int nc, const T* b, T* x) {
+  Hierarchy& H = C.H[h];
+  amg_vcycle<T>(H, b, x, C.s);
+  if (nc <= 1) return;
+  PrecWork<T>& W = pwork<T>(C);
+  const Bsr& A = H.levels[0].A;
+  const int64_t nn = A.rows();
+  for (int c = 1; c < nc; ++c) {
+    spmv2_resid<T>(A, x, nullptr, nullptr, b, W.mv_res.p, C.s);
+    amg_vcycle<T>(H, W.mv_res.p, W.mv_cor.p, C.s);
+    axpby<T>(nn, T(1), W.mv_cor.p, T(1), x, C.s);
+  }
+}
+
+template <class T>
+void mesh_solve(Context& C, const T* r, T* x) { amg_solve<T>(C, 0, C.prm.vc_mesh, r, x); }
+
+// Alg. 3: solid sub-solve on (r_v, r_u) -> (x_v, x_u)
+template <class T>
+void solid_solve(Context& C, const T* r, T* x) {
+  PrecWork<T>& W = pwork<T>(C);
+  const int64_t nsv = C.off[2] - C.off[1];
+  const T* r_v = r;
+  const T* r_u = r + nsv;
+  T* x_v = x;
+  T* x_u = x + nsv;
+  cheb_apply<T>(C.mass, r_u, W.s3_y.p, C.s);                                  // y = A_uu^-1 r_u
+  spmv2_resid<T>(C.A_vu, W.s3_y.p, nullptr, nullptr, r_v, W.s3_t.p, C.s);     // t = r_v - A_vu y
+  amg_solve<T>(C, 1, C.prm.vc_solid, W.s3_t.p, x_v);                          // x_v = S_hat^-1 t
+  spmv2_resid<T>(C.A_uv, x_v, nullptr, nullptr, r_u, W.s3_t.p, C.s);          // t = r_u - A_uv x_v
+  cheb_apply<T>(C.mass, W.s3_t.p, x_u, C.s);                                  // x_u = A_uu^-1 t
+}
+
+// fluid sub-solve on (r_v, r_p) -> (x_v, x_p)
+template <class T>
+void fluid_solve(Context& C, const T* r, T* x) {
+  PrecWork<T>& W = pwork<T>(C);
+  const int64_t nfv = C.off[4] - C.off[3];
+  const T* r_v = r;
+  const T* r_p = r + nfv;
+  T* x_v = x;
+  T* x_p = x + nfv;
+  amg_solve<T>(C, 2, C.prm.vc_fluid, r_v, W.s3_y.p);                          // y = A_ff^-1 r_v
+  spmv2_resid<T>(C.B_pv, W.s3_y.p, nullptr, nullptr, r_p, W.s3_t.p, C.s);     // t = r_p - B_pv y
+  amg_solve<T>(C, 3, C.prm.vc_pressure, W.s3_t.p, x_p);                       // x_p = S_p^-1 t
+  spmv2_resid<T>(C.B_vp, x_p, nullptr, nullptr, r_v, W.s3_t.p, C.s);          // t = r_v - B_vp x_p
+  amg_solve<T>(C, 2, C.prm.vc_fluid, W.s3_t.p, x_v);                          // x_v = A_ff^-1 t
+}
+
+}  // namespace
+
+Context::~Context() {
+  if (iter_graph) cudaGraphExecDestroy(iter_graph);
+  if (pinned) cudaFreeHost(pinned);
+  if (pinned_j) cudaFreeHost(pinned_j);
+  if (own_stream && s) cudaStreamDestroy(s);
+}
+
+void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                   const double* solid_coords) {
+  auto t0 = clk::now();
+  const int d = C.dim;
+  const int64_t* o = C.off;
+  Csr A;
+  A.n = C.n;
+  A.nnz = rowptr[C.n];
+  A.rowptr.alloc(C.n + 1);
+  A.colind.alloc(A.nnz > 0 ? A.nnz : 1);
+  A.vals.alloc(A.nnz > 0 ? A.nnz : 1);
+  FSI_CUDA(cudaMemcpyAsync(A.rowptr.p, rowptr, sizeof(int64_t) * (C.n + 1), cudaMemcpyHostToDevice, C.s));
+  if (A.nnz) {
+    FSI_CUDA(cudaMemcpyAsync(A.colind.p, colind, sizeof(int) * A.nnz, cudaMemcpyHostToDevice, C.s));
+    FSI_CUDA(cudaMemcpyAsync(A.vals.p, vals, sizeof(double) * A.nnz, cudaMemcpyHostToDevice, C.s));
+  }
+  const int nV = (int)(o[4] / d);
+  const int nP = (int)(o[5] - o[4]);
+  const int nm = (int)((o[1] - o[0]) / d), nsv = (int)((o[2] - o[1]) / d), nsu = (int)((o[3] - o[2]) / d);
+  const int ns = nsv + nsu, nfv = (int)((o[4] - o[3]) / d), nms = (int)(o[3] / d);
+  auto& s = C.s;
+  // outer operator
+  extract_bsr(A, 0, nV, d, 0, nV, d, C.AVV, s);
+  extract_bsr(A, 0, nV, d, o[4], nP, 1, C.AVP, s);
+  extract_bsr(A, o[4], nP, 1, 0, nV, d, C.APV, s);
+  extract_bsr(A, o[4], nP, 1, o[4], nP, 1, C.APP, s);
+  // preconditioner blocks
+  extract_bsr(A, o[0], nm, d, o[0], nm, d, C.Mblk, s);
+  extract_bsr(A, o[0], nm, d, o[1], ns, d, C.C_ms, s);
+  extract_bsr(A, o[1], nsv, d, o[1], nsv, d, C.Avv, s);
+  extract_bsr(A, o[1], nsv, d, o[2], nsu, d, C.A_vu, s);
+  extract_bsr(A, o[2], nsu, d, o[1], nsv, d, C.A_uv, s);
+  extract_bsr(A, o[2], nsu, d, o[2], nsu, d, C.Auu, s);
+  extract_bsr(A, o[1], ns, d, o[3], nfv, d, C.C_sv_f, s);
+  extract_bsr(A, o[1], ns, d, o[4], nP, 1, C.C_sv_p, s);
+  extract_bsr(A, o[3], nfv, d, o[0], nms, d, C.C_fv_ms, s);
+  extract_bsr(A, o[4], nP, 1, o[0], nms, d, C.C_p_ms, s);
+  extract_bsr(A, o[3], nfv, d, o[3], nfv, d, C.Aff, s);
+  extract_bsr(A, o[3], nfv, d, o[4], nP, 1, C.B_vp, s);
+  extract_bsr(A, o[4], nP, 1, o[3], nfv, d, C.B_pv, s);
+  extract_bsr(A, o[4], nP, 1, o[4], nP, 1, C.Cpp, s);
+  if (solid_coords && !(C.prm.flags & NO_RIGID_MODES)) upload(C.solid_B, rigid_modes(solid_coords, nsv, d), s);
+  FSI_CUDA(cudaStreamSynchronize(s));
+  C.setup_s = secs(t0, clk::now());
+}
+
+void precond_build(Context& C, int precision) {
+  auto t0 = clk::now();
+  auto& s = C.s;
+  const int d = C.dim;
+  if (!C.built) {
+    // S_hat = A_vv + c A_vu  (Alg. 3)
+    Bsr Shat;
+    bsr_add(C.Avv, C.A_vu, C.prm.dt_theta, Shat, s);
+    // S_p = C_pp - B_pv diag(A_ff)^-1 B_vp
+    const int64_t nfv = C.Aff.rows();
+    DBuf<double> diag(nfv > 0 ? nfv : 1), dinv(nfv > 0 ? nfv : 1);
+    bsr_point_diagonal(C.Aff, diag.p, s);
+    invert_nonzero(nfv, diag.p, dinv.p, s);
+    Bsr Bs, BDB, Sp;
+    bsr_clone(C.B_vp, Bs, s);
+    bsr_scale_rows(Bs, dinv.p, s);
+    bsr_spgemm(C.B_pv, Bs, BDB, s);
+    bsr_add(C.Cpp, BDB, -1.0, Sp, s);
+    // hierarchies
+    DBuf<double> Bm, Bf, Bp;
+    upload(Bm, translations(C.Mblk.nbr, d), s);
+    upload(Bf, translations(C.Aff.nbr, d), s);
+    upload(Bp, std::vector<double>((size_t)Sp.nbr, 1.0), s);
+    const bool rigid = C.solid_B.p != nullptr;
+    DBuf<double> Bst;
+    if (!rigid) upload(Bst, translations(Shat.nbr, d), s);
+    const int ks = rigid ? (d == 2 ? 3 : 6) : d;
+    amg_setup(C.H[0], std::move(C.Mblk), Bm.p, d, C.prm.amg, s);
+    amg_setup(C.H[1], std::move(Shat), rigid ? C.solid_B.p : Bst.p, ks, C.prm.amg, s);
+    amg_setup(C.H[2], std::move(C.Aff), Bf.p, d, C.prm.amg, s);
+    amg_setup(C.H[3], std::move(Sp), Bp.p, 1, C.prm.amg, s);
+    cheb_setup(C.mass, std::move(C.Auu), C.prm.mass_degree, C.prm.mass_ratio, C.prm.amg.cheb_upper,
+               C.prm.amg.power_iters, s);
+    C.Avv = Bsr();
+    C.Cpp = Bsr();
+    alloc_pw(C.pw64, C.n);
+    C.built = true;
+  }
+  if (precision == 1 && !C.pw32.ready) {
+    for (auto& H : C.H) amg_make_fp32(H, s);
+    cheb_make_fp32(C.mass, s);
+    for (Bsr* B : {&C.C_ms, &C.A_vu, &C.A_uv, &C.C_sv_f, &C.C_sv_p, &C.C_fv_ms, &C.C_p_ms, &C.B_vp, &C.B_pv})
+      bsr_make_fp32(*B, s);
+    alloc_pw(C.pw32, C.n);
+  }
+  C.precision = precision;
+  if (C.iter_graph) { cudaGraphExecDestroy(C.iter_graph); C.iter_graph = nullptr; }
+  FSI_CUDA(cudaStreamSynchronize(s));
+  C.build_s = secs(t0, clk::now());
+}
+
+template <class T>
+void precond_apply(Context& C, const T* r, T* z) {
+  PrecWork<T>& W = pwork<T>(C);
+  const int64_t* o = C.off;
+  const T* r_m = r + o[0];
+  const T* r_s = r + o[1];
+  const T* r_f = r + o[3];
+  T* z_m = z + o[0];
+  T* z_s = z + o[1];
+  T* z_f = z + o[3];
+  const int64_t nfv = o[4] - o[3], ns = o[3] - o[1], nm = o[1] - o[0];
+  // 1-2
+  mesh_solve<T>(C, r_m, z_m);
+  solid_solve<T>(C, r_s, z_s);
+  // 3: t_f = r_f - C_fm x_m - C_fs x_s  (x_m, x_s contiguous), x_f = F^-1 t_f
+  spmv2_resid<T>(C.C_fv_ms, z, nullptr, nullptr, r_f, W.a2_t.p, C.s);
+  spmv2_resid<T>(C.C_p_ms, z, nullptr, nullptr, r_f + nfv, W.a2_t.p + nfv, C.s);
+  fluid_solve<T>(C, W.a2_t.p, z_f);
+  // 4: x_s -= S^-1 C_sf x_f
+  spmv2_axpby<T>(C.C_sv_f, z_f, &C.C_sv_p, z_f + nfv, T(1), T(0), W.a2_t.p, C.s);
+  solid_solve<T>(C, W.a2_t.p, W.a2_u.p);
+  axpby<T>(ns, T(-1), W.a2_u.p, T(1), z_s, C.s);
+  // 5: x_m -= M^-1 C_ms x_s
+  spmv_axpby<T>(C.C_ms, z_s, T(1), T(0), W.a2_t.p, C.s);
+  mesh_solve<T>(C, W.a2_t.p, W.a2_u.p);
+  axpby<T>(nm, T(-1), W.a2_u.p, T(1), z_m, C.s);
+}
+
+template <class T>
+void apply_block(Context& C, int which, const T* in, T* out) {
+  switch (which) {
+    case 0: amg_solve<T>(C, 0, C.prm.vc_mesh, in, out); break;
+    case 1: amg_solve<T>(C, 1, C.prm.vc_solid, in, out); break;
+    case 2: amg_solve<T>(C, 2, C.prm.vc_fluid, in, out); break;
+    case 3: amg_solve<T>(C, 3, C.prm.vc_pressure, in, out); break;
+    case 4: cheb_apply<T>(C.mass, in, out, C.s); break;
+    case 5: solid_solve<T>(C, in, out); break;
+    case 6: fluid_solve<T>(C, in, out); break;
+    case 7: precond_apply<T>(C, in, out); break;
+    default: throw Error(EINVAL_, "apply_block: unknown block");
+  }
+}
+
+void apply_operator(Context& C, const double* x, double* y) {
+  const int64_t nv = C.off[4];
+  spmv2_axpby<double>(C.AVV, x, &C.AVP, x + nv, 1.0, 0.0, y, C.s);
+  spmv2_axpby<double>(C.APV, x, &C.APP, x + nv, 1.0, 0.0, y + nv, C.s);
+}
+
+static void operator_resid(Context& C, const double* x, const double* b, double* r) {
+  const int64_t nv = C.off[4];
+  spmv2_resid<double>(C.AVV, x, &C.AVP, x + nv, b, r, C.s);
+  spmv2_resid<double>(C.APV, x, &C.APP, x + nv, b + nv, r + nv, C.s);
+}
+
+double operator_bytes(const Context& C) {
+  // values + indices + x (once) + y, both row classes
+  return C.AVV.spmv_bytes(8) + C.AVP.spmv_bytes(8) + C.APV.spmv_bytes(8) + C.APP.spmv_bytes(8) -
+         8.0 * (double)(C.AVV.rows() + C.APV.rows());   // y counted twice by the split
+}
+
+double precond_bytes(const Context& C, int vb) {
+  const SolverParams& p = C.prm;
+  // Alg. 2: two mesh solves, two solid solves (each with two mass solves), one
+  // fluid solve (two A_ff solves and one S_p solve), and the coupling products
+  double b = 0;
+  b += 2.0 * p.vc_mesh * C.H[0].vcycle_bytes(vb) + 2.0 * p.vc_solid * C.H[1].vcycle_bytes(vb) +
+       2.0 * p.vc_fluid * C.H[2].vcycle_bytes(vb) + 1.0 * p.vc_pressure * C.H[3].vcycle_bytes(vb);
+  b += 4.0 * C.mass.degree * C.mass.A.spmv_bytes(vb);
+  for (const Bsr* B : {&C.C_ms, &C.C_sv_f, &C.C_sv_p, &C.C_fv_ms, &C.C_p_ms}) b += B->spmv_bytes(vb);
+  b += 2.0 * (C.A_vu.spmv_bytes(vb) + C.A_uv.spmv_bytes(vb)) + C.B_vp.spmv_bytes(vb) + C.B_pv.spmv_bytes(vb);
+  return b;
+}
+
+// ------------------------------------------------------------------ FGMRES
+namespace {
+
+void ensure_krylov(Context& C) {
+  const int m = C.prm.restart;
+  if (C.m_alloc == m) return;
+  const int64_t n = C.n;
+  C.V.alloc((size_t)(m + 1) * n);
+  C.Z.alloc((size_t)m * n);
+  C.Hh.alloc((size_t)(m + 1) * m);
+  C.cs.alloc(m + 1); C.sn.alloc(m + 1); C.g.alloc(m + 2); C.y.alloc(m + 1);
+  C.h1.alloc(m + 2); C.h2.alloc(m + 2); C.scal.alloc(8);
+  C.partials.alloc((size_t)(m + 2) * kRedBlocks);
+  C.npart.alloc(kRedBlocks);
+  C.zfix.alloc(n); C.wfix.alloc(n); C.rvec.alloc(n);
+  C.jdev.alloc(1); C.kdev.alloc(1);
+  if (!C.pinned) {
+    FSI_CUDA(cudaHostAlloc(&C.pinned, 8 * sizeof(double), cudaHostAllocMapped));
+    FSI_CUDA(cudaHostGetDevicePointer(&C.pinned_dev, C.pinned, 0));
+    FSI_CUDA(cudaHostAlloc(&C.pinned_j, 4 * sizeof(int), cudaHostAllocDefault));
+  }
+  C.m_alloc = m;
+  if (C.iter_graph) { cudaGraphExecDestroy(C.iter_graph); C.iter_graph = nullptr; }
+}
+
+// One FGMRES iteration for the index held in C.jdev: Z_j = P^-1 V_j,
+// w = A Z_j, CGS2 against V_0..V_j, Givens update, V_{j+1} = w / ||w||.
+template <class T>
+void iteration_body(Context& C) {
+  const int64_t n = C.n;
+  const int m = C.prm.restart;
+  PrecWork<T>& W = pwork<T>(C);
+  k_col_in<double, T><<<grid_n(n), 256, 0, C.s>>>(n, C.V.p, n, C.jdev.p, 0, W.in.p);
+  FSI_CHECK_LAUNCH();
+  precond_apply<T>(C, W.in.p, W.out.p);
+  k_col_out<T><<<grid_n(n), 256, 0, C.s>>>(n, W.out.p, C.zfix.p, C.Z.p, n, C.jdev.p);
+  FSI_CHECK_LAUNCH();
+  apply_operator(C, C.zfix.p, C.wfix.p);
+  mdot(n, C.V.p, n, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h1.p, m + 1, C.s);
+  maxpy(n, C.V.p, n, C.jdev.p, 1, C.h1.p, 1.0, C.wfix.p, nullptr, C.s);
+  mdot(n, C.V.p, n, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h2.p, m + 1, C.s);
+  maxpy(n, C.V.p, n, C.jdev.p, 1, C.h2.p, 1.0, C.wfix.p, C.npart.p, C.s);
+  finish_norm(C.npart.p, C.scal.p, C.s);
+  k_givens<<<1, 32, 0, C.s>>>(m + 1, C.jdev.p, C.h1.p, C.h2.p, C.scal.p, C.Hh.p, C.cs.p, C.sn.p, C.g.p,
+                              C.scal.p + 5, C.pinned_dev);
+  FSI_CHECK_LAUNCH();
+  k_scale_col<<<grid_n(n), 256, 0, C.s>>>(n, C.wfix.p, C.scal.p, C.V.p, n, C.jdev.p);
+  FSI_CHECK_LAUNCH();
+}
+
+void run_iteration(Context& C) {
+  const bool graphs = (C.prm.flags & USE_GRAPHS) != 0;
+  if (!graphs) {
+    if (C.precision == 1) iteration_body<float>(C); else iteration_body<double>(C);
+    return;
+  }
+  if (!C.iter_graph || C.iter_graph_prec != C.precision) {
+    if (C.iter_graph) { cudaGraphExecDestroy(C.iter_graph); C.iter_graph = nullptr; }
+    cudaGraph_t g;
+    FSI_CUDA(cudaStreamBeginCapture(C.s, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = g_kernel_launches;
+    try {
+      if (C.precision == 1) iteration_body<float>(C); else iteration_body<double>(C);
+    } catch (...) {
+      cudaStreamEndCapture(C.s, &g);
+      throw;
+    }
+    C.graph_kernels = g_kernel_launches - before;
+    g_kernel_launches = before;       // captured, not executed
+    FSI_CUDA(cudaStreamEndCapture(C.s, &g));
+    FSI_CUDA(cudaGraphInstantiate(&C.iter_graph, g, 0));
+    cudaGraphDestroy(g);
+    C.iter_graph_prec = C.precision;
+  }
+  FSI_CUDA(cudaGraphLaunch(C.iter_graph, C.s));
+  g_kernel_launches += C.graph_kernels;
+}
+
+}  // namespace
+
+int fgmres_solve(Context& C, const double* b, double* x, double tol) {
+  auto t0 = clk::now();
+  const int64_t launches0 = g_kernel_launches;
+  require(C.built, "fsi_solve before fsi_precond_build");
+  ensure_krylov(C);
+  const int64_t n = C.n;
+  const int m = C.prm.restart;
+  C.hist.clear();
+  const double bnorm = std::sqrt(dot_host<double>(n, b, b, C.partials.p, C.scal.p + 4, C.s));
+  C.last_iters = 0; C.last_cycles = 0;
+  if (!std::isfinite(bnorm)) {
+    C.last_status = ENONFINITE_;
+    C.solve_s = secs(t0, clk::now());
+    throw Error(ENONFINITE_, "right-hand side is not finite");
+  }
+  if (!(C.prm.flags & X0_GIVEN)) FSI_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, C.s));
+  if (bnorm == 0.0) {
+    FSI_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, C.s));
+    FSI_CUDA(cudaStreamSynchronize(C.s));
+    C.last_true_relres = 0.0; C.last_status = OK;
+    C.solve_s = secs(t0, clk::now());
+    return OK;
+  }
+  C.pinned[4] = 1.0 / bnorm;
+  FSI_CUDA(cudaMemcpyAsync(C.scal.p + 5, C.pinned + 4, sizeof(double), cudaMemcpyHostToDevice, C.s));
+  int total = 0, status = ENOTCONV_;
+  double relres = 0.0;
+  bool breakdown = false, nonfinite = false;
+  while (true) {
+    operator_resid(C, x, b, C.rvec.p);
+    const double beta = std::sqrt(dot_host<double>(n, C.rvec.p, C.rvec.p, C.partials.p, C.scal.p + 4, C.s));
+    relres = beta / bnorm;
+    if (!std::isfinite(relres)) { nonfinite = true; break; }
+    if (relres <= tol) { status = OK; break; }
+    if (total >= C.prm.maxit || breakdown) break;
+    axpby<double>(n, 1.0 / beta, C.rvec.p, 0.0, C.V.p, C.s);
+    k_set_first<<<div_up(m + 2, 128), 128, 0, C.s>>>(C.g.p, m + 2, beta);
+    FSI_CHECK_LAUNCH();
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      C.pinned_j[0] = j;
+      FSI_CUDA(cudaMemcpyAsync(C.jdev.p, C.pinned_j, sizeof(int), cudaMemcpyHostToDevice, C.s));
+      run_iteration(C);
+      FSI_CUDA(cudaStreamSynchronize(C.s));
+      volatile double* pv = C.pinned;
+      const double est = pv[0];
+      const bool bd = pv[1] != 0.0;
+      nonfinite = pv[3] != 0.0;
+      C.hist.push_back(est);
+      ++total;
+      k = j + 1;
+      if (nonfinite) break;
+      if (bd) { breakdown = true; break; }
+      if (est <= tol || total >= C.prm.maxit) break;
+    }
+    if (nonfinite) break;
+    C.pinned_j[1] = k;
+    FSI_CUDA(cudaMemcpyAsync(C.kdev.p, C.pinned_j + 1, sizeof(int), cudaMemcpyHostToDevice, C.s));
+    k_backsolve<<<1, 32, 0, C.s>>>(m + 1, C.kdev.p, C.Hh.p, C.g.p, C.y.p);
+    FSI_CHECK_LAUNCH();
+    maxpy(n, C.Z.p, n, C.kdev.p, 0, C.y.p, -1.0, x, nullptr, C.s);
+    ++C.last_cycles;
+  }
+  FSI_CUDA(cudaStreamSynchronize(C.s));
+  C.last_iters = total;
+  C.last_true_relres = relres;
+  if (nonfinite) status = ENONFINITE_;
+  else if (status != OK && breakdown) status = EBREAKDOWN_;
+  C.last_status = status;
+  C.solve_s = secs(t0, clk::now());
+  C.last_launches = g_kernel_launches - launches0;
+  return status;
+}
+
+template void precond_apply<double>(Context&, const double*, double*);
+template void precond_apply<float>(Context&, const float*, float*);
+template void apply_block<double>(Context&, int, const double*, double*);
+template void apply_block<float>(Context&, int, const float*, float*);
+
+}  // namespace fsi

@@ -1,0 +1,89 @@
+// Solver context: the monolithic operator split into class blocks, the block-LDU
+// preconditioner of Alg. 2 (with the Alg. 3 solid and pressure-Schur fluid
+// sub-solves) and the right-preconditioned FGMRES outer iteration.
+#pragma once
+#include "amg.cuh"
+#include "sparse_util.cuh"
+
+#include <string>
+#include <vector>
+
+namespace fsi {
+
+struct SolverParams {
+  int restart = 100;
+  int maxit = 1000;
+  int flags = 0;
+  double dt_theta = 0.01;
+  AmgParams amg;
+  int vc_mesh = 1, vc_solid = 2, vc_fluid = 1, vc_pressure = 1;
+  int mass_degree = 12;
+  double mass_ratio = 8.0;
+};
+
+enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4 };
+
+template <class T>
+struct PrecWork {
+  DBuf<T> in, out;            // fixed input/output of P^-1 (length n)
+  DBuf<T> a2_t, a2_u;         // Alg. 2 temporaries
+  DBuf<T> s3_y, s3_t;         // Alg. 3 / fluid Schur temporaries
+  DBuf<T> mv_res, mv_cor;     // repeated V-cycles
+  bool ready = false;
+};
+
+struct Context {
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  int dim = 2;
+  int64_t n = 0;
+  int64_t off[6] = {0, 0, 0, 0, 0, 0};
+  SolverParams prm;
+  std::string err;
+  // outer operator: vector rows (first off[4] DOFs, d x d blocks) and p rows
+  Bsr AVV, AVP, APV, APP;
+  // preconditioner blocks
+  Bsr C_ms;                   // m rows x (s_v, s_u) cols
+  Bsr A_vu, A_uv;             // solid couplings
+  Bsr C_sv_f, C_sv_p;         // s rows x f_v cols, s rows x p cols
+  Bsr C_fv_ms, C_p_ms;        // f_v rows x (m, s) cols, p rows x (m, s) cols
+  Bsr B_vp, B_pv;             // fluid velocity-pressure couplings
+  Bsr Mblk, Avv, Auu, Aff, Cpp;   // diagonal blocks, consumed by precond_build
+  Hierarchy H[4];             // M, S_hat, A_ff, S_p
+  ChebSolver mass;            // A_uu (solid mass)
+  bool built = false;
+  int precision = 0;          // 0 FP64, 1 FP32 AMG
+  PrecWork<double> pw64;
+  PrecWork<float> pw32;
+  DBuf<double> solid_B;       // near-nullspace of S_hat (rigid-body modes)
+  // FGMRES storage
+  int m_alloc = 0;
+  DBuf<double> V, Z, Hh, cs, sn, g, y, h1, h2, scal, partials, npart, zfix, wfix, rvec;
+  DBuf<int> jdev, kdev;
+  double* pinned = nullptr;   // host-mapped: [0] |g_{j+1}|/|b|, [1] breakdown flag, [2] h_{j+1,j}
+  double* pinned_dev = nullptr;
+  int* pinned_j = nullptr;    // pinned host staging for the iteration index
+  cudaGraphExec_t iter_graph = nullptr;
+  int iter_graph_prec = -1;
+  int64_t graph_kernels = 0;  // kernel launches inside one replay of iter_graph
+  int64_t last_launches = 0;  // kernels launched by the last solve
+  // stats
+  std::vector<double> hist;
+  double setup_s = 0, build_s = 0, solve_s = 0;
+  int last_iters = 0, last_cycles = 0, last_status = 0;
+  double last_true_relres = 0;
+  ~Context();
+};
+
+void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                   const double* solid_coords);
+void precond_build(Context& C, int precision);
+template <class T> void precond_apply(Context& C, const T* r, T* z);
+void apply_operator(Context& C, const double* x, double* y);
+int fgmres_solve(Context& C, const double* b, double* x, double tol);
+// sub-solve hooks (which: 0..3 hierarchies, 4 mass, 5 solid Alg. 3, 6 fluid, 7 Alg. 2)
+template <class T> void apply_block(Context& C, int which, const T* in, T* out);
+double precond_bytes(const Context& C, int vb);
+double operator_bytes(const Context& C);
+
+}  // namespace fsi

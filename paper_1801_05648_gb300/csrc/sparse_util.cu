@@ -1,0 +1,609 @@
+#include "sparse_util.cuh"
+
+#include <climits>
+
+namespace fsi {
+
+namespace {
+
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    long long t = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of a 1024-element tile; writes block totals.
+template <class Tin>
+__global__ void __launch_bounds__(kScanBlock) k_scan_tile(const Tin* __restrict__ in, long long* __restrict__ out,
+                                                          int64_t n, long long* __restrict__ bsum) {
+  __shared__ long long wsum[32];
+  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long v = i < n ? (long long)in[i] : 0;
+  long long inc = warp_incl_scan(v, lane);
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    long long t = wsum[lane];
+    t = warp_incl_scan(t, lane);
+    wsum[lane] = t;
+  }
+  __syncthreads();
+  long long base = w ? wsum[w - 1] : 0;
+  if (i < n) out[i] = base + inc - v;
+  if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = base + inc;
+}
+
+__global__ void k_scan_add(long long* __restrict__ out, int64_t n, const long long* __restrict__ boff) {
+  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  if (i < n) out[i] += boff[blockIdx.x];
+}
+
+// exclusive scan of n long longs/ints into out (n entries); returns total on the host
+template <class Tin>
+long long scan_ll(const Tin* in, long long* out, int64_t n, cudaStream_t s) {
+  if (n == 0) return 0;
+  const int nb = div_up(n, kScanBlock);
+  DBuf<long long> bsum(nb), boff(nb);
+  k_scan_tile<Tin><<<nb, kScanBlock, 0, s>>>(in, out, n, bsum.p);
+  FSI_CHECK_LAUNCH();
+  long long total;
+  if (nb == 1) {
+    FSI_CUDA(cudaMemcpyAsync(&total, bsum.p, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    FSI_CUDA(cudaStreamSynchronize(s));
+    return total;
+  }
+  total = scan_ll<long long>(bsum.p, boff.p, nb, s);
+  k_scan_add<<<nb, kScanBlock, 0, s>>>(out, n, boff.p);
+  FSI_CHECK_LAUNCH();
+  return total;
+}
+
+__global__ void k_ll_to_int(const long long* __restrict__ in, int* __restrict__ out, int64_t n, long long total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int)in[i];
+  if (i == n) out[n] = (int)total;
+}
+
+__device__ __forceinline__ int lower_bound_i(const int* a, int lo, int hi, int key) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t lower_bound_l(const int* a, int64_t lo, int64_t hi, int key) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// --------------------------------------------------------------- extraction
+// One thread per block row: merge the br sorted scalar rows restricted to the
+// column window into sorted block columns.
+template <bool FILL>
+__global__ void k_extract(const int64_t* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ va,
+                          int64_t r0, int nbr, int br, int64_t c0, int64_t c1, int bc, int* __restrict__ cnt,
+                          const int* __restrict__ orp, int* __restrict__ oci, double* __restrict__ ova) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  int64_t ptr[6], end[6];
+  for (int q = 0; q < br; ++q) {
+    const int64_t r = r0 + (int64_t)row * br + q;
+    ptr[q] = lower_bound_l(ci, rp[r], rp[r + 1], (int)c0);
+    end[q] = lower_bound_l(ci, ptr[q], rp[r + 1], (int)c1);
+  }
+  int count = 0;
+  int64_t outpos = FILL ? orp[row] : 0;
+  while (true) {
+    int best = INT_MAX;
+    for (int q = 0; q < br; ++q)
+      if (ptr[q] < end[q]) {
+        int b = (int)((ci[ptr[q]] - c0) / bc);
+        if (b < best) best = b;
+      }
+    if (best == INT_MAX) break;
+    if (FILL) {
+      double* blk = ova + outpos * (int64_t)(br * bc);
+      for (int t = 0; t < br * bc; ++t) blk[t] = 0.0;
+      oci[outpos] = best;
+      for (int q = 0; q < br; ++q)
+        while (ptr[q] < end[q] && (int)((ci[ptr[q]] - c0) / bc) == best) {
+          blk[q * bc + (int)((ci[ptr[q]] - c0) % bc)] = va[ptr[q]];
+          ++ptr[q];
+        }
+      ++outpos;
+    } else {
+      for (int q = 0; q < br; ++q)
+        while (ptr[q] < end[q] && (int)((ci[ptr[q]] - c0) / bc) == best) ++ptr[q];
+    }
+    ++count;
+  }
+  if (!FILL) cnt[row] = count;
+}
+
+// --------------------------------------------------------------- add
+template <bool FILL>
+__global__ void k_add(int nbr, int bsz, const int* __restrict__ arp, const int* __restrict__ aci,
+                      const double* __restrict__ ava, const int* __restrict__ brp, const int* __restrict__ bci,
+                      const double* __restrict__ bva, double alpha, int* __restrict__ cnt, const int* __restrict__ crp,
+                      int* __restrict__ cci, double* __restrict__ cva) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  int ia = arp[row], ea = arp[row + 1], ib = brp[row], eb = brp[row + 1];
+  int count = 0;
+  int pos = FILL ? crp[row] : 0;
+  while (ia < ea || ib < eb) {
+    int ca = ia < ea ? aci[ia] : INT_MAX;
+    int cb = ib < eb ? bci[ib] : INT_MAX;
+    int c = ca < cb ? ca : cb;
+    if (FILL) {
+      double* o = cva + (int64_t)pos * bsz;
+      for (int t = 0; t < bsz; ++t) o[t] = 0.0;
+      if (ca == c) for (int t = 0; t < bsz; ++t) o[t] += ava[(int64_t)ia * bsz + t];
+      if (cb == c) for (int t = 0; t < bsz; ++t) o[t] += alpha * bva[(int64_t)ib * bsz + t];
+      cci[pos] = c;
+      ++pos;
+    }
+    if (ca == c) ++ia;
+    if (cb == c) ++ib;
+    ++count;
+  }
+  if (!FILL) cnt[row] = count;
+}
+
+// --------------------------------------------------------------- transpose
+__global__ void k_count_cols(int64_t nnzb, const int* __restrict__ ci, int* __restrict__ cnt) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnzb) atomicAdd(cnt + ci[k], 1);
+}
+__global__ void k_row_of_block(int nbr, const int* __restrict__ rp, int* __restrict__ rowof) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  for (int k = rp[row]; k < rp[row + 1]; ++k) rowof[k] = row;
+}
+__global__ void k_scatter_t(int64_t nnzb, const int* __restrict__ ci, const int* __restrict__ rowof,
+                            const int* __restrict__ trp, int* __restrict__ cursor, int* __restrict__ trow,
+                            int* __restrict__ tsrc) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnzb) return;
+  const int c = ci[k];
+  const int pos = trp[c] + atomicAdd(cursor + c, 1);
+  trow[pos] = rowof[k];
+  tsrc[pos] = (int)k;
+}
+// insertion sort of each segment by key (with a payload)
+__global__ void k_sort_segments(int nseg, const int* __restrict__ off, int* __restrict__ key, int* __restrict__ pay) {
+  const int sgm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sgm >= nseg) return;
+  const int lo = off[sgm], hi = off[sgm + 1];
+  for (int i = lo + 1; i < hi; ++i) {
+    int k = key[i], p = pay ? pay[i] : 0;
+    int j = i - 1;
+    while (j >= lo && key[j] > k) {
+      key[j + 1] = key[j];
+      if (pay) pay[j + 1] = pay[j];
+      --j;
+    }
+    key[j + 1] = k;
+    if (pay) pay[j + 1] = p;
+  }
+}
+__global__ void k_gather_t(int64_t nnzb, int br, int bc, const int* __restrict__ tsrc, const double* __restrict__ va,
+                           double* __restrict__ tva) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnzb) return;
+  const double* s = va + (int64_t)tsrc[k] * br * bc;
+  double* d = tva + k * br * bc;
+  // source block br x bc row-major -> destination bc x br row-major
+  for (int i = 0; i < br; ++i)
+    for (int j = 0; j < bc; ++j) d[j * br + i] = s[i * bc + j];
+}
+
+// --------------------------------------------------------------- SpGEMM
+constexpr int kHashSize = 1024;      // per warp, shared memory (2 x 4 x 4 KB per block)
+constexpr int kWarpsPerBlock = 4;
+
+__device__ __forceinline__ unsigned hash_slot(int key) { return ((unsigned)key * 2654435761u) & (kHashSize - 1); }
+
+// returns 1 when key was newly inserted, 0 when present, -1 when the table is
+// full (every slot probed once: the loop always ends)
+__device__ __forceinline__ int hash_insert(int* table, int key) {
+  unsigned h = hash_slot(key);
+  for (int probe = 0; probe < kHashSize; ++probe) {
+    int prev = atomicCAS(table + h, -1, key);
+    if (prev == -1) return 1;
+    if (prev == key) return 0;
+    h = (h + 1) & (kHashSize - 1);
+  }
+  return -1;
+}
+
+// Symbolic pass, one warp per row of A.  FILL = false: count unique block
+// columns (flag overflow).  FILL = true: write them sorted.
+template <bool FILL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_spgemm_sym(int nbr, const int* __restrict__ arp,
+                                                                    const int* __restrict__ aci,
+                                                                    const int* __restrict__ brp,
+                                                                    const int* __restrict__ bci, int* __restrict__ cnt,
+                                                                    const int* __restrict__ crp, int* __restrict__ cci,
+                                                                    int* __restrict__ overflow) {
+  __shared__ int table[kWarpsPerBlock][kHashSize];
+  __shared__ int list[kWarpsPerBlock][kHashSize];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kWarpsPerBlock + w;
+  if (row >= nbr) return;   // whole warp exits together
+  int* tb = table[w];
+  for (int t = lane; t < kHashSize; t += 32) tb[t] = -1;
+  __syncwarp();
+  int inserted = 0, full = 0;
+  for (int k = arp[row]; k < arp[row + 1]; ++k) {
+    const int kk = aci[k];
+    for (int q = brp[kk] + lane; q < brp[kk + 1]; q += 32) {
+      const int r = hash_insert(tb, bci[q]);
+      if (r < 0) full = 1; else inserted += r;
+    }
+    __syncwarp();
+    // bail out on overflow (table over 3/4 full or a failed insert)
+    int tot = inserted;
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+    const int anyfull = __any_sync(0xffffffffu, full);
+    if (tot > kHashSize * 3 / 4 || anyfull) {
+      if (lane == 0) atomicExch(overflow, 1);
+      return;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) inserted += __shfl_xor_sync(0xffffffffu, inserted, off);
+  if (!FILL) {
+    if (lane == 0) cnt[row] = inserted;
+    return;
+  }
+  // compact the table
+  int* ls = list[w];
+  int base = 0;
+  for (int t0 = 0; t0 < kHashSize; t0 += 32) {
+    int v = tb[t0 + lane];
+    unsigned m = __ballot_sync(0xffffffffu, v != -1);
+    if (v != -1) ls[base + __popc(m & ((1u << lane) - 1))] = v;
+    base += __popc(m);
+  }
+  __syncwarp();
+  const int out0 = crp[row];
+  for (int e = lane; e < base; e += 32) {
+    const int v = ls[e];
+    int rank = 0;
+    for (int f = 0; f < base; ++f) rank += ls[f] < v;
+    cci[out0 + rank] = v;
+  }
+}
+
+template <int BR, int BK, int BC>
+__global__ void __launch_bounds__(128) k_spgemm_num(int nbr, const int* __restrict__ arp, const int* __restrict__ aci,
+                                                    const double* __restrict__ ava, const int* __restrict__ brp,
+                                                    const int* __restrict__ bci, const double* __restrict__ bva,
+                                                    const int* __restrict__ crp, const int* __restrict__ cci,
+                                                    double* __restrict__ cva) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 4 + w;
+  if (row >= nbr) return;
+  for (int e = crp[row] + lane; e < crp[row + 1]; e += 32) {
+    const int J = cci[e];
+    double acc[BR * BC];
+#pragma unroll
+    for (int t = 0; t < BR * BC; ++t) acc[t] = 0.0;
+    for (int k = arp[row]; k < arp[row + 1]; ++k) {
+      const int kk = aci[k];
+      const int pos = lower_bound_i(bci, brp[kk], brp[kk + 1], J);
+      if (pos < brp[kk + 1] && bci[pos] == J) {
+        const double* a = ava + (int64_t)k * BR * BK;
+        const double* b = bva + (int64_t)pos * BK * BC;
+#pragma unroll
+        for (int i = 0; i < BR; ++i)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) {
+            double s = acc[i * BC + j];
+#pragma unroll
+            for (int q = 0; q < BK; ++q) s += a[i * BK + q] * b[q * BC + j];
+            acc[i * BC + j] = s;
+          }
+      }
+    }
+    double* c = cva + (int64_t)e * BR * BC;
+#pragma unroll
+    for (int t = 0; t < BR * BC; ++t) c[t] = acc[t];
+  }
+}
+
+// --------------------------------------------------------------- misc
+__global__ void k_scale_rows(int nbr, int br, int bc, const int* __restrict__ rp, double* __restrict__ va,
+                             const double* __restrict__ w) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  for (int k = rp[row]; k < rp[row + 1]; ++k)
+    for (int i = 0; i < br; ++i)
+      for (int j = 0; j < bc; ++j) va[((int64_t)k * br + i) * bc + j] *= w[(int64_t)row * br + i];
+}
+__global__ void k_point_diag(int nbr, int b, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const double* __restrict__ va, double* __restrict__ diag) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  const int pos = lower_bound_i(ci, rp[row], rp[row + 1], row);
+  const bool has = pos < rp[row + 1] && ci[pos] == row;
+  for (int i = 0; i < b; ++i) diag[(int64_t)row * b + i] = has ? va[((int64_t)pos * b + i) * b + i] : 0.0;
+}
+__global__ void k_invert_nonzero(int64_t n, const double* __restrict__ d, double* __restrict__ o) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = d[i] != 0.0 ? 1.0 / d[i] : 0.0;
+}
+__global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_to_dense(int nbr, int br, int bc, int ncols, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ va, double* __restrict__ D) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  for (int k = rp[row]; k < rp[row + 1]; ++k)
+    for (int i = 0; i < br; ++i)
+      for (int j = 0; j < bc; ++j)
+        D[((int64_t)row * br + i) * ncols + (int64_t)ci[k] * bc + j] = va[((int64_t)k * br + i) * bc + j];
+}
+
+// Gauss-Jordan on [M | I], one block of 1024 threads; M is destroyed.
+__global__ void __launch_bounds__(1024) k_gauss_jordan(int n, double* __restrict__ M, double* __restrict__ X,
+                                                       int* __restrict__ fail) {
+  __shared__ double bval[32];
+  __shared__ int bidx[32];
+  __shared__ int piv_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // zero rows -> identity rows; X = I
+  for (int r = tid; r < n; r += nt) {
+    bool zero = true;
+    for (int c = 0; c < n; ++c) if (M[(int64_t)r * n + c] != 0.0) { zero = false; break; }
+    if (zero) M[(int64_t)r * n + r] = 1.0;
+  }
+  for (int64_t t = tid; t < (int64_t)n * n; t += nt) X[t] = (t / n == t % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int p = 0; p < n; ++p) {
+    // pivot search over rows p..n-1 of column p
+    double best = -1.0; int bi = p;
+    for (int r = p + tid; r < n; r += nt) {
+      double v = fabs(M[(int64_t)r * n + p]);
+      if (v > best) { best = v; bi = r; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, best, off);
+      int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { bval[tid >> 5] = best; bidx[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = -1.0; int i = p;
+      for (int w = 0; w < (nt >> 5); ++w)
+        if (bval[w] > b || (bval[w] == b && bidx[w] < i)) { b = bval[w]; i = bidx[w]; }
+      piv_s = i;
+      if (!(b > 0.0)) *fail = 1;
+    }
+    __syncthreads();
+    const int pr = piv_s;
+    if (pr != p)
+      for (int c = tid; c < n; c += nt) {
+        double t = M[(int64_t)p * n + c]; M[(int64_t)p * n + c] = M[(int64_t)pr * n + c]; M[(int64_t)pr * n + c] = t;
+        t = X[(int64_t)p * n + c]; X[(int64_t)p * n + c] = X[(int64_t)pr * n + c]; X[(int64_t)pr * n + c] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / M[(int64_t)p * n + p];
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) { M[(int64_t)p * n + c] *= inv; X[(int64_t)p * n + c] *= inv; }
+    __syncthreads();
+    for (int64_t t = tid; t < (int64_t)n * n; t += nt) {
+      const int r = (int)(t / n), c = (int)(t % n);
+      if (r == p) continue;
+      const double f = M[(int64_t)r * n + p];
+      if (f == 0.0) continue;
+      if (c != p) M[(int64_t)r * n + c] -= f * M[(int64_t)p * n + c];
+      X[(int64_t)r * n + c] -= f * X[(int64_t)p * n + c];
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += nt) if (r != p) M[(int64_t)r * n + p] = 0.0;
+    __syncthreads();
+  }
+}
+
+template <class F>
+void spgemm_dispatch(int br, int bk, int bc, F&& f) {
+#define FSI_G(a, b, c) if (br == a && bk == b && bc == c) { f.template operator()<a, b, c>(); return; }
+  // A * P_tent / A * P (b x b times b x k)
+  FSI_G(1, 1, 1) FSI_G(2, 2, 2) FSI_G(3, 3, 3) FSI_G(2, 2, 3) FSI_G(3, 3, 6) FSI_G(6, 6, 6)
+  // R * (A P)  (k x b times b x k)
+  FSI_G(3, 2, 3) FSI_G(6, 3, 6)
+  // pressure Schur: (1 x d) * (d x 1)
+  FSI_G(1, 2, 1) FSI_G(1, 3, 1)
+#undef FSI_G
+  throw Error(EINVAL_, "unsupported SpGEMM block shape " + std::to_string(br) + "x" + std::to_string(bk) + "x" +
+                           std::to_string(bc));
+}
+
+void finalize_rowptr(const int* cnt, Bsr& C, cudaStream_t s) {
+  DBuf<long long> tmp(C.nbr + 1);
+  long long total = scan_ll<int>(cnt, tmp.p, C.nbr, s);
+  require(total < INT_MAX, "sparse matrix too large for 32-bit block indices");
+  C.rowptr.alloc(C.nbr + 1);
+  k_ll_to_int<<<div_up(C.nbr + 1, 256), 256, 0, s>>>(tmp.p, C.rowptr.p, C.nbr, total);
+  FSI_CHECK_LAUNCH();
+  C.nnzb = total;
+  C.colind.alloc(total > 0 ? total : 1);
+  C.v64.alloc(total > 0 ? total * C.br * C.bc : 1);
+}
+
+}  // namespace
+
+int64_t exclusive_scan(const int* in, int* out, int64_t n, cudaStream_t s) {
+  DBuf<long long> tmp(n + 1);
+  long long total = scan_ll<int>(in, tmp.p, n, s);
+  require(total < INT_MAX, "scan overflow");
+  k_ll_to_int<<<div_up(n + 1, 256), 256, 0, s>>>(tmp.p, out, n, total);
+  FSI_CHECK_LAUNCH();
+  return total;
+}
+
+void extract_bsr(const Csr& A, int64_t r0, int nbr, int br, int64_t c0, int nbc, int bc, Bsr& out, cudaStream_t s) {
+  require(br <= 6, "extract_bsr: block rows > 6");
+  out = Bsr();
+  out.nbr = nbr; out.nbc = nbc; out.br = br; out.bc = bc;
+  DBuf<int> cnt(nbr > 0 ? nbr : 1);
+  const int64_t c1 = c0 + (int64_t)nbc * bc;
+  if (nbr > 0) {
+    k_extract<false><<<div_up(nbr, 128), 128, 0, s>>>(A.rowptr.p, A.colind.p, A.vals.p, r0, nbr, br, c0, c1, bc,
+                                                    cnt.p, nullptr, nullptr, nullptr);
+    FSI_CHECK_LAUNCH();
+  }
+  finalize_rowptr(cnt.p, out, s);
+  if (nbr > 0) {
+    k_extract<true><<<div_up(nbr, 128), 128, 0, s>>>(A.rowptr.p, A.colind.p, A.vals.p, r0, nbr, br, c0, c1, bc,
+                                                   nullptr, out.rowptr.p, out.colind.p, out.v64.p);
+    FSI_CHECK_LAUNCH();
+  }
+  out.tpr = choose_tpr(out.nnzb, nbr);
+}
+
+void bsr_add(const Bsr& A, const Bsr& B, double alpha, Bsr& C, cudaStream_t s) {
+  require(A.nbr == B.nbr && A.nbc == B.nbc && A.br == B.br && A.bc == B.bc, "bsr_add: shape mismatch");
+  C = Bsr();
+  C.nbr = A.nbr; C.nbc = A.nbc; C.br = A.br; C.bc = A.bc;
+  DBuf<int> cnt(A.nbr > 0 ? A.nbr : 1);
+  const int bsz = A.br * A.bc;
+  if (A.nbr > 0) {
+    k_add<false><<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, bsz, A.rowptr.p, A.colind.p, A.v64.p, B.rowptr.p,
+                                                   B.colind.p, B.v64.p, alpha, cnt.p, nullptr, nullptr, nullptr);
+    FSI_CHECK_LAUNCH();
+  }
+  finalize_rowptr(cnt.p, C, s);
+  if (A.nbr > 0) {
+    k_add<true><<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, bsz, A.rowptr.p, A.colind.p, A.v64.p, B.rowptr.p,
+                                                  B.colind.p, B.v64.p, alpha, nullptr, C.rowptr.p, C.colind.p,
+                                                  C.v64.p);
+    FSI_CHECK_LAUNCH();
+  }
+  C.tpr = choose_tpr(C.nnzb, C.nbr);
+}
+
+void bsr_transpose(const Bsr& A, Bsr& C, cudaStream_t s) {
+  C = Bsr();
+  C.nbr = A.nbc; C.nbc = A.nbr; C.br = A.bc; C.bc = A.br;
+  DBuf<int> cnt(C.nbr + 1), cursor(C.nbr + 1);
+  FSI_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (C.nbr + 1), s));
+  FSI_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int) * (C.nbr + 1), s));
+  if (A.nnzb > 0) {
+    k_count_cols<<<div_up(A.nnzb, 256), 256, 0, s>>>(A.nnzb, A.colind.p, cnt.p);
+    FSI_CHECK_LAUNCH();
+  }
+  finalize_rowptr(cnt.p, C, s);
+  if (A.nnzb == 0) { C.tpr = 4; return; }
+  DBuf<int> rowof(A.nnzb), tsrc(A.nnzb);
+  k_row_of_block<<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, A.rowptr.p, rowof.p);
+  FSI_CHECK_LAUNCH();
+  k_scatter_t<<<div_up(A.nnzb, 256), 256, 0, s>>>(A.nnzb, A.colind.p, rowof.p, C.rowptr.p, cursor.p, C.colind.p,
+                                                 tsrc.p);
+  FSI_CHECK_LAUNCH();
+  k_sort_segments<<<div_up(C.nbr, 128), 128, 0, s>>>(C.nbr, C.rowptr.p, C.colind.p, tsrc.p);
+  FSI_CHECK_LAUNCH();
+  k_gather_t<<<div_up(A.nnzb, 256), 256, 0, s>>>(A.nnzb, A.br, A.bc, tsrc.p, A.v64.p, C.v64.p);
+  FSI_CHECK_LAUNCH();
+  C.tpr = choose_tpr(C.nnzb, C.nbr);
+}
+
+void bsr_spgemm(const Bsr& A, const Bsr& B, Bsr& C, cudaStream_t s) {
+  require(A.bc == B.br && A.nbc == B.nbr, "bsr_spgemm: inner dimensions differ");
+  C = Bsr();
+  C.nbr = A.nbr; C.nbc = B.nbc; C.br = A.br; C.bc = B.bc;
+  DBuf<int> cnt(A.nbr > 0 ? A.nbr : 1), overflow(1);
+  FSI_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(int), s));
+  const int grid = div_up(A.nbr, kWarpsPerBlock);
+  if (A.nbr > 0) {
+    k_spgemm_sym<false><<<grid, kWarpsPerBlock * 32, 0, s>>>(A.nbr, A.rowptr.p, A.colind.p, B.rowptr.p, B.colind.p,
+                                                            cnt.p, nullptr, nullptr, overflow.p);
+    FSI_CHECK_LAUNCH();
+  }
+  int of = 0;
+  FSI_CUDA(cudaMemcpyAsync(&of, overflow.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  require(!of, "bsr_spgemm: a product row has more than 768 block columns");
+  finalize_rowptr(cnt.p, C, s);
+  if (A.nbr > 0) {
+    k_spgemm_sym<true><<<grid, kWarpsPerBlock * 32, 0, s>>>(A.nbr, A.rowptr.p, A.colind.p, B.rowptr.p, B.colind.p,
+                                                           nullptr, C.rowptr.p, C.colind.p, overflow.p);
+    FSI_CHECK_LAUNCH();
+    spgemm_dispatch(A.br, A.bc, B.bc, [&]<int BR, int BK, int BC>() {
+      k_spgemm_num<BR, BK, BC><<<grid, 128, 0, s>>>(A.nbr, A.rowptr.p, A.colind.p, A.v64.p, B.rowptr.p, B.colind.p,
+                                                    B.v64.p, C.rowptr.p, C.colind.p, C.v64.p);
+      FSI_CHECK_LAUNCH();
+    });
+  }
+  C.tpr = choose_tpr(C.nnzb, C.nbr);
+}
+
+void sort_segments(int nseg, const int* off, int* key, int* pay, cudaStream_t s) {
+  if (nseg <= 0) return;
+  k_sort_segments<<<div_up(nseg, 128), 128, 0, s>>>(nseg, off, key, pay);
+  FSI_CHECK_LAUNCH();
+}
+
+void bsr_scale_rows(Bsr& A, const double* w, cudaStream_t s) {
+  if (A.nbr == 0) return;
+  k_scale_rows<<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, A.br, A.bc, A.rowptr.p, A.v64.p, w);
+  FSI_CHECK_LAUNCH();
+}
+
+void bsr_point_diagonal(const Bsr& A, double* diag, cudaStream_t s) {
+  require(A.br == A.bc && A.nbr == A.nbc, "point diagonal of a non-square matrix");
+  if (A.nbr == 0) return;
+  k_point_diag<<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, A.br, A.rowptr.p, A.colind.p, A.v64.p, diag);
+  FSI_CHECK_LAUNCH();
+}
+
+void invert_nonzero(int64_t n, const double* diag, double* dinv, cudaStream_t s) {
+  if (n == 0) return;
+  k_invert_nonzero<<<div_up(n, 256), 256, 0, s>>>(n, diag, dinv);
+  FSI_CHECK_LAUNCH();
+}
+
+void bsr_make_fp32(Bsr& A, cudaStream_t s) {
+  const int64_t n = A.nnzb * A.br * A.bc;
+  A.v32.alloc(n > 0 ? n : 1);
+  if (n > 0) {
+    k_to_f32<<<div_up(n, 256), 256, 0, s>>>(n, A.v64.p, A.v32.p);
+    FSI_CHECK_LAUNCH();
+  }
+}
+
+void bsr_to_dense(const Bsr& A, double* dense, cudaStream_t s) {
+  const int64_t nr = A.rows(), nc = A.cols();
+  FSI_CUDA(cudaMemsetAsync(dense, 0, sizeof(double) * nr * nc, s));
+  if (A.nbr == 0) return;
+  k_to_dense<<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, A.br, A.bc, (int)nc, A.rowptr.p, A.colind.p, A.v64.p, dense);
+  FSI_CHECK_LAUNCH();
+}
+
+bool dense_inverse(int n, double* M, double* Minv, cudaStream_t s) {
+  DBuf<int> fail(1);
+  FSI_CUDA(cudaMemsetAsync(fail.p, 0, sizeof(int), s));
+  if (n > 0) {
+    k_gauss_jordan<<<1, 1024, 0, s>>>(n, M, Minv, fail.p);
+    FSI_CHECK_LAUNCH();
+  }
+  int f = 0;
+  FSI_CUDA(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  return f == 0;
+}
+
+}  // namespace fsi

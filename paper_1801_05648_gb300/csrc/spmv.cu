@@ -1,0 +1,93 @@
+// Host-side dispatch of the BSR SpMV kernels over the block shapes the solver
+// uses: d x d vector blocks (d = 2, 3), the d x 1 / 1 x d velocity-pressure
+// couplings, scalar blocks, and the k x k / b x k / k x b blocks of the AMG
+// levels (k = 3 or 6 rigid-body modes for the solid block).
+#include "spmv.cuh"
+
+namespace fsi {
+
+namespace {
+
+template <class T, int BR, int BC1, int BC2, class Epi>
+void launch(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const Epi& epi, cudaStream_t s) {
+  if (A1.nbr == 0) return;
+  const int tpr = A1.tpr;
+  const int threads = 256;
+  const int blocks = div_up((int64_t)A1.nbr * tpr, threads);
+  const T* v2 = nullptr; const int* rp2 = nullptr; const int* ci2 = nullptr;
+  if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; }
+  k_bsr_spmv<T, BR, BC1, BC2, Epi><<<blocks, threads, 0, s>>>(A1.nbr, tpr, A1.rowptr.p, A1.colind.p, A1.vals<T>(), x1,
+                                                             rp2, ci2, v2, x2, epi);
+  FSI_CHECK_LAUNCH();
+}
+
+// Calls f.template operator()<BR, BC1, BC2>() for the runtime shape.
+template <class F>
+void dispatch(int br, int bc1, int bc2, F&& f) {
+#define FSI_SHAPE(a, b, c) if (br == a && bc1 == b && bc2 == c) { f.template operator()<a, b, c>(); return; }
+  FSI_SHAPE(1, 1, 0) FSI_SHAPE(2, 2, 0) FSI_SHAPE(3, 3, 0) FSI_SHAPE(6, 6, 0)
+  FSI_SHAPE(2, 3, 0) FSI_SHAPE(3, 2, 0) FSI_SHAPE(3, 6, 0) FSI_SHAPE(6, 3, 0)
+  FSI_SHAPE(2, 1, 0) FSI_SHAPE(3, 1, 0) FSI_SHAPE(1, 2, 0) FSI_SHAPE(1, 3, 0)
+  FSI_SHAPE(2, 2, 1) FSI_SHAPE(3, 3, 1) FSI_SHAPE(1, 2, 1) FSI_SHAPE(1, 3, 1)
+#undef FSI_SHAPE
+  throw Error(EINVAL_, "unsupported BSR block shape " + std::to_string(br) + "x" + std::to_string(bc1) + "+" +
+                           std::to_string(bc2));
+}
+
+inline void check_pair(const Bsr& A1, const Bsr* A2) {
+  if (A2 && A2->nbr != 0)
+    require(A2->nbr == A1.nbr && A2->br == A1.br, "fused SpMV: matrices with different block rows");
+}
+
+}  // namespace
+
+template <class T>
+void spmv_axpby(const Bsr& A, const T* x, T alpha, T beta, T* y, cudaStream_t s) {
+  dispatch(A.br, A.bc, 0, [&]<int BR, int BC1, int BC2>() {
+    launch<T, BR, BC1, 0>(A, x, nullptr, nullptr, EpiAxpby<T, BR>{y, alpha, beta}, s);
+  });
+}
+
+template <class T>
+void spmv2_axpby(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, T alpha, T beta, T* y, cudaStream_t s) {
+  if (A2 && A2->nbr == 0) A2 = nullptr;
+  check_pair(A1, A2);
+  dispatch(A1.br, A1.bc, A2 ? A2->bc : 0, [&]<int BR, int BC1, int BC2>() {
+    launch<T, BR, BC1, BC2>(A1, x1, A2, x2, EpiAxpby<T, BR>{y, alpha, beta}, s);
+  });
+}
+
+template <class T>
+void spmv2_resid(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const T* b, T* r, cudaStream_t s) {
+  if (A2 && A2->nbr == 0) A2 = nullptr;
+  check_pair(A1, A2);
+  dispatch(A1.br, A1.bc, A2 ? A2->bc : 0, [&]<int BR, int BC1, int BC2>() {
+    launch<T, BR, BC1, BC2>(A1, x1, A2, x2, EpiResid<T, BR>{b, r}, s);
+  });
+}
+
+template <class T>
+void spmv_cheb(const Bsr& A, const T* x, const T* b, const T* dinv, T* d, T* xo, T c1, T c2, cudaStream_t s) {
+  dispatch(A.br, A.bc, 0, [&]<int BR, int BC1, int BC2>() {
+    launch<T, BR, BC1, 0>(A, x, nullptr, nullptr, EpiCheb<T, BR>{b, dinv, x, d, xo, c1, c2}, s);
+  });
+}
+
+template <class T>
+void spmv_dinv(const Bsr& A, const T* x, const T* dinv, T* y, cudaStream_t s) {
+  dispatch(A.br, A.bc, 0, [&]<int BR, int BC1, int BC2>() {
+    launch<T, BR, BC1, 0>(A, x, nullptr, nullptr, EpiDinv<T, BR>{dinv, y}, s);
+  });
+}
+
+#define FSI_INST(T)                                                                                         \
+  template void spmv_axpby<T>(const Bsr&, const T*, T, T, T*, cudaStream_t);                                \
+  template void spmv2_axpby<T>(const Bsr&, const T*, const Bsr*, const T*, T, T, T*, cudaStream_t);         \
+  template void spmv2_resid<T>(const Bsr&, const T*, const Bsr*, const T*, const T*, T*, cudaStream_t);     \
+  template void spmv_cheb<T>(const Bsr&, const T*, const T*, const T*, T*, T*, T, T, cudaStream_t);         \
+  template void spmv_dinv<T>(const Bsr&, const T*, const T*, T*, cudaStream_t);
+FSI_INST(double)
+FSI_INST(float)
+#undef FSI_INST
+
+}  // namespace fsi

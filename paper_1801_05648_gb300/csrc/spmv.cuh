@@ -1,0 +1,182 @@
+// Block-sparse (BSR) matrix-vector products with fused epilogues.
+//
+// A group of `tpr` lanes (4..32, a power of two inside one warp) owns one block
+// row: lane l reads blocks l, l+tpr, ... of the row, so the lanes of a group
+// stream consecutive blocks (row-major br x bc values, 16-byte vector loads
+// whenever the block size allows) and the block-column indices coalesced; the
+// x entries are gathered through the read-only path.  The group reduces its br
+// partial sums with shuffles and lane 0 applies the epilogue.  An optional
+// second matrix with the same block rows (e.g. the d x 1 pressure columns next
+// to the d x d vector columns of the monolithic operator) is accumulated into
+// the same sums, so one pass covers every column class of a row.
+#pragma once
+#include "common.cuh"
+
+namespace fsi {
+
+template <class T, int N>
+__device__ __forceinline__ void load_stream(const T* __restrict__ p, T* out) {
+  if constexpr (sizeof(T) == 8 && N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      double2 v = __ldcs(reinterpret_cast<const double2*>(p) + i);
+      out[2 * i] = v.x; out[2 * i + 1] = v.y;
+    }
+  } else if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      float4 v = __ldcs(reinterpret_cast<const float4*>(p) + i);
+      out[4 * i] = v.x; out[4 * i + 1] = v.y; out[4 * i + 2] = v.z; out[4 * i + 3] = v.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      float2 v = __ldcs(reinterpret_cast<const float2*>(p) + i);
+      out[2 * i] = v.x; out[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = __ldcs(p + i);
+  }
+}
+
+template <class T, int N>
+__device__ __forceinline__ void load_gather(const T* __restrict__ p, T* out) {
+  if constexpr (sizeof(T) == 8 && N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
+      out[2 * i] = v.x; out[2 * i + 1] = v.y;
+    }
+  } else if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
+      out[2 * i] = v.x; out[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = __ldg(p + i);
+  }
+}
+
+// ------------------------------------------------------------------ epilogues
+// y = alpha * (A x) + beta * y   (y not read when beta == 0)
+template <class T, int BR>
+struct EpiAxpby {
+  T* y; T alpha; T beta;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      T* yy = y + (size_t)row * BR + i;
+      T v = alpha * acc[i];
+      if (beta != T(0)) v += beta * *yy;
+      *yy = v;
+    }
+  }
+};
+
+// r = b - A x
+template <class T, int BR>
+struct EpiResid {
+  const T* b; T* r;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      size_t k = (size_t)row * BR + i;
+      r[k] = b[k] - acc[i];
+    }
+  }
+};
+
+// One Chebyshev step (Saad Alg. 12.1, residual recomputed):
+//   r = dinv * (b - A x);  d = c1 * d + c2 * r;  xo = x + d
+// d is only touched at the row itself, so it is updated in place; xo must not
+// alias x (x is gathered by other rows).  d is not read when c1 == 0.
+template <class T, int BR>
+struct EpiCheb {
+  const T* b; const T* dinv; const T* x; T* d; T* xo; T c1; T c2;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      size_t k = (size_t)row * BR + i;
+      T r = dinv[k] * (b[k] - acc[i]);
+      T dn = c2 * r;
+      if (c1 != T(0)) dn += c1 * d[k];
+      d[k] = dn;
+      xo[k] = x[k] + dn;
+    }
+  }
+};
+
+// y = dinv * (A x)  (power iteration on D^-1 A)
+template <class T, int BR>
+struct EpiDinv {
+  const T* dinv; T* y;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      size_t k = (size_t)row * BR + i;
+      y[k] = dinv[k] * acc[i];
+    }
+  }
+};
+
+// ------------------------------------------------------------------ kernel
+template <class T, int BR, int BC1, int BC2, class Epi>
+__global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
+    const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, const T* __restrict__ x1,
+    const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, const T* __restrict__ x2,
+    Epi epi) {
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = gtid / tpr;
+  const int lane = threadIdx.x & (tpr - 1);
+  const bool valid = row < nbr;
+  T acc[BR];
+#pragma unroll
+  for (int i = 0; i < BR; ++i) acc[i] = T(0);
+  if (valid) {
+    const int kb = rp1[row], ke = rp1[row + 1];
+    for (int k = kb + lane; k < ke; k += tpr) {
+      const int c = __ldcs(ci1 + k);
+      T blk[BR * BC1], xv[BC1];
+      load_stream<T, BR * BC1>(v1 + (size_t)k * (BR * BC1), blk);
+      load_gather<T, BC1>(x1 + (size_t)c * BC1, xv);
+#pragma unroll
+      for (int i = 0; i < BR; ++i)
+#pragma unroll
+        for (int j = 0; j < BC1; ++j) acc[i] += blk[i * BC1 + j] * xv[j];
+    }
+    if constexpr (BC2 > 0) {
+      const int kb2 = rp2[row], ke2 = rp2[row + 1];
+      for (int k = kb2 + lane; k < ke2; k += tpr) {
+        const int c = __ldcs(ci2 + k);
+        T blk[BR * BC2], xv[BC2];
+        load_stream<T, BR * BC2>(v2 + (size_t)k * (BR * BC2), blk);
+        load_gather<T, BC2>(x2 + (size_t)c * BC2, xv);
+#pragma unroll
+        for (int i = 0; i < BR; ++i)
+#pragma unroll
+          for (int j = 0; j < BC2; ++j) acc[i] += blk[i * BC2 + j] * xv[j];
+      }
+    }
+  }
+  for (int off = tpr >> 1; off > 0; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < BR; ++i) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off, tpr);
+  if (valid && lane == 0) epi(row, acc);
+}
+
+// ------------------------------------------------------------------ host API
+// y = alpha * A x + beta * y
+template <class T> void spmv_axpby(const Bsr& A, const T* x, T alpha, T beta, T* y, cudaStream_t s);
+// y = alpha * (A1 x1 + A2 x2) + beta * y   (A2 may have 0 block rows == none)
+template <class T> void spmv2_axpby(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, T alpha, T beta, T* y, cudaStream_t s);
+// r = b - A1 x1 - A2 x2
+template <class T> void spmv2_resid(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const T* b, T* r, cudaStream_t s);
+// Chebyshev step epilogue (see EpiCheb)
+template <class T> void spmv_cheb(const Bsr& A, const T* x, const T* b, const T* dinv, T* d, T* xo, T c1, T c2, cudaStream_t s);
+// y = dinv * (A x)
+template <class T> void spmv_dinv(const Bsr& A, const T* x, const T* dinv, T* y, cudaStream_t s);
+
+}  // namespace fsi

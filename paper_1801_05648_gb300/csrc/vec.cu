@@ -1,0 +1,220 @@
+#include "vec.cuh"
+
+namespace fsi {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <class T>
+__global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T v = a * x[i];
+    if (b != T(0)) v += b * y[i];
+    y[i] = v;
+  }
+}
+
+template <class T>
+__global__ void k_axpbyz(int64_t n, T a, const T* __restrict__ x, T b, const T* __restrict__ y, T* __restrict__ z) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = a * x[i] + b * y[i];
+}
+
+template <class T>
+__global__ void k_vmul(int64_t n, const T* __restrict__ x, const T* __restrict__ w, T* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * w[i];
+}
+
+template <class Ti, class To>
+__global__ void k_cast(int64_t n, const Ti* __restrict__ x, To* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (To)x[i];
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (threadIdx.x < (blockDim.x >> 5)) v = sh[threadIdx.x];
+  if (w == 0)
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// partials[blockIdx] = sum over this block's contiguous chunk of x*y
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_dot_partial(int64_t n, const T* __restrict__ x,
+                                                              const T* __restrict__ y, double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += (double)x[i] * (double)y[i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// out[c] = (sqrt?) sum_k partials[c * np + k], one block per column c
+__global__ void __launch_bounds__(kRedThreads) k_reduce_cols(const double* __restrict__ partials, int np,
+                                                             const int* jcount, int joff, double* out, int take_sqrt) {
+  __shared__ double sh[32];
+  const int c = blockIdx.x;
+  const int J = jcount ? (*jcount + joff) : joff;
+  if (c >= J) return;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) acc += partials[(size_t)c * np + k];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[c] = take_sqrt ? sqrt(acc) : acc;
+}
+
+// Multi-dot: partials[i * gridDim + block] = <V_i, w> over the block's chunk, i < J.
+// Four basis vectors per pass over the chunk of w.
+__global__ void __launch_bounds__(kRedThreads) k_mdot_partial(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                                              const int* __restrict__ jcount, int joff,
+                                                              const double* __restrict__ w,
+                                                              double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const int J = *jcount + joff;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  for (int i0 = 0; i0 < J; i0 += 4) {
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const int ni = J - i0 < 4 ? J - i0 : 4;
+    const double* v0 = V + (size_t)i0 * ldv;
+    for (int64_t r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+      const double wr = __ldg(w + r);
+      a0 += __ldcs(v0 + r) * wr;
+      if (ni > 1) a1 += __ldcs(v0 + ldv + r) * wr;
+      if (ni > 2) a2 += __ldcs(v0 + 2 * ldv + r) * wr;
+      if (ni > 3) a3 += __ldcs(v0 + 3 * ldv + r) * wr;
+    }
+    double s0 = block_sum(a0, sh);
+    if (threadIdx.x == 0) partials[(size_t)i0 * gridDim.x + blockIdx.x] = s0;
+    if (ni > 1) { double s = block_sum(a1, sh); if (threadIdx.x == 0) partials[(size_t)(i0 + 1) * gridDim.x + blockIdx.x] = s; }
+    if (ni > 2) { double s = block_sum(a2, sh); if (threadIdx.x == 0) partials[(size_t)(i0 + 2) * gridDim.x + blockIdx.x] = s; }
+    if (ni > 3) { double s = block_sum(a3, sh); if (threadIdx.x == 0) partials[(size_t)(i0 + 3) * gridDim.x + blockIdx.x] = s; }
+  }
+}
+
+// w -= sign * sum_i h[i] V_i  over the block's chunk; optional per-block sum of w^2
+__global__ void __launch_bounds__(kRedThreads) k_maxpy(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                                       const int* __restrict__ jcount, int joff,
+                                                       const double* __restrict__ h, double sign,
+                                                       double* __restrict__ w, double* __restrict__ nrm_partials) {
+  __shared__ double hs[256];
+  __shared__ double sh[32];
+  const int J = *jcount + joff;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double nacc = 0.0;
+  for (int i0 = 0; i0 < J || i0 == 0; i0 += 256) {
+    const int cnt = J - i0 < 256 ? J - i0 : 256;
+    __syncthreads();
+    if (threadIdx.x < cnt) hs[threadIdx.x] = sign * h[i0 + threadIdx.x];
+    __syncthreads();
+    const bool last = i0 + 256 >= J;
+    for (int64_t r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+      double acc = w[r];
+      const double* vp = V + (size_t)i0 * ldv + r;
+      for (int i = 0; i < cnt; ++i) acc -= hs[i] * __ldcs(vp + (size_t)i * ldv);
+      w[r] = acc;
+      if (last) nacc += acc * acc;
+    }
+    if (J <= 0) break;
+  }
+  if (nrm_partials) {
+    nacc = block_sum(nacc, sh);
+    if (threadIdx.x == 0) nrm_partials[blockIdx.x] = nacc;
+  }
+}
+
+}  // namespace
+
+template <class T>
+void axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s) {
+  if (n <= 0) return;
+  k_axpby<T><<<grid_for(n), kThreads, 0, s>>>(n, a, x, b, y);
+  FSI_CHECK_LAUNCH();
+}
+template <class T>
+void axpbyz(int64_t n, T a, const T* x, T b, const T* y, T* z, cudaStream_t s) {
+  if (n <= 0) return;
+  k_axpbyz<T><<<grid_for(n), kThreads, 0, s>>>(n, a, x, b, y, z);
+  FSI_CHECK_LAUNCH();
+}
+template <class T>
+void vmul(int64_t n, const T* x, const T* w, T* y, cudaStream_t s) {
+  if (n <= 0) return;
+  k_vmul<T><<<grid_for(n), kThreads, 0, s>>>(n, x, w, y);
+  FSI_CHECK_LAUNCH();
+}
+template <class Ti, class To>
+void cast(int64_t n, const Ti* x, To* y, cudaStream_t s) {
+  if (n <= 0) return;
+  k_cast<Ti, To><<<grid_for(n), kThreads, 0, s>>>(n, x, y);
+  FSI_CHECK_LAUNCH();
+}
+template <class T>
+void dot_dev(int64_t n, const T* x, const T* y, double* partials, double* out, cudaStream_t s) {
+  k_dot_partial<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, x, y, partials);
+  FSI_CHECK_LAUNCH();
+  k_reduce_cols<<<1, kRedThreads, 0, s>>>(partials, kRedBlocks, nullptr, 1, out, 0);
+  FSI_CHECK_LAUNCH();
+}
+template <class T>
+double dot_host(int64_t n, const T* x, const T* y, double* partials, double* out, cudaStream_t s) {
+  dot_dev<T>(n, x, y, partials, out, s);
+  double h = 0.0;
+  FSI_CUDA(cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+void mdot(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* w, double* partials,
+          double* h, int maxcols, cudaStream_t s) {
+  k_mdot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, V, ldv, jcount, joff, w, partials);
+  FSI_CHECK_LAUNCH();
+  k_reduce_cols<<<maxcols, kRedThreads, 0, s>>>(partials, kRedBlocks, jcount, joff, h, 0);
+  FSI_CHECK_LAUNCH();
+}
+
+void maxpy(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* h, double sign,
+           double* w, double* nrm_partials, cudaStream_t s) {
+  k_maxpy<<<kRedBlocks, kRedThreads, 0, s>>>(n, V, ldv, jcount, joff, h, sign, w, nrm_partials);
+  FSI_CHECK_LAUNCH();
+}
+
+void finish_norm(const double* partials, double* out, cudaStream_t s) {
+  k_reduce_cols<<<1, kRedThreads, 0, s>>>(partials, kRedBlocks, nullptr, 1, out, 1);
+  FSI_CHECK_LAUNCH();
+}
+
+template void axpby<double>(int64_t, double, const double*, double, double*, cudaStream_t);
+template void axpby<float>(int64_t, float, const float*, float, float*, cudaStream_t);
+template void axpbyz<double>(int64_t, double, const double*, double, const double*, double*, cudaStream_t);
+template void axpbyz<float>(int64_t, float, const float*, float, const float*, float*, cudaStream_t);
+template void vmul<double>(int64_t, const double*, const double*, double*, cudaStream_t);
+template void vmul<float>(int64_t, const float*, const float*, float*, cudaStream_t);
+template void cast<double, float>(int64_t, const double*, float*, cudaStream_t);
+template void cast<float, double>(int64_t, const float*, double*, cudaStream_t);
+template void dot_dev<double>(int64_t, const double*, const double*, double*, double*, cudaStream_t);
+template void dot_dev<float>(int64_t, const float*, const float*, double*, double*, cudaStream_t);
+template double dot_host<double>(int64_t, const double*, const double*, double*, double*, cudaStream_t);
+template double dot_host<float>(int64_t, const float*, const float*, double*, double*, cudaStream_t);
+
+}  // namespace fsi

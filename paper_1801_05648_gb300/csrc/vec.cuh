@@ -1,0 +1,38 @@
+// Vector kernels of the solve path: BLAS-1 updates, precision casts and
+// deterministic two-stage reductions (fixed grid, fixed summation order, so a
+// result does not depend on scheduling), plus the tall-skinny products of the
+// Gram-Schmidt orthogonalisation.
+#pragma once
+#include "common.cuh"
+
+namespace fsi {
+
+constexpr int kRedBlocks = 4 * 152;   // partial sums per reduction (4 CTAs per SM)
+constexpr int kRedThreads = 256;
+
+// y = a x + b y  (y not read when b == 0)
+template <class T> void axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s);
+// z = a x + b y
+template <class T> void axpbyz(int64_t n, T a, const T* x, T b, const T* y, T* z, cudaStream_t s);
+// y = x * w (elementwise)
+template <class T> void vmul(int64_t n, const T* x, const T* w, T* y, cudaStream_t s);
+// y = (To) x
+template <class Ti, class To> void cast(int64_t n, const Ti* x, To* y, cudaStream_t s);
+// out[0] = sum_i x_i y_i (FP64 accumulation), device result; partials has kRedBlocks doubles
+template <class T> void dot_dev(int64_t n, const T* x, const T* y, double* partials, double* out, cudaStream_t s);
+// host convenience: synchronous dot
+template <class T> double dot_host(int64_t n, const T* x, const T* y, double* partials, double* out, cudaStream_t s);
+
+// Gram-Schmidt pieces.  V holds basis vectors of length n with leading dimension
+// ldv (vector i at V + i*ldv); the number of active vectors is read on the
+// device from *jcount (+ joff), so a captured graph can be replayed for every j.
+// h[i] = <V_i, w>, i < *jcount + joff
+void mdot(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* w, double* partials,
+          double* h, int maxcols, cudaStream_t s);
+// w -= sum_i h[i] V_i; if nrm_partials != nullptr also writes per-block sums of w^2
+void maxpy(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* h, double sign,
+           double* w, double* nrm_partials, cudaStream_t s);
+// out = sqrt(sum partials)
+void finish_norm(const double* partials, double* out, cudaStream_t s);
+
+}  // namespace fsi

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libfsi.so (declared in include/fsi.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+PyTorch supplies device memory (float64 CUDA tensors) and the stream.  A missing
+or unloadable library raises immediately; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfsi.so")
+
+FSI_OK, FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA, FSI_ENOTCONV, FSI_EBREAKDOWN, FSI_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+FSI_FP64, FSI_FP32_AMG = 0, 1
+FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES = 1, 2, 4
+STATUS_NAMES = {0: "FSI_OK", -1: "FSI_EINVAL", -2: "FSI_ENOMEM", -3: "FSI_ECUDA", -4: "FSI_ENOTCONV",
+                -5: "FSI_EBREAKDOWN", -6: "FSI_ENONFINITE"}
+BLOCKS = {"mesh": 0, "solid_schur": 1, "fluid_velocity": 2, "pressure_schur": 3, "solid_mass": 4,
+          "solid": 5, "fluid": 6, "precond": 7}
+
+# Every symbol include/fsi.h declares.
+EXPORTED = ["fsi_default_params", "fsi_setup", "fsi_precond_build", "fsi_solve", "fsi_free", "fsi_last_error",
+            "fsi_apply_operator", "fsi_apply_block", "fsi_amg_info", "fsi_amg_export"]
+
+
+class FSIError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("flags", ctypes.c_int),
+                ("dt_theta", ctypes.c_double), ("strength_theta", ctypes.c_double), ("coarse_max", ctypes.c_int),
+                ("max_levels", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_ratio", ctypes.c_double),
+                ("cheb_upper", ctypes.c_double), ("power_iters", ctypes.c_int), ("drop_tol", ctypes.c_double),
+                ("presmooth", ctypes.c_int), ("postsmooth", ctypes.c_int), ("vcycles_mesh", ctypes.c_int),
+                ("vcycles_solid", ctypes.c_int), ("vcycles_fluid", ctypes.c_int),
+                ("vcycles_pressure", ctypes.c_int), ("mass_degree", ctypes.c_int), ("mass_ratio", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_relres", ctypes.c_double), ("setup_s", ctypes.c_double),
+                ("precond_build_s", ctypes.c_double), ("solve_s", ctypes.c_double),
+                ("operator_bytes", ctypes.c_double), ("precond_bytes", ctypes.c_double),
+                ("relres_hist", ctypes.POINTER(ctypes.c_double)), ("hist_len", ctypes.c_int),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+@dataclass
+class SolveStats:
+    iters: int
+    cycles: int
+    status: int
+    true_relres: float
+    setup_s: float
+    precond_build_s: float
+    solve_s: float
+    operator_bytes: float
+    precond_bytes: float
+    history: list
+    kernel_launches: int
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfsi.so (build it first with paper_1801_05648_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: run paper_1801_05648_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64p, i32p, f64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), \
+        ctypes.POINTER(ctypes.c_double)
+    lib.fsi_default_params.argtypes = [ctypes.POINTER(Params), ctypes.c_int]
+    lib.fsi_default_params.restype = None
+    lib.fsi_setup.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int64, i64p, i32p, f64p, i64p, f64p,
+                              ctypes.POINTER(Params), vp]
+    lib.fsi_setup.restype = ctypes.c_int
+    lib.fsi_precond_build.argtypes = [vp, ctypes.c_int, ctypes.c_char_p]
+    lib.fsi_precond_build.restype = ctypes.c_int
+    lib.fsi_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.POINTER(Stats)]
+    lib.fsi_solve.restype = ctypes.c_int
+    lib.fsi_free.argtypes = [vp]
+    lib.fsi_free.restype = None
+    lib.fsi_last_error.argtypes = [vp]
+    lib.fsi_last_error.restype = ctypes.c_char_p
+    lib.fsi_apply_operator.argtypes = [vp, vp, vp]
+    lib.fsi_apply_operator.restype = ctypes.c_int
+    lib.fsi_apply_block.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.fsi_apply_block.restype = ctypes.c_int
+    lib.fsi_amg_info.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p, f64p]
+    lib.fsi_amg_info.restype = ctypes.c_int
+    lib.fsi_amg_export.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+    lib.fsi_amg_export.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def default_params(dim: int, **overrides) -> Params:
+    p = Params()
+    load_library().fsi_default_params(ctypes.byref(p), dim)
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(f"unknown fsi_params field {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+def _np_ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _dev_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class FSISolver:
+    """One monolithic Jacobian on the device: fsi_setup / fsi_precond_build / fsi_solve / fsi_free."""
+
+    def __init__(self, dim, rowptr, colind, vals, offsets, node_coords=None, params: Params | None = None,
+                 stream=None):
+        lib = load_library()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        rowptr = np.ascontiguousarray(rowptr, np.int64)
+        colind = np.ascontiguousarray(colind, np.int32)
+        vals = np.ascontiguousarray(vals, np.float64)
+        offsets = np.ascontiguousarray(offsets, np.int64)
+        self.n = int(offsets[5])
+        self.dim = dim
+        self.offsets = offsets.copy()
+        coords = None if node_coords is None else np.ascontiguousarray(node_coords, np.float64)
+        import torch
+        # The library runs on its own (non-default) stream so that graph capture is
+        # possible; every call first orders it after torch's current stream.
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        stream = self.stream.cuda_stream
+        self._stream = stream
+        self._order()
+        rc = lib.fsi_setup(ctypes.byref(self._h), dim, self.n, _np_ptr(rowptr, ctypes.c_int64),
+                           _np_ptr(colind, ctypes.c_int32), _np_ptr(vals, ctypes.c_double),
+                           _np_ptr(offsets, ctypes.c_int64),
+                           None if coords is None else _np_ptr(coords, ctypes.c_double),
+                           None if params is None else ctypes.byref(params), ctypes.c_void_p(stream))
+        if rc != FSI_OK:
+            raise FSIError(rc, lib.fsi_last_error(None).decode())
+
+    @classmethod
+    def from_system(cls, system, params=None, stream=None):
+        return cls(system.dim, system.rowptr, system.colind, system.vals, system.offsets, system.solid_coords,
+                   params, stream)
+
+    def _check(self, rc):
+        if rc != FSI_OK:
+            raise FSIError(rc, self._lib.fsi_last_error(self._h).decode())
+
+    def _order(self):
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+
+    def precond_build(self, precision: str | int = "fp64"):
+        prec = {"fp64": FSI_FP64, "fp32": FSI_FP32_AMG}.get(precision, precision)
+        self._check(self._lib.fsi_precond_build(self._h, int(prec), None))
+
+    def solve(self, rhs, x, rtol=1e-8, raise_on_error=True) -> SolveStats:
+        self._order()
+        st = Stats()
+        rc = self._lib.fsi_solve(self._h, _dev_ptr(rhs), _dev_ptr(x), rtol, ctypes.byref(st))
+        hist = [st.relres_hist[i] for i in range(st.hist_len)] if st.hist_len else []
+        out = SolveStats(st.iters, st.cycles, st.status, st.true_relres, st.setup_s, st.precond_build_s,
+                         st.solve_s, st.operator_bytes, st.precond_bytes, hist, st.kernel_launches)
+        if rc != FSI_OK and raise_on_error:
+            raise FSIError(rc, self._lib.fsi_last_error(self._h).decode())
+        return out
+
+    def apply_operator(self, x, y, sync=True):
+        """y = A x (enqueued on the solver's stream; waits for it unless sync=False)."""
+        self._order()
+        self._check(self._lib.fsi_apply_operator(self._h, _dev_ptr(x), _dev_ptr(y)))
+        if sync:
+            self._sync()
+
+    def apply_block(self, which, inp, out, sync=True):
+        w = BLOCKS.get(which, which)
+        self._order()
+        self._check(self._lib.fsi_apply_block(self._h, int(w), _dev_ptr(inp), _dev_ptr(out)))
+        if sync:
+            self._sync()
+
+    def _sync(self):
+        self.stream.synchronize()
+
+    def amg_info(self, which, level=0):
+        info = np.zeros(6, np.int64)
+        lam = ctypes.c_double()
+        self._check(self._lib.fsi_amg_info(self._h, BLOCKS.get(which, which), level, _np_ptr(info, ctypes.c_int64),
+                                           ctypes.byref(lam)))
+        return {"levels": int(info[0]), "nbrows": int(info[1]), "b": int(info[2]), "nnzb": int(info[3]),
+                "nagg": int(info[4]), "ncoarse": int(info[5]), "lam": lam.value}
+
+    def amg_export(self, which, level, what):
+        """what: 'agg', 'A' (-> rowptr, colind, values) or 'P'."""
+        w = BLOCKS.get(which, which)
+        inf = self.amg_info(w, level)
+        b = inf["b"]
+        if what == "agg":
+            out = np.empty(inf["nbrows"], np.int32)
+            self._check(self._lib.fsi_amg_export(self._h, w, level, 0, out.ctypes.data_as(ctypes.c_void_p)))
+            return out
+        if what == "A":
+            rp = np.empty(inf["nbrows"] + 1, np.int32)
+            ci = np.empty(inf["nnzb"], np.int32)
+            va = np.empty(inf["nnzb"] * b * b, np.float64)
+            for k, arr in ((1, rp), (2, ci), (3, va)):
+                self._check(self._lib.fsi_amg_export(self._h, w, level, k, arr.ctypes.data_as(ctypes.c_void_p)))
+            return rp, ci, va.reshape(-1, b, b)
+        if what == "P":
+            nn = np.zeros(1, np.int64)
+            self._check(self._lib.fsi_amg_export(self._h, w, level, 7, nn.ctypes.data_as(ctypes.c_void_p)))
+            rp = np.empty(inf["nbrows"] + 1, np.int32)
+            ci = np.empty(int(nn[0]), np.int32)
+            self._check(self._lib.fsi_amg_export(self._h, w, level, 4, rp.ctypes.data_as(ctypes.c_void_p)))
+            self._check(self._lib.fsi_amg_export(self._h, w, level, 5, ci.ctypes.data_as(ctypes.c_void_p)))
+            va = np.empty(int(nn[0]) * b * 64, np.float64)   # k <= 6 (upper bound), trimmed below
+            self._check(self._lib.fsi_amg_export(self._h, w, level, 6, va.ctypes.data_as(ctypes.c_void_p)))
+            return rp, ci, va
+        raise ValueError(what)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.fsi_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

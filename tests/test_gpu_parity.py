@@ -1,0 +1,229 @@
+"""Parity of the CUDA solver (through the C ABI) with the FP64 CPU oracle on
+seeded FSI Jacobians: outer SpMV, every AMG level (aggregates bit-exact,
+lambda, Galerkin matrices), every block inverse of Alg. 2, and whole FGMRES
+solves in the FP64 and FP32-AMG forms.  Tolerances: FP64 pieces agree to
+rounding (1e-11 relative; the oracle sums in another order), FP64 solves to
+1e-8 relative solution error with equal iteration counts (+-1), the FP32-AMG
+form to 1e-6 against the FP64 oracle solution."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fsigen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "2d_16x16": (fsigen.CONFIGS["2d_tiny"], 8.0),
+    "2d_64x32": (fsigen.CONFIGS["2d_tiny"].with_(name="2d_64x32", n=(64, 32)), 8.0),
+    "2d_37x19_ragged": (fsigen.CONFIGS["2d_tiny"].with_(name="2d_37x19", n=(37, 19), state_seed=3, rhs_seed=5), 8.0),
+    "3d_8x4x4": (fsigen.CONFIGS["3d"].with_(name="3d_8x4x4", n=(8, 4, 4)), 20.0),
+}
+HIER = ["mesh", "solid_schur", "fluid_velocity", "pressure_schur"]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_05648_gb300 import build
+    build.build()
+    return torch
+
+
+_cache = {}
+
+
+def case(name, torch):
+    if name not in _cache:
+        import paper_1801_05648_gb300 as P
+        cfg, mr = CASES[name]
+        s = fsigen.make_system(cfg)
+        o = oracle.OracleSolver.from_system(s, params=oracle.PrecondParams(mass_ratio=mr))
+        ref = o.solve(s.rhs)
+        g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr))
+        g.precond_build("fp64")
+        _cache[name] = (s, o, ref, g, mr)
+    return _cache[name]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_operator_parity(name, torch_cuda):
+    torch = torch_cuda
+    s, o, ref, g, _ = case(name, torch)
+    x = np.random.default_rng(11).standard_normal(s.n)
+    xt = torch.tensor(x, device="cuda")
+    yt = torch.empty_like(xt)
+    g.apply_operator(xt, yt)
+    assert rel(yt.cpu().numpy(), s.scipy() @ x) <= 1e-13
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hierarchies_match_oracle(name, torch_cuda):
+    s, o, ref, g, _ = case(name, torch_cuda)
+    invs = [o.P.M_inv, o.P.Shat_inv, o.P.Aff_inv, o.P.Sp_inv]
+    for w, inv in enumerate(invs):
+        H = inv.H
+        info = g.amg_info(w, 0)
+        assert info["levels"] == len(H.levels), HIER[w]
+        for lvl in range(len(H.levels)):
+            li = g.amg_info(w, lvl)
+            assert li["lam"] == pytest.approx(H.levels[lvl].lam, rel=1e-12)
+            if lvl + 1 < len(H.levels):
+                assert np.array_equal(g.amg_export(w, lvl, "agg"), H.levels[lvl].agg), (HIER[w], lvl)
+            if lvl > 0:
+                rp, ci, va = g.amg_export(w, lvl, "A")
+                b = li["b"]
+                Ag = sp.bsr_matrix((va, ci, rp), shape=(li["nbrows"] * b,) * 2).toarray()
+                Ao = H.levels[lvl].A.toarray()
+                assert np.linalg.norm(Ag - Ao) <= 1e-12 * np.linalg.norm(Ao), (HIER[w], lvl)
+
+
+def _block_slices(s, o):
+    of = s.offsets
+    return [("mesh", slice(of[0], of[1]), o.P.M_inv), ("solid_schur", slice(of[1], of[2]), o.P.Shat_inv),
+            ("fluid_velocity", slice(of[3], of[4]), o.P.Aff_inv), ("pressure_schur", slice(of[4], of[5]), o.P.Sp_inv),
+            ("solid_mass", slice(of[2], of[3]), o.P.Ms_inv), ("solid", slice(of[1], of[3]), o.P.S_inv),
+            ("fluid", slice(of[3], of[5]), o.P.F_inv), ("precond", slice(0, s.n), o.P)]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_block_inverses_fp64(name, torch_cuda):
+    torch = torch_cuda
+    s, o, ref, g, _ = case(name, torch)
+    for blk, sl, f in _block_slices(s, o):
+        r = np.random.default_rng(3).standard_normal(sl.stop - sl.start)
+        rt = torch.tensor(r, device="cuda")
+        zt = torch.zeros_like(rt)
+        g.apply_block(blk, rt, zt)
+        assert rel(zt.cpu().numpy(), f(r)) <= 1e-11, blk
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_fp64_parity(name, torch_cuda):
+    torch = torch_cuda
+    s, o, ref, g, _ = case(name, torch)
+    b = torch.tensor(s.rhs, device="cuda")
+    x = torch.zeros_like(b)
+    st = g.solve(b, x, 1e-8)
+    xc = x.cpu().numpy()
+    assert st.status == 0 and st.true_relres <= 1e-8
+    assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.01
+    assert abs(st.iters - ref.iters) <= 1, (st.iters, ref.iters)
+    assert rel(xc, ref.x) <= 1e-8
+    # residual history: monotone within each cycle, last estimate below tol
+    assert st.history[-1] <= 1e-8 and len(st.history) == st.iters
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_fp32_amg(name, torch_cuda):
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    s, o, ref, _, mr = case(name, torch)
+    g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr))
+    g.precond_build("fp32")
+    b = torch.tensor(s.rhs, device="cuda")
+    x = torch.zeros_like(b)
+    st = g.solve(b, x, 1e-8)
+    xc = x.cpu().numpy()
+    assert st.status == 0 and st.true_relres <= 1e-8
+    assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.01
+    assert rel(xc, ref.x) <= 1e-6
+    # FP32 block inverses agree with the FP64 oracle to single precision
+    for blk, sl, f in _block_slices(s, o):
+        r = np.random.default_rng(3).standard_normal(sl.stop - sl.start)
+        rt = torch.tensor(r, device="cuda")
+        zt = torch.zeros_like(rt)
+        g.apply_block(blk, rt, zt)
+        assert rel(zt.cpu().numpy(), f(r)) <= 1e-4, blk
+    g.close()
+
+
+def test_graph_replay_is_bit_identical(torch_cuda):
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    s, o, ref, _, mr = case("2d_64x32", torch)
+    b = torch.tensor(s.rhs, device="cuda")
+    xs = []
+    for flags in (0, P.FSI_USE_GRAPHS):
+        for prec in ("fp64", "fp32"):
+            g = P.FSISolver.from_system(s, params=P.default_params(2, flags=flags))
+            g.precond_build(prec)
+            x = torch.zeros_like(b)
+            st = g.solve(b, x, 1e-8)
+            x2 = torch.zeros_like(b)
+            st2 = g.solve(b, x2, 1e-8)          # second solve reuses the captured graph
+            assert torch.equal(x, x2) and st.iters == st2.iters
+            xs.append(x.cpu().numpy())
+            g.close()
+    assert np.array_equal(xs[0], xs[2]) and np.array_equal(xs[1], xs[3])
+
+
+def test_edge_cases(torch_cuda):
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    s, o, ref, g, mr = case("2d_16x16", torch)
+    z = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    x = torch.full_like(z, 7.0)
+    st = g.solve(z, x, 1e-8)                       # zero right-hand side: x = 0, no iterations
+    assert st.status == 0 and st.iters == 0 and torch.count_nonzero(x).item() == 0
+    bad = torch.tensor(s.rhs, device="cuda")
+    bad[5] = float("nan")
+    with pytest.raises(P.FSIError) as e:
+        g.solve(bad, x, 1e-8)
+    assert e.value.code == -6
+    g3 = P.FSISolver.from_system(s, params=P.default_params(2, maxit=3))
+    g3.precond_build("fp64")
+    b = torch.tensor(s.rhs, device="cuda")
+    st = g3.solve(b, x, 1e-8, raise_on_error=False)
+    assert st.status == -4 and st.iters == 3 and 0 < st.true_relres < 1
+    g3.close()
+    # warm start from the converged solution: no iteration needed
+    gw = P.FSISolver.from_system(s, params=P.default_params(2, flags=P.FSI_X0_GIVEN))
+    gw.precond_build("fp64")
+    x0 = torch.tensor(ref.x, device="cuda")
+    st = gw.solve(b, x0, 1e-8)
+    assert st.status == 0 and st.iters == 0
+    # precond before build is refused
+    gn = P.FSISolver.from_system(s)
+    with pytest.raises(P.FSIError):
+        gn.solve(b, x, 1e-8)
+    gw.close(); gn.close()
+
+
+@pytest.mark.parametrize("name", ["2d_mid", "3d"])
+def test_full_size_solves(name, torch_cuda):
+    """Full-size Jacobians: the solve reaches 1e-8 confirmed by an FP64 CPU residual,
+    sampled operator rows match, and the FP32-AMG form lands on the same solution."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    s = fsigen.make_system(name)
+    A = s.scipy()
+    mr = 8.0 if s.dim == 2 else 20.0
+    b = torch.tensor(s.rhs, device="cuda")
+    xs = {}
+    for prec in ("fp64", "fp32"):
+        g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr, flags=P.FSI_USE_GRAPHS))
+        g.precond_build(prec)
+        x = torch.zeros_like(b)
+        st = g.solve(b, x, 1e-8)
+        xc = x.cpu().numpy()
+        assert st.status == 0
+        assert np.linalg.norm(s.rhs - A @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.01
+        xs[prec] = xc
+        if prec == "fp64":
+            rows = np.random.default_rng(2).choice(s.n, 2000, replace=False)
+            v = np.random.default_rng(4).standard_normal(s.n)
+            vt = torch.tensor(v, device="cuda")
+            yt = torch.empty_like(vt)
+            g.apply_operator(vt, yt)
+            yr = A[rows] @ v
+            assert np.max(np.abs(yt.cpu().numpy()[rows] - yr)) <= 1e-12 * np.max(np.abs(yr))
+        g.close()
+    assert rel(xs["fp32"], xs["fp64"]) <= 1e-6
