@@ -1,10 +1,17 @@
 """Parity of the CUDA solver (through the C ABI) with the FP64 CPU oracle on
 seeded FSI Jacobians: outer SpMV, every AMG level (aggregates bit-exact,
 lambda, Galerkin matrices), every block inverse of Alg. 2, and whole FGMRES
-solves in the FP64 and FP32-AMG forms.  Tolerances: FP64 pieces agree to
-rounding (1e-11 relative; the oracle sums in another order), FP64 solves to
-1e-8 relative solution error with equal iteration counts (+-1), the FP32-AMG
-form to 1e-6 against the FP64 oracle solution."""
+solves in the FP64 and FP32-AMG forms.
+
+Tolerances: FP64 pieces agree to rounding (1e-11 relative; the oracle sums in
+another order); FP64 solves agree with the oracle's to 1e-8 relative solution
+error with iteration counts within +-1.  The FP32-AMG form runs another Krylov
+trajectory; both stop at ||b - Ax||/||b|| <= 1e-8, and with condition numbers
+near 1e14 that residual bounds the solution error only to ~1e-2 (measured: the
+FP64 oracle solution is 7e-3 from the manufactured x* on the 64x32 mesh, almost
+all of it in the pressure).  The FP32 form is therefore required to meet the
+1e-8 residual and to be as accurate as the FP64 form: error against x* within
+10x of the FP64 oracle's error (1e-6 when that is smaller)."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -114,7 +121,7 @@ def test_solve_fp64_parity(name, torch_cuda):
     st = g.solve(b, x, 1e-8)
     xc = x.cpu().numpy()
     assert st.status == 0 and st.true_relres <= 1e-8
-    assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.01
+    assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.001
     assert abs(st.iters - ref.iters) <= 1, (st.iters, ref.iters)
     assert rel(xc, ref.x) <= 1e-8
     # residual history: monotone within each cycle, last estimate below tol
@@ -133,8 +140,9 @@ def test_solve_fp32_amg(name, torch_cuda):
     st = g.solve(b, x, 1e-8)
     xc = x.cpu().numpy()
     assert st.status == 0 and st.true_relres <= 1e-8
-    assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.01
-    assert rel(xc, ref.x) <= 1e-6
+    assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.001
+    err64 = rel(ref.x, s.x_exact)
+    assert rel(xc, s.x_exact) <= max(10.0 * err64, 1e-6), (rel(xc, s.x_exact), err64)
     # FP32 block inverses agree with the FP64 oracle to single precision
     for blk, sl, f in _block_slices(s, o):
         r = np.random.default_rng(3).standard_normal(sl.stop - sl.start)
@@ -200,7 +208,8 @@ def test_edge_cases(torch_cuda):
 @pytest.mark.parametrize("name", ["2d_mid", "3d"])
 def test_full_size_solves(name, torch_cuda):
     """Full-size Jacobians: the solve reaches 1e-8 confirmed by an FP64 CPU residual,
-    sampled operator rows match, and the FP32-AMG form lands on the same solution."""
+    sampled operator rows match, and the FP32-AMG form is as accurate (against the
+    manufactured solution) as the FP64 form."""
     torch = torch_cuda
     import paper_1801_05648_gb300 as P
     s = fsigen.make_system(name)
@@ -215,7 +224,7 @@ def test_full_size_solves(name, torch_cuda):
         st = g.solve(b, x, 1e-8)
         xc = x.cpu().numpy()
         assert st.status == 0
-        assert np.linalg.norm(s.rhs - A @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.01
+        assert np.linalg.norm(s.rhs - A @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.001
         xs[prec] = xc
         if prec == "fp64":
             rows = np.random.default_rng(2).choice(s.n, 2000, replace=False)
@@ -226,4 +235,5 @@ def test_full_size_solves(name, torch_cuda):
             yr = A[rows] @ v
             assert np.max(np.abs(yt.cpu().numpy()[rows] - yr)) <= 1e-12 * np.max(np.abs(yr))
         g.close()
-    assert rel(xs["fp32"], xs["fp64"]) <= 1e-6
+    e64, e32 = rel(xs["fp64"], s.x_exact), rel(xs["fp32"], s.x_exact)
+    assert e32 <= max(10.0 * e64, 1e-6), (e32, e64)
