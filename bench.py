@@ -50,8 +50,9 @@ def parse_args(argv=None):
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--kernel-only", choices=["spmv"], default=None,
-                    help="run only the outer SpMV a few times (a small program for ncu captures)")
+    ap.add_argument("--kernel-only", choices=["spmv", "solve"], default=None,
+                    help="small programs for ncu captures: 'spmv' runs the outer SpMV 6 times; 'solve' runs "
+                         "one solve of the bench workload inside cudaProfilerStart/Stop")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-iters", type=int, default=8)
     ap.add_argument("--full-iters", type=int, default=0)
@@ -163,20 +164,32 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def kernel_traffic(profile_name: str, source_files):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is
-    unchanged since it was captured (else None)."""
-    path = os.path.join(ROOT, "profiles", profile_name)
-    try:
-        d = json.load(open(path))
-    except Exception:
-        return None
+def source_hash(source_files) -> str:
     h = hashlib.sha256()
     for f in source_files:
         h.update(open(os.path.join(ROOT, f), "rb").read())
-    if d.get("source_sha256") != h.hexdigest():
+    return h.hexdigest()
+
+
+def kernel_traffic(profile_name: str, source_files):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from a
+    committed ncu summary under profiles/, read from its 'dram_bytes_per_launch:'
+    and 'source_sha256:' lines; None when the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", profile_name)
+    vals = {}
+    try:
+        for line in open(path):
+            if ":" in line and line.split(":", 1)[0].strip() in ("dram_bytes_per_launch", "source_sha256"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    except OSError:
         return None
-    return d.get("dram_bytes_per_launch")
+    if vals.get("source_sha256") != source_hash(source_files):
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def dist_setup(args):
@@ -301,8 +314,27 @@ def bench_ours(args):
         rr = np.linalg.norm(systems[i].rhs - A @ xc) / np.linalg.norm(systems[i].rhs)
         assert rr <= 1.001e-8, f"end-to-end result fails the residual check ({rr})"
 
-    # ---- roofline of the dominant kernel family (BSR SpMV): the outer FP64 operator,
-    # alternating between the resident Jacobians so L2 holds none of the next one's data
+    # ---- roofline of the dominant kernel: the fused FP32 2x2 Chebyshev SpMV step of the
+    # V-cycles, on level 0 of the mesh and fluid-velocity hierarchies of every resident
+    # Jacobian in turn (10 matrices, ~0.3 GB together: each launch finds the L2 holding
+    # the other nine's data, not its own)
+    targets = [(g, w) for g in solvers for w in ("mesh", "fluid_velocity")]
+    for g, w in targets:
+        g.smoother_steps(w, 0, 1)
+    bs.synchronize()
+    rounds = 6
+    cheb_bytes = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bs)
+    for _ in range(rounds):
+        for g, w in targets:
+            cheb_bytes += g.smoother_steps(w, 0, 1)
+    e1.record(bs)
+    bs.synchronize()
+    cheb_launches = rounds * len(targets)
+    cheb_s = e0.elapsed_time(e1) / 1e3
+    cheb_achieved = cheb_bytes / cheb_s / 1e9
+    # ---- the outer FP64 operator (secondary), alternating between the resident Jacobians
     reps = 60
     yv = [torch.empty(n, dtype=torch.float64, device=dev) for _ in systems]
     for k in range(5):
@@ -318,8 +350,9 @@ def bench_ours(args):
     op_bytes = st[0].operator_bytes
     achieved = op_bytes / spmv_s / 1e9
     peak, peak_kind = measured_peak()
-    traffic = kernel_traffic("spmv_operator_2d_mid.json",
-                             ["paper_1801_05648_gb300/csrc/spmv.cuh", "paper_1801_05648_gb300/csrc/spmv.cu"])
+    srcs = ["paper_1801_05648_gb300/csrc/spmv.cuh", "paper_1801_05648_gb300/csrc/spmv.cu"]
+    traffic = kernel_traffic("spmv_outer_fp64_2d_mid.md", srcs)
+    cheb_traffic = kernel_traffic("spmv_cheb_fp32_2d_mid.md", srcs)
 
     # ---- CPU baseline: the oracle on this host's cores (bounded sample)
     cpu = None
@@ -371,10 +404,16 @@ def bench_ours(args):
         "precond_build_s_fp64": statistics.mean(build_s),
         "solve_algorithmic_gbs": bytes_per_solve / (ms / 1e3) / 1e9,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
-        "roofline": {"kernel": "BSR SpMV (outer FP64 operator: vector rows d x d + d x 1, pressure rows 1 x d + 1 x 1)",
-                     "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": op_bytes,
-                     "launch_us": spmv_s * 1e6},
+        "roofline": {"kernel": "k_bsr_spmv<float,2,2,0,EpiCheb>: fused Chebyshev step of the FP32 V-cycle "
+                               "(level 0 of the mesh and fluid-velocity hierarchies)",
+                     "bound": "hbm", "achieved": cheb_achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": cheb_achieved / peak, "traffic": cheb_traffic,
+                     "algorithmic_bytes": cheb_bytes / cheb_launches, "launch_us": cheb_s / cheb_launches * 1e6},
+        "roofline_outer_spmv": {"kernel": "k_bsr_spmv<double,2,2,1,EpiAxpby> + <double,1,2,1,EpiAxpby>: outer "
+                                          "FP64 operator (vector rows, pressure rows)",
+                                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": op_bytes,
+                                "launch_us": spmv_s * 1e6},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": launches,
@@ -417,13 +456,31 @@ def bench_reference(args):
 
 
 def kernel_only(args):
-    """Outer SpMV only: one resident Jacobian, 6 applications of the operator."""
+    """'spmv': one resident Jacobian, 6 applications of the outer operator.
+    'solve': set-up and one warm-up solve unprofiled, then one solve of the
+    bench form between cudaProfilerStart and cudaProfilerStop."""
     import torch
     import fsigen
     from paper_1801_05648_gb300 import build as libbuild
     import paper_1801_05648_gb300 as P
     libbuild.build()
     s = fsigen.make_system(args.workload)
+    if args.kernel_only == "solve":
+        g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=8.0 if s.dim == 2 else 20.0,
+                                                               flags=0 if args.no_graphs else P.FSI_USE_GRAPHS))
+        g.precond_build(args.precision)
+        b = torch.tensor(s.rhs, device="cuda")
+        x = torch.zeros_like(b)
+        g.solve(b, x, 1e-8)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        st = g.solve(b, x, 1e-8)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"kernel_only": "solve", "workload": args.workload, "form": args.precision,
+                          "iters": st.iters, "kernel_launches": st.kernel_launches, "solve_s": st.solve_s}))
+        g.close()
+        return
     g = P.FSISolver.from_system(s)
     x = torch.tensor(s.x_exact if s.x_exact is not None else s.rhs, device="cuda")
     y = torch.empty_like(x)

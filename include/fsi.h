@@ -176,6 +176,17 @@ int fsi_apply_operator(fsi_ctx* ctx, const double* x_dev, double* y_dev);
 int fsi_apply_block(fsi_ctx* ctx, int which, const double* in_dev, double* out_dev);
 
 /*
+ * Enqueue `reps` fused Chebyshev smoothing steps (one SpMV each:
+ * r = D^-1 (b - A x); d = c1 d + c2 r; x' = x + d) on `level` (which must have a
+ * coarser level) of hierarchy `which` (0..3), in the built precision, on that
+ * level's own work vectors; returns without waiting.  This is the V-cycle's
+ * dominant kernel, exposed for timing.  *bytes_per_step (nullable) receives its
+ * algorithmic bytes: matrix values and indices, x read once, x' written, and b,
+ * D^-1, d read and d written.
+ */
+int fsi_smoother_step(fsi_ctx* ctx, int which, int level, int reps, double* bytes_per_step);
+
+/*
  * AMG hierarchy inspection (which 0..3 as above, level >= 0).
  *   info[0] levels, [1] block rows of this level, [2] block size, [3] nnz blocks,
  *   [4] aggregates formed from this level (0 on the coarsest), [5] scalar rows of

@@ -500,7 +500,7 @@ void amg_setup(Hierarchy& H, Bsr&& A0, const double* B0, int k0, const AmgParams
     k_tentative<<<div_up(nagg, 64), 64, 0, s>>>(nagg, b, k, aoff.p, mem.p, Pt.rowptr.p, B, prm.drop_tol, Pt.v64.p,
                                                 Bc.p);
     FSI_CHECK_LAUNCH();
-    Pt.tpr = choose_tpr(Pt.nnzb, Pt.nbr);
+    set_tpr(Pt);
     // ---- smoothed prolongator
     const double omega = 4.0 / (3.0 * L.lam);
     Bsr AP;
@@ -512,7 +512,7 @@ void amg_setup(Hierarchy& H, Bsr&& A0, const double* B0, int k0, const AmgParams
     k_smooth_p<<<div_up(nbr, 128), 128, 0, s>>>(nbr, b, k, L.P.rowptr.p, L.P.colind.p, AP.v64.p, L.agg.p,
                                                 Pt.rowptr.p, Pt.v64.p, L.dinv64.p, omega, L.P.v64.p);
     FSI_CHECK_LAUNCH();
-    L.P.tpr = choose_tpr(L.P.nnzb, L.P.nbr);
+    set_tpr(L.P);
     bsr_transpose(L.P, L.R, s);
     Bsr AP2, Ac;
     bsr_spgemm(L.A, L.P, AP2, s);
@@ -584,6 +584,27 @@ void cheb_apply(ChebSolver& C, const T* b, T* x, cudaStream_t s) {
   cheb_sweep<T>(C.A, dinv, C.lam, C.degree, C.ratio, C.upper, b, x, W.xb.p, W.d.p, true, s);
 }
 
+template <class T>
+double amg_smoother_steps(Hierarchy& H, int level, int reps, cudaStream_t s) {
+  require(level >= 0 && level + 1 < (int)H.levels.size(), "smoother level must have a coarser level");
+  AmgLevel& L = H.levels[level];
+  LevelWork<T>& W = work<T>(L);
+  const int64_t n = L.A.rows();
+  if (!W.zeroed) {
+    for (DBuf<T>* v : {&W.b, &W.x, &W.xb, &W.d}) FSI_CUDA(cudaMemsetAsync(v->p, 0, sizeof(T) * n, s));
+    W.zeroed = true;
+  }
+  T* cur = W.x.p;
+  T* oth = W.xb.p;
+  for (int r = 0; r < reps; ++r) {
+    spmv_cheb<T>(L.A, cur, W.b.p, dinv_of<T>(L), W.d.p, oth, T(0.5), T(0.5), s);
+    T* t = cur; cur = oth; oth = t;
+  }
+  return cheb_step_bytes(L.A, (int)sizeof(T));
+}
+
+template double amg_smoother_steps<double>(Hierarchy&, int, int, cudaStream_t);
+template double amg_smoother_steps<float>(Hierarchy&, int, int, cudaStream_t);
 template void amg_vcycle<double>(Hierarchy&, const double*, double*, cudaStream_t);
 template void amg_vcycle<float>(Hierarchy&, const float*, float*, cudaStream_t);
 template void cheb_apply<double>(ChebSolver&, const double*, double*, cudaStream_t);

@@ -41,6 +41,7 @@ struct AmgParams {
 template <class T>
 struct LevelWork {
   DBuf<T> b, x, xb, r, d;   // rhs, iterate, ping-pong iterate, residual, Chebyshev direction
+  bool zeroed = false;      // cleared once for the timing hook
 };
 
 struct AmgLevel {
@@ -71,6 +72,13 @@ struct Hierarchy {
 // Build the hierarchy of A (FP64 values, square, br == bc) with near-nullspace B
 // (device, (A.rows()) x k, node-major rows, row-major k columns).
 void amg_setup(Hierarchy& H, Bsr&& A, const double* B, int k, const AmgParams& prm, cudaStream_t s);
+// Enqueue `reps` fused Chebyshev SpMV steps on level `level` (timing hook; the
+// level's own work vectors, zeroed on first use).  Returns algorithmic bytes per step.
+template <class T> double amg_smoother_steps(Hierarchy& H, int level, int reps, cudaStream_t s);
+// Algorithmic bytes of one fused Chebyshev step on A (value size vb): the SpMV
+// (values, indices, row pointers, x once, x' written) plus b, D^-1 and d read, d written.
+inline double cheb_step_bytes(const Bsr& A, int vb) { return A.spmv_bytes(vb) + 4.0 * vb * A.rows(); }
+
 // FP32 copies of every level's matrices, diagonal and coarse inverse.
 void amg_make_fp32(Hierarchy& H, cudaStream_t s);
 // x = V(b): one V-cycle from x = 0 (x, b: level-0 sized, distinct)

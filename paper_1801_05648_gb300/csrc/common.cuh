@@ -79,7 +79,8 @@ struct Bsr {
   DBuf<int> colind;     // nnzb
   DBuf<double> v64;     // nnzb * br * bc
   DBuf<float> v32;      // optional FP32 copy
-  int tpr = 32;         // threads per block row for the SpMV, from the mean row length
+  int tpr = 32;         // threads per block row of the FP32 SpMV, from the mean row length
+  int tpr64 = 2;        // ... of the FP64 SpMV (fewer lanes: FP64 issue slots are scarce)
   int64_t rows() const { return (int64_t)nbr * br; }
   int64_t cols() const { return (int64_t)nbc * bc; }
   template <class T> const T* vals() const;
@@ -91,15 +92,36 @@ struct Bsr {
 template <> inline const double* Bsr::vals<double>() const { return v64.p; }
 template <> inline const float* Bsr::vals<float>() const { return v32.p; }
 
+// FP32 lanes per block row: about four blocks per lane (one unrolled trip of
+// the SpMV loop), at most a warp.
 inline int choose_tpr(int64_t nnzb, int nbr) {
   double mean = nbr ? (double)nnzb / nbr : 0.0;
-  if (mean >= 24) return 32;
-  if (mean >= 12) return 16;
-  if (mean >= 6) return 8;
-  return 4;
+  int t = 1;
+  while (t < 32 && mean / (2 * t) >= 4.0) t *= 2;
+  return t;
 }
 
+// FP64 lanes per block row.  The FP64 pipe of this GPU retires a small fraction
+// of the FP32 rate, so the shuffle reduction across a wide lane group would cost
+// more FP64 instructions than the products themselves; about eight blocks per
+// lane keeps the reduction (log2(tpr) adds per row entry) small next to the one
+// fused multiply-add per stored value.
+inline int choose_tpr64(int64_t nnzb, int nbr) {
+  double mean = nbr ? (double)nnzb / nbr : 0.0;
+  int t = 1;
+  while (t < 32 && mean / (2 * t) >= 8.0) t *= 2;
+  return t;
+}
+
+// Sets both lane counts of a matrix from its shape.
+inline void set_tpr(struct Bsr& A);
+
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+inline void set_tpr(Bsr& A) {
+  A.tpr = choose_tpr(A.nnzb, A.nbr);
+  A.tpr64 = choose_tpr64(A.nnzb, A.nbr);
+}
 
 // Streams and scratch shared by one context.
 struct Exec {

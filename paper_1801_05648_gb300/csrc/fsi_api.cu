@@ -232,6 +232,18 @@ int fsi_apply_block(fsi_ctx* ctx, int which, const double* in_dev, double* out_d
   });
 }
 
+int fsi_smoother_step(fsi_ctx* ctx, int which, int level, int reps, double* bytes_per_step) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::Context& C = ctx->C;
+    fsi::require(C.built, "fsi_smoother_step before fsi_precond_build");
+    fsi::require(which >= 0 && which <= 3 && reps >= 0, "bad arguments");
+    const double b = C.precision == 1 ? fsi::amg_smoother_steps<float>(C.H[which], level, reps, C.s)
+                                      : fsi::amg_smoother_steps<double>(C.H[which], level, reps, C.s);
+    if (bytes_per_step) *bytes_per_step = b;
+  });
+}
+
 int fsi_amg_info(fsi_ctx* ctx, int which, int level, int64_t info[6], double* lambda) {
   if (!ctx) return FSI_EINVAL;
   return guarded(ctx, [&] {

@@ -42,7 +42,7 @@ void alloc_pw(PrecWork<T>& W, int64_t n) {
 
 void bsr_clone(const Bsr& A, Bsr& B, cudaStream_t s) {
   B = Bsr();
-  B.nbr = A.nbr; B.nbc = A.nbc; B.br = A.br; B.bc = A.bc; B.nnzb = A.nnzb; B.tpr = A.tpr;
+  B.nbr = A.nbr; B.nbc = A.nbc; B.br = A.br; B.bc = A.bc; B.nnzb = A.nnzb; B.tpr = A.tpr; B.tpr64 = A.tpr64;
   B.rowptr.alloc(A.nbr + 1);
   B.colind.alloc(A.nnzb > 0 ? A.nnzb : 1);
   B.v64.alloc(A.nnzb > 0 ? A.nnzb * A.br * A.bc : 1);

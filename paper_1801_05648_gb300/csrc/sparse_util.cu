@@ -472,7 +472,7 @@ void extract_bsr(const Csr& A, int64_t r0, int nbr, int br, int64_t c0, int nbc,
                                                    nullptr, out.rowptr.p, out.colind.p, out.v64.p);
     FSI_CHECK_LAUNCH();
   }
-  out.tpr = choose_tpr(out.nnzb, nbr);
+  set_tpr(out);
 }
 
 void bsr_add(const Bsr& A, const Bsr& B, double alpha, Bsr& C, cudaStream_t s) {
@@ -493,7 +493,7 @@ void bsr_add(const Bsr& A, const Bsr& B, double alpha, Bsr& C, cudaStream_t s) {
                                                   C.v64.p);
     FSI_CHECK_LAUNCH();
   }
-  C.tpr = choose_tpr(C.nnzb, C.nbr);
+  set_tpr(C);
 }
 
 void bsr_transpose(const Bsr& A, Bsr& C, cudaStream_t s) {
@@ -507,7 +507,7 @@ void bsr_transpose(const Bsr& A, Bsr& C, cudaStream_t s) {
     FSI_CHECK_LAUNCH();
   }
   finalize_rowptr(cnt.p, C, s);
-  if (A.nnzb == 0) { C.tpr = 4; return; }
+  if (A.nnzb == 0) { set_tpr(C); return; }
   DBuf<int> rowof(A.nnzb), tsrc(A.nnzb);
   k_row_of_block<<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, A.rowptr.p, rowof.p);
   FSI_CHECK_LAUNCH();
@@ -518,7 +518,7 @@ void bsr_transpose(const Bsr& A, Bsr& C, cudaStream_t s) {
   FSI_CHECK_LAUNCH();
   k_gather_t<<<div_up(A.nnzb, 256), 256, 0, s>>>(A.nnzb, A.br, A.bc, tsrc.p, A.v64.p, C.v64.p);
   FSI_CHECK_LAUNCH();
-  C.tpr = choose_tpr(C.nnzb, C.nbr);
+  set_tpr(C);
 }
 
 void bsr_spgemm(const Bsr& A, const Bsr& B, Bsr& C, cudaStream_t s) {
@@ -548,7 +548,7 @@ void bsr_spgemm(const Bsr& A, const Bsr& B, Bsr& C, cudaStream_t s) {
       FSI_CHECK_LAUNCH();
     });
   }
-  C.tpr = choose_tpr(C.nnzb, C.nbr);
+  set_tpr(C);
 }
 
 void sort_segments(int nseg, const int* off, int* key, int* pay, cudaStream_t s) {

@@ -11,7 +11,7 @@ namespace {
 template <class T, int BR, int BC1, int BC2, class Epi>
 void launch(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const Epi& epi, cudaStream_t s) {
   if (A1.nbr == 0) return;
-  const int tpr = A1.tpr;
+  const int tpr = sizeof(T) == 8 ? A1.tpr64 : A1.tpr;
   const int threads = 256;
   const int blocks = div_up((int64_t)A1.nbr * tpr, threads);
   const T* v2 = nullptr; const int* rp2 = nullptr; const int* ci2 = nullptr;

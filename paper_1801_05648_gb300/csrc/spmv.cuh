@@ -1,11 +1,15 @@
 // Block-sparse (BSR) matrix-vector products with fused epilogues.
 //
-// A group of `tpr` lanes (4..32, a power of two inside one warp) owns one block
+// A group of `tpr` lanes (1..32, a power of two inside one warp) owns one block
 // row: lane l reads blocks l, l+tpr, ... of the row, so the lanes of a group
 // stream consecutive blocks (row-major br x bc values, 16-byte vector loads
 // whenever the block size allows) and the block-column indices coalesced; the
-// x entries are gathered through the read-only path.  The group reduces its br
-// partial sums with shuffles and lane 0 applies the epilogue.  An optional
+// x entries are gathered through the read-only path.  Each lane issues several
+// blocks' loads before multiplying (bytes in flight hide the DRAM latency).
+// The group reduces its br partial sums with shuffles and lane 0 applies the
+// epilogue.  FP32 groups hold about four blocks per lane; FP64 groups fewer
+// lanes (about eight blocks each), because on this GPU the FP64 pipe, not DRAM,
+// limits a wide FP64 reduction.  An optional
 // second matrix with the same block rows (e.g. the d x 1 pressure columns next
 // to the d x d vector columns of the monolithic operator) is accumulated into
 // the same sums, so one pass covers every column class of a row.
@@ -123,6 +127,49 @@ struct EpiDinv {
 };
 
 // ------------------------------------------------------------------ kernel
+// Unroll depth: blocks each lane has in flight per trip (register budget).
+template <class T, int BR, int BC>
+constexpr int unroll_for() {
+  return (int)(sizeof(T) * (BR * BC + BC)) <= 64 ? 4 : 2;
+}
+
+// acc += sum over the lane's share of row entries [kb, ke) of block * x[col].
+// The U column indices are loaded first, then the U blocks and x segments, so a
+// lane keeps U independent requests in flight before it multiplies.
+template <class T, int BR, int BC>
+__device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const T* __restrict__ v,
+                                               const T* __restrict__ x, int kb, int ke, int lane, int tpr,
+                                               T* acc) {
+  constexpr int U = unroll_for<T, BR, BC>();
+  for (int k0 = kb + lane; k0 < ke; k0 += tpr * U) {
+    int col[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * tpr;
+      col[u] = k < ke ? __ldcs(ci + k) : -1;
+    }
+    T blk[U][BR * BC], xv[U][BC];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (col[u] >= 0) {
+        load_stream<T, BR * BC>(v + (size_t)(k0 + u * tpr) * (BR * BC), blk[u]);
+        load_gather<T, BC>(x + (size_t)col[u] * BC, xv[u]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < BR * BC; ++t) blk[u][t] = T(0);
+#pragma unroll
+        for (int t = 0; t < BC; ++t) xv[u][t] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < BR; ++i)
+#pragma unroll
+        for (int j = 0; j < BC; ++j) acc[i] += blk[u][i * BC + j] * xv[u][j];
+  }
+}
+
 template <class T, int BR, int BC1, int BC2, class Epi>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
     const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, const T* __restrict__ x1,
@@ -136,30 +183,8 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
 #pragma unroll
   for (int i = 0; i < BR; ++i) acc[i] = T(0);
   if (valid) {
-    const int kb = rp1[row], ke = rp1[row + 1];
-    for (int k = kb + lane; k < ke; k += tpr) {
-      const int c = __ldcs(ci1 + k);
-      T blk[BR * BC1], xv[BC1];
-      load_stream<T, BR * BC1>(v1 + (size_t)k * (BR * BC1), blk);
-      load_gather<T, BC1>(x1 + (size_t)c * BC1, xv);
-#pragma unroll
-      for (int i = 0; i < BR; ++i)
-#pragma unroll
-        for (int j = 0; j < BC1; ++j) acc[i] += blk[i * BC1 + j] * xv[j];
-    }
-    if constexpr (BC2 > 0) {
-      const int kb2 = rp2[row], ke2 = rp2[row + 1];
-      for (int k = kb2 + lane; k < ke2; k += tpr) {
-        const int c = __ldcs(ci2 + k);
-        T blk[BR * BC2], xv[BC2];
-        load_stream<T, BR * BC2>(v2 + (size_t)k * (BR * BC2), blk);
-        load_gather<T, BC2>(x2 + (size_t)c * BC2, xv);
-#pragma unroll
-        for (int i = 0; i < BR; ++i)
-#pragma unroll
-          for (int j = 0; j < BC2; ++j) acc[i] += blk[i * BC2 + j] * xv[j];
-      }
-    }
+    row_accumulate<T, BR, BC1>(ci1, v1, x1, rp1[row], rp1[row + 1], lane, tpr, acc);
+    if constexpr (BC2 > 0) row_accumulate<T, BR, BC2>(ci2, v2, x2, rp2[row], rp2[row + 1], lane, tpr, acc);
   }
   for (int off = tpr >> 1; off > 0; off >>= 1)
 #pragma unroll

@@ -25,7 +25,7 @@ BLOCKS = {"mesh": 0, "solid_schur": 1, "fluid_velocity": 2, "pressure_schur": 3,
 
 # Every symbol include/fsi.h declares.
 EXPORTED = ["fsi_default_params", "fsi_setup", "fsi_precond_build", "fsi_solve", "fsi_free", "fsi_last_error",
-            "fsi_apply_operator", "fsi_apply_block", "fsi_amg_info", "fsi_amg_export"]
+            "fsi_apply_operator", "fsi_apply_block", "fsi_smoother_step", "fsi_amg_info", "fsi_amg_export"]
 
 
 class FSIError(RuntimeError):
@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH):
     lib.fsi_apply_operator.restype = ctypes.c_int
     lib.fsi_apply_block.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.fsi_apply_block.restype = ctypes.c_int
+    lib.fsi_smoother_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, f64p]
+    lib.fsi_smoother_step.restype = ctypes.c_int
     lib.fsi_amg_info.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p, f64p]
     lib.fsi_amg_info.restype = ctypes.c_int
     lib.fsi_amg_export.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
@@ -202,6 +204,13 @@ class FSISolver:
 
     def _sync(self):
         self.stream.synchronize()
+
+    def smoother_steps(self, which, level, reps):
+        """Enqueue `reps` Chebyshev SpMV steps on a hierarchy level (no wait); returns bytes per step."""
+        b = ctypes.c_double()
+        self._order()
+        self._check(self._lib.fsi_smoother_step(self._h, BLOCKS.get(which, which), level, reps, ctypes.byref(b)))
+        return b.value
 
     def amg_info(self, which, level=0):
         info = np.zeros(6, np.int64)
