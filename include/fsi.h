@@ -202,6 +202,26 @@ int fsi_amg_info(fsi_ctx* ctx, int which, int level, int64_t info[6], double* la
  */
 int fsi_amg_export(fsi_ctx* ctx, int which, int level, int what, void* dst);
 
+/*
+ * fsi_mass_solve_noalloc - out = A_uu^-1 in, the solid-mass Chebyshev solve of
+ * fsi_apply_block(ctx, 4, ...) in FP64 (whatever precision was built), for
+ * callers that cannot allocate device memory when they call: code running
+ * while its stream is captured into a CUDA graph (cudaMalloc is not permitted
+ * there) or code whose device memory is owned by another allocator.  The paper
+ * has no counterpart; it is an interface convenience.
+ *   in_dev, out_dev  device, one double per s_u DOF (block_offsets[3] - [2])
+ * Allocates nothing: its two scratch vectors live in a static device array of
+ * 2 x 2^20 doubles (16 MiB) that every GPU loading the library keeps until the
+ * process exits, so the solid block may have at most 2^20 displacement DOFs
+ * (larger blocks return FSI_EINVAL).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on the
+ * GPU (other streams or devices' contexts on the same device) race on it.  Its
+ * contents are fully overwritten by each call before they are read.  Enqueued on
+ * the context's stream without waiting.
+ */
+int fsi_mass_solve_noalloc(fsi_ctx* ctx, const double* in_dev, double* out_dev);
+
 #ifdef __cplusplus
 }
 #endif

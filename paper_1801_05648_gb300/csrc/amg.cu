@@ -605,6 +605,11 @@ double amg_smoother_steps(Hierarchy& H, int level, int reps, cudaStream_t s) {
 
 template double amg_smoother_steps<double>(Hierarchy&, int, int, cudaStream_t);
 template double amg_smoother_steps<float>(Hierarchy&, int, int, cudaStream_t);
+void cheb_apply_scratch(const ChebSolver& C, const double* b, double* x, double* xb, double* d, cudaStream_t s) {
+  if (C.A.nbr == 0) return;
+  cheb_sweep<double>(C.A, C.dinv64.p, C.lam, C.degree, C.ratio, C.upper, b, x, xb, d, true, s);
+}
+
 template void amg_vcycle<double>(Hierarchy&, const double*, double*, cudaStream_t);
 template void amg_vcycle<float>(Hierarchy&, const float*, float*, cudaStream_t);
 template void cheb_apply<double>(ChebSolver&, const double*, double*, cudaStream_t);

@@ -99,6 +99,9 @@ struct ChebSolver {
 void cheb_setup(ChebSolver& C, Bsr&& A, int degree, double ratio, double upper, int power_iters, cudaStream_t s);
 void cheb_make_fp32(ChebSolver& C, cudaStream_t s);
 template <class T> void cheb_apply(ChebSolver& C, const T* b, T* x, cudaStream_t s);
+// Same polynomial, FP64, with caller-provided scratch vectors xb and d (each of
+// C.A.rows() entries) instead of the solver's own work vectors.
+void cheb_apply_scratch(const ChebSolver& C, const double* b, double* x, double* xb, double* d, cudaStream_t s);
 
 // |lambda_max(D^-1 A)| estimate by power iteration (see above), FP64.
 double power_lambda(const Bsr& A, const double* dinv, int iters, int stream_id, cudaStream_t s);

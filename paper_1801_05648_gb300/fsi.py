@@ -25,7 +25,8 @@ BLOCKS = {"mesh": 0, "solid_schur": 1, "fluid_velocity": 2, "pressure_schur": 3,
 
 # Every symbol include/fsi.h declares.
 EXPORTED = ["fsi_default_params", "fsi_setup", "fsi_precond_build", "fsi_solve", "fsi_free", "fsi_last_error",
-            "fsi_apply_operator", "fsi_apply_block", "fsi_smoother_step", "fsi_amg_info", "fsi_amg_export"]
+            "fsi_apply_operator", "fsi_apply_block", "fsi_smoother_step", "fsi_amg_info", "fsi_amg_export",
+            "fsi_mass_solve_noalloc"]
 
 
 class FSIError(RuntimeError):
@@ -104,6 +105,8 @@ def load_library(path: str = LIB_PATH):
     lib.fsi_amg_info.restype = ctypes.c_int
     lib.fsi_amg_export.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
     lib.fsi_amg_export.restype = ctypes.c_int
+    lib.fsi_mass_solve_noalloc.argtypes = [vp, vp, vp]
+    lib.fsi_mass_solve_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -204,6 +207,13 @@ class FSISolver:
 
     def _sync(self):
         self.stream.synchronize()
+
+    def mass_solve_noalloc(self, inp, out, sync=True):
+        """A_uu^-1 in through fsi_mass_solve_noalloc (static device scratch, no allocation)."""
+        self._order()
+        self._check(self._lib.fsi_mass_solve_noalloc(self._h, _dev_ptr(inp), _dev_ptr(out)))
+        if sync:
+            self._sync()
 
     def smoother_steps(self, which, level, reps):
         """Enqueue `reps` Chebyshev SpMV steps on a hierarchy level (no wait); returns bytes per step."""
