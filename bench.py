@@ -404,8 +404,8 @@ def bench_ours(args):
         "precond_build_s_fp64": statistics.mean(build_s),
         "solve_algorithmic_gbs": bytes_per_solve / (ms / 1e3) / 1e9,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
-        "roofline": {"kernel": "k_bsr_spmv<float,2,2,0,EpiCheb>: fused Chebyshev step of the FP32 V-cycle "
-                               "(level 0 of the mesh and fluid-velocity hierarchies)",
+        "roofline": {"kernel": f"k_bsr_spmv<float,{systems[0].dim},{systems[0].dim},0,EpiCheb>: fused Chebyshev "
+                               "step of the FP32 V-cycle (level 0 of the mesh and fluid-velocity hierarchies)",
                      "bound": "hbm", "achieved": cheb_achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": cheb_achieved / peak, "traffic": cheb_traffic,
                      "algorithmic_bytes": cheb_bytes / cheb_launches, "launch_us": cheb_s / cheb_launches * 1e6},

@@ -92,26 +92,21 @@ struct Bsr {
 template <> inline const double* Bsr::vals<double>() const { return v64.p; }
 template <> inline const float* Bsr::vals<float>() const { return v32.p; }
 
-// FP32 lanes per block row: about four blocks per lane (one unrolled trip of
-// the SpMV loop), at most a warp.
-inline int choose_tpr(int64_t nnzb, int nbr) {
-  double mean = nbr ? (double)nnzb / nbr : 0.0;
+// Lanes per block row.  Enough lanes that the launch fills about one wave of
+// the GPU (152 SMs x 2048 threads) when the rows are long enough, while each
+// lane keeps at least `min_per_lane` blocks.  FP32 rows stop at two blocks per
+// lane.  FP64 rows keep at least eight: the FP64 pipe of this GPU retires a
+// small fraction of the FP32 rate, and the shuffle reduction across a wide lane
+// group would cost more FP64 instructions than the products themselves.
+inline int lanes_for(int64_t nnzb, int nbr, double min_per_lane) {
+  const double mean = nbr ? (double)nnzb / nbr : 0.0;
+  const double target_threads = 152.0 * 2048.0;
   int t = 1;
-  while (t < 32 && mean / (2 * t) >= 4.0) t *= 2;
+  while (t < 32 && (double)nbr * t < target_threads && mean / (2 * t) >= min_per_lane) t *= 2;
   return t;
 }
-
-// FP64 lanes per block row.  The FP64 pipe of this GPU retires a small fraction
-// of the FP32 rate, so the shuffle reduction across a wide lane group would cost
-// more FP64 instructions than the products themselves; about eight blocks per
-// lane keeps the reduction (log2(tpr) adds per row entry) small next to the one
-// fused multiply-add per stored value.
-inline int choose_tpr64(int64_t nnzb, int nbr) {
-  double mean = nbr ? (double)nnzb / nbr : 0.0;
-  int t = 1;
-  while (t < 32 && mean / (2 * t) >= 8.0) t *= 2;
-  return t;
-}
+inline int choose_tpr(int64_t nnzb, int nbr) { return lanes_for(nnzb, nbr, 2.0); }
+inline int choose_tpr64(int64_t nnzb, int nbr) { return lanes_for(nnzb, nbr, 8.0); }
 
 // Sets both lane counts of a matrix from its shape.
 inline void set_tpr(struct Bsr& A);

@@ -36,7 +36,7 @@ template <class T>
 void alloc_pw(PrecWork<T>& W, int64_t n) {
   if (W.ready) return;
   W.in.alloc(n); W.out.alloc(n); W.a2_t.alloc(n); W.a2_u.alloc(n);
-  W.s3_y.alloc(n); W.s3_t.alloc(n); W.mv_res.alloc(n); W.mv_cor.alloc(n);
+  W.s3_y.alloc(n); W.s3_t.alloc(n);
   W.ready = true;
 }
 
@@ -180,60 +180,68 @@ void upload(DBuf<double>& dst, const std::vector<double>& src, cudaStream_t s) {
 
 // ------------------------------------------------------------------ sub-solves
 // x = inverse of hierarchy h applied with `nc` V-cycles: x = V(b); x += V(b - A x) ...
+// The residual and correction of the repeated cycles use the level-0 work vectors
+// b and x of that hierarchy (a V-cycle leaves them untouched on level 0), so
+// sub-solves on different hierarchies can run concurrently.
 template <class T>
-void amg_solve(Context& C, int h, int nc, const T* b, T* x) {
+void amg_solve(Context& C, int h, int nc, const T* b, T* x, cudaStream_t st) {
   Hierarchy& H = C.H[h];
-  amg_vcycle<T>(H, b, x, C.s);
+  amg_vcycle<T>(H, b, x, st);
   if (nc <= 1) return;
-  PrecWork<T>& W = pwork<T>(C);
   const Bsr& A = H.levels[0].A;
   const int64_t nn = A.rows();
+  LevelWork<T>& W = [&]() -> LevelWork<T>& {
+    if constexpr (sizeof(T) == 8) return H.levels[0].w64; else return H.levels[0].w32;
+  }();
   for (int c = 1; c < nc; ++c) {
-    spmv2_resid<T>(A, x, nullptr, nullptr, b, W.mv_res.p, C.s);
-    amg_vcycle<T>(H, W.mv_res.p, W.mv_cor.p, C.s);
-    axpby<T>(nn, T(1), W.mv_cor.p, T(1), x, C.s);
+    spmv2_resid<T>(A, x, nullptr, nullptr, b, W.b.p, st);
+    amg_vcycle<T>(H, W.b.p, W.x.p, st);
+    axpby<T>(nn, T(1), W.x.p, T(1), x, st);
   }
 }
 
 template <class T>
-void mesh_solve(Context& C, const T* r, T* x) { amg_solve<T>(C, 0, C.prm.vc_mesh, r, x); }
+void mesh_solve(Context& C, const T* r, T* x, cudaStream_t st) { amg_solve<T>(C, 0, C.prm.vc_mesh, r, x, st); }
 
 // Alg. 3: solid sub-solve on (r_v, r_u) -> (x_v, x_u)
 template <class T>
-void solid_solve(Context& C, const T* r, T* x) {
+void solid_solve(Context& C, const T* r, T* x, cudaStream_t st) {
   PrecWork<T>& W = pwork<T>(C);
   const int64_t nsv = C.off[2] - C.off[1];
   const T* r_v = r;
   const T* r_u = r + nsv;
   T* x_v = x;
   T* x_u = x + nsv;
-  cheb_apply<T>(C.mass, r_u, W.s3_y.p, C.s);                                  // y = A_uu^-1 r_u
-  spmv2_resid<T>(C.A_vu, W.s3_y.p, nullptr, nullptr, r_v, W.s3_t.p, C.s);     // t = r_v - A_vu y
-  amg_solve<T>(C, 1, C.prm.vc_solid, W.s3_t.p, x_v);                          // x_v = S_hat^-1 t
-  spmv2_resid<T>(C.A_uv, x_v, nullptr, nullptr, r_u, W.s3_t.p, C.s);          // t = r_u - A_uv x_v
-  cheb_apply<T>(C.mass, W.s3_t.p, x_u, C.s);                                  // x_u = A_uu^-1 t
+  cheb_apply<T>(C.mass, r_u, W.s3_y.p, st);                                   // y = A_uu^-1 r_u
+  spmv2_resid<T>(C.A_vu, W.s3_y.p, nullptr, nullptr, r_v, W.s3_t.p, st);      // t = r_v - A_vu y
+  amg_solve<T>(C, 1, C.prm.vc_solid, W.s3_t.p, x_v, st);                      // x_v = S_hat^-1 t
+  spmv2_resid<T>(C.A_uv, x_v, nullptr, nullptr, r_u, W.s3_t.p, st);           // t = r_u - A_uv x_v
+  cheb_apply<T>(C.mass, W.s3_t.p, x_u, st);                                   // x_u = A_uu^-1 t
 }
 
 // fluid sub-solve on (r_v, r_p) -> (x_v, x_p)
 template <class T>
-void fluid_solve(Context& C, const T* r, T* x) {
+void fluid_solve(Context& C, const T* r, T* x, cudaStream_t st) {
   PrecWork<T>& W = pwork<T>(C);
   const int64_t nfv = C.off[4] - C.off[3];
   const T* r_v = r;
   const T* r_p = r + nfv;
   T* x_v = x;
   T* x_p = x + nfv;
-  amg_solve<T>(C, 2, C.prm.vc_fluid, r_v, W.s3_y.p);                          // y = A_ff^-1 r_v
-  spmv2_resid<T>(C.B_pv, W.s3_y.p, nullptr, nullptr, r_p, W.s3_t.p, C.s);     // t = r_p - B_pv y
-  amg_solve<T>(C, 3, C.prm.vc_pressure, W.s3_t.p, x_p);                       // x_p = S_p^-1 t
-  spmv2_resid<T>(C.B_vp, x_p, nullptr, nullptr, r_v, W.s3_t.p, C.s);          // t = r_v - B_vp x_p
-  amg_solve<T>(C, 2, C.prm.vc_fluid, W.s3_t.p, x_v);                          // x_v = A_ff^-1 t
+  amg_solve<T>(C, 2, C.prm.vc_fluid, r_v, W.s3_y.p, st);                      // y = A_ff^-1 r_v
+  spmv2_resid<T>(C.B_pv, W.s3_y.p, nullptr, nullptr, r_p, W.s3_t.p, st);      // t = r_p - B_pv y
+  amg_solve<T>(C, 3, C.prm.vc_pressure, W.s3_t.p, x_p, st);                   // x_p = S_p^-1 t
+  spmv2_resid<T>(C.B_vp, x_p, nullptr, nullptr, r_v, W.s3_t.p, st);           // t = r_v - B_vp x_p
+  amg_solve<T>(C, 2, C.prm.vc_fluid, W.s3_t.p, x_v, st);                      // x_v = A_ff^-1 t
 }
 
 }  // namespace
 
 Context::~Context() {
   if (iter_graph) cudaGraphExecDestroy(iter_graph);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (s2) cudaStreamDestroy(s2);
   if (pinned) cudaFreeHost(pinned);
   if (pinned_j) cudaFreeHost(pinned_j);
   if (own_stream && s) cudaStreamDestroy(s);
@@ -242,6 +250,9 @@ Context::~Context() {
 void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, const double* vals,
                    const double* solid_coords) {
   auto t0 = clk::now();
+  FSI_CUDA(cudaStreamCreateWithFlags(&C.s2, cudaStreamNonBlocking));
+  FSI_CUDA(cudaEventCreateWithFlags(&C.ev_fork, cudaEventDisableTiming));
+  FSI_CUDA(cudaEventCreateWithFlags(&C.ev_join, cudaEventDisableTiming));
   const int d = C.dim;
   const int64_t* o = C.off;
   Csr A;
@@ -347,33 +358,38 @@ void precond_apply(Context& C, const T* r, T* z) {
   T* z_s = z + o[1];
   T* z_f = z + o[3];
   const int64_t nfv = o[4] - o[3], ns = o[3] - o[1], nm = o[1] - o[0];
-  // 1-2
-  mesh_solve<T>(C, r_m, z_m);
-  solid_solve<T>(C, r_s, z_s);
+  // 1-2: independent, the mesh solve runs on the second stream (a parallel
+  // branch when captured into a graph)
+  FSI_CUDA(cudaEventRecord(C.ev_fork, C.s));
+  FSI_CUDA(cudaStreamWaitEvent(C.s2, C.ev_fork, 0));
+  mesh_solve<T>(C, r_m, z_m, C.s2);
+  solid_solve<T>(C, r_s, z_s, C.s);
+  FSI_CUDA(cudaEventRecord(C.ev_join, C.s2));
+  FSI_CUDA(cudaStreamWaitEvent(C.s, C.ev_join, 0));
   // 3: t_f = r_f - C_fm x_m - C_fs x_s  (x_m, x_s contiguous), x_f = F^-1 t_f
   spmv2_resid<T>(C.C_fv_ms, z, nullptr, nullptr, r_f, W.a2_t.p, C.s);
   spmv2_resid<T>(C.C_p_ms, z, nullptr, nullptr, r_f + nfv, W.a2_t.p + nfv, C.s);
-  fluid_solve<T>(C, W.a2_t.p, z_f);
+  fluid_solve<T>(C, W.a2_t.p, z_f, C.s);
   // 4: x_s -= S^-1 C_sf x_f
   spmv2_axpby<T>(C.C_sv_f, z_f, &C.C_sv_p, z_f + nfv, T(1), T(0), W.a2_t.p, C.s);
-  solid_solve<T>(C, W.a2_t.p, W.a2_u.p);
+  solid_solve<T>(C, W.a2_t.p, W.a2_u.p, C.s);
   axpby<T>(ns, T(-1), W.a2_u.p, T(1), z_s, C.s);
   // 5: x_m -= M^-1 C_ms x_s
   spmv_axpby<T>(C.C_ms, z_s, T(1), T(0), W.a2_t.p, C.s);
-  mesh_solve<T>(C, W.a2_t.p, W.a2_u.p);
+  mesh_solve<T>(C, W.a2_t.p, W.a2_u.p, C.s);
   axpby<T>(nm, T(-1), W.a2_u.p, T(1), z_m, C.s);
 }
 
 template <class T>
 void apply_block(Context& C, int which, const T* in, T* out) {
   switch (which) {
-    case 0: amg_solve<T>(C, 0, C.prm.vc_mesh, in, out); break;
-    case 1: amg_solve<T>(C, 1, C.prm.vc_solid, in, out); break;
-    case 2: amg_solve<T>(C, 2, C.prm.vc_fluid, in, out); break;
-    case 3: amg_solve<T>(C, 3, C.prm.vc_pressure, in, out); break;
+    case 0: amg_solve<T>(C, 0, C.prm.vc_mesh, in, out, C.s); break;
+    case 1: amg_solve<T>(C, 1, C.prm.vc_solid, in, out, C.s); break;
+    case 2: amg_solve<T>(C, 2, C.prm.vc_fluid, in, out, C.s); break;
+    case 3: amg_solve<T>(C, 3, C.prm.vc_pressure, in, out, C.s); break;
     case 4: cheb_apply<T>(C.mass, in, out, C.s); break;
-    case 5: solid_solve<T>(C, in, out); break;
-    case 6: fluid_solve<T>(C, in, out); break;
+    case 5: solid_solve<T>(C, in, out, C.s); break;
+    case 6: fluid_solve<T>(C, in, out, C.s); break;
     case 7: precond_apply<T>(C, in, out); break;
     default: throw Error(EINVAL_, "apply_block: unknown block");
   }

@@ -28,13 +28,14 @@ struct PrecWork {
   DBuf<T> in, out;            // fixed input/output of P^-1 (length n)
   DBuf<T> a2_t, a2_u;         // Alg. 2 temporaries
   DBuf<T> s3_y, s3_t;         // Alg. 3 / fluid Schur temporaries
-  DBuf<T> mv_res, mv_cor;     // repeated V-cycles
   bool ready = false;
 };
 
 struct Context {
   cudaStream_t s = nullptr;
   bool own_stream = false;
+  cudaStream_t s2 = nullptr;              // second branch of Alg. 2 (mesh solve next to the solid solve)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int dim = 2;
   int64_t n = 0;
   int64_t off[6] = {0, 0, 0, 0, 0, 0};

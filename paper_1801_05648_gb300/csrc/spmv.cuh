@@ -6,10 +6,9 @@
 // whenever the block size allows) and the block-column indices coalesced; the
 // x entries are gathered through the read-only path.  Each lane issues several
 // blocks' loads before multiplying (bytes in flight hide the DRAM latency).
-// The group reduces its br partial sums with shuffles and lane 0 applies the
-// epilogue.  FP32 groups hold about four blocks per lane; FP64 groups fewer
-// lanes (about eight blocks each), because on this GPU the FP64 pipe, not DRAM,
-// limits a wide FP64 reduction.  An optional
+// Lane 0 loads its row's own epilogue operands first, then the group reduces its
+// br partial sums with shuffles and lane 0 applies the epilogue.  The lane count
+// is chosen per matrix and precision (see lanes_for in common.cuh).  An optional
 // second matrix with the same block rows (e.g. the d x 1 pressure columns next
 // to the d x d vector columns of the monolithic operator) is accumulated into
 // the same sums, so one pass covers every column class of a row.
@@ -65,17 +64,26 @@ __device__ __forceinline__ void load_gather(const T* __restrict__ p, T* out) {
 }
 
 // ------------------------------------------------------------------ epilogues
+// Each epilogue loads its row's own operands (load) before the row product is
+// accumulated, so those loads overlap the gathers, and combines them (store).
+
 // y = alpha * (A x) + beta * y   (y not read when beta == 0)
 template <class T, int BR>
 struct EpiAxpby {
   T* y; T alpha; T beta;
-  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+  struct Pre { T y[BR]; };
+  __device__ __forceinline__ Pre load(int row) const {
+    Pre p;
+#pragma unroll
+    for (int i = 0; i < BR; ++i) p.y[i] = beta != T(0) ? y[(size_t)row * BR + i] : T(0);
+    return p;
+  }
+  __device__ __forceinline__ void store(int row, const T* acc, const Pre& p) const {
 #pragma unroll
     for (int i = 0; i < BR; ++i) {
-      T* yy = y + (size_t)row * BR + i;
       T v = alpha * acc[i];
-      if (beta != T(0)) v += beta * *yy;
-      *yy = v;
+      if (beta != T(0)) v += beta * p.y[i];
+      y[(size_t)row * BR + i] = v;
     }
   }
 };
@@ -84,12 +92,16 @@ struct EpiAxpby {
 template <class T, int BR>
 struct EpiResid {
   const T* b; T* r;
-  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+  struct Pre { T b[BR]; };
+  __device__ __forceinline__ Pre load(int row) const {
+    Pre p;
 #pragma unroll
-    for (int i = 0; i < BR; ++i) {
-      size_t k = (size_t)row * BR + i;
-      r[k] = b[k] - acc[i];
-    }
+    for (int i = 0; i < BR; ++i) p.b[i] = b[(size_t)row * BR + i];
+    return p;
+  }
+  __device__ __forceinline__ void store(int row, const T* acc, const Pre& p) const {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) r[(size_t)row * BR + i] = p.b[i] - acc[i];
   }
 };
 
@@ -100,15 +112,28 @@ struct EpiResid {
 template <class T, int BR>
 struct EpiCheb {
   const T* b; const T* dinv; const T* x; T* d; T* xo; T c1; T c2;
-  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+  struct Pre { T b[BR], dinv[BR], x[BR], d[BR]; };
+  __device__ __forceinline__ Pre load(int row) const {
+    Pre p;
 #pragma unroll
     for (int i = 0; i < BR; ++i) {
-      size_t k = (size_t)row * BR + i;
-      T r = dinv[k] * (b[k] - acc[i]);
+      const size_t k = (size_t)row * BR + i;
+      p.b[i] = b[k];
+      p.dinv[i] = dinv[k];
+      p.x[i] = x[k];
+      p.d[i] = c1 != T(0) ? d[k] : T(0);
+    }
+    return p;
+  }
+  __device__ __forceinline__ void store(int row, const T* acc, const Pre& p) const {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      const size_t k = (size_t)row * BR + i;
+      const T r = p.dinv[i] * (p.b[i] - acc[i]);
       T dn = c2 * r;
-      if (c1 != T(0)) dn += c1 * d[k];
+      if (c1 != T(0)) dn += c1 * p.d[i];
       d[k] = dn;
-      xo[k] = x[k] + dn;
+      xo[k] = p.x[i] + dn;
     }
   }
 };
@@ -117,19 +142,23 @@ struct EpiCheb {
 template <class T, int BR>
 struct EpiDinv {
   const T* dinv; T* y;
-  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+  struct Pre { T dinv[BR]; };
+  __device__ __forceinline__ Pre load(int row) const {
+    Pre p;
 #pragma unroll
-    for (int i = 0; i < BR; ++i) {
-      size_t k = (size_t)row * BR + i;
-      y[k] = dinv[k] * acc[i];
-    }
+    for (int i = 0; i < BR; ++i) p.dinv[i] = dinv[(size_t)row * BR + i];
+    return p;
+  }
+  __device__ __forceinline__ void store(int row, const T* acc, const Pre& p) const {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) y[(size_t)row * BR + i] = p.dinv[i] * acc[i];
   }
 };
 
 // ------------------------------------------------------------------ kernel
 // Unroll depth: blocks each lane has in flight per trip (register budget).
 template <class T, int BR, int BC>
-constexpr int unroll_for() {
+__host__ __device__ constexpr int unroll_for() {
   return (int)(sizeof(T) * (BR * BC + BC)) <= 64 ? 4 : 2;
 }
 
@@ -182,6 +211,8 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
   T acc[BR];
 #pragma unroll
   for (int i = 0; i < BR; ++i) acc[i] = T(0);
+  typename Epi::Pre pre;
+  if (valid && lane == 0) pre = epi.load(row);
   if (valid) {
     row_accumulate<T, BR, BC1>(ci1, v1, x1, rp1[row], rp1[row + 1], lane, tpr, acc);
     if constexpr (BC2 > 0) row_accumulate<T, BR, BC2>(ci2, v2, x2, rp2[row], rp2[row + 1], lane, tpr, acc);
@@ -189,7 +220,7 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
   for (int off = tpr >> 1; off > 0; off >>= 1)
 #pragma unroll
     for (int i = 0; i < BR; ++i) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off, tpr);
-  if (valid && lane == 0) epi(row, acc);
+  if (valid && lane == 0) epi.store(row, acc, pre);
 }
 
 // ------------------------------------------------------------------ host API
