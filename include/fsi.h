@@ -53,13 +53,16 @@ enum { FSI_FP64 = 0, FSI_FP32_AMG = 1 };
 enum {
   FSI_X0_GIVEN = 1,        /* fsi_solve starts from the x passed in (else from 0) */
   FSI_USE_GRAPHS = 2,      /* replay each FGMRES iteration as one captured CUDA graph */
-  FSI_NO_RIGID_MODES = 4   /* solid AMG with translations only, even when coordinates are given */
+  FSI_NO_RIGID_MODES = 4,  /* solid AMG with translations only, even when coordinates are given */
+  FSI_CLUSTER_COARSE = 8   /* run the coarse AMG levels (matrices <= 6 MB) of each V-cycle in one
+                              16-CTA thread-block-cluster launch instead of one launch per step
+                              (fewer launches, but slower on the 256x128 case: 26.7 vs 15.7 ms) */
 };
 
 typedef struct fsi_params {
   int restart;              /* FGMRES restart length m (default 100) */
   int maxit;                /* maximum FGMRES iterations (default 1000) */
-  int flags;                /* FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES */
+  int flags;                /* FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE */
   double dt_theta;          /* c = dt*theta of the solid Schur complement S_hat = A_vv + c A_vu (0.01) */
   /* smoothed-aggregation AMG */
   double strength_theta;    /* strength threshold on node-block Frobenius norms (0.08) */

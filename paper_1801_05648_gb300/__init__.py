@@ -5,7 +5,9 @@ The solver lives in ``libfsi.so`` (CUDA, sm_103a) behind the C ABI of
 ``include/fsi.h``; ``fsi.py`` is its ctypes binding.
 """
 from .fsi import (FSISolver, FSIError, Params, SolveStats, default_params, load_library, BLOCKS, EXPORTED,
-                  FSI_FP64, FSI_FP32_AMG, FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, LIB_PATH)
+                  FSI_FP64, FSI_FP32_AMG, FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE,
+                  LIB_PATH)
 
 __all__ = ["FSISolver", "FSIError", "Params", "SolveStats", "default_params", "load_library", "BLOCKS", "EXPORTED",
-           "FSI_FP64", "FSI_FP32_AMG", "FSI_X0_GIVEN", "FSI_USE_GRAPHS", "FSI_NO_RIGID_MODES", "LIB_PATH"]
+           "FSI_FP64", "FSI_FP32_AMG", "FSI_X0_GIVEN", "FSI_USE_GRAPHS", "FSI_NO_RIGID_MODES",
+           "FSI_CLUSTER_COARSE", "LIB_PATH"]

@@ -339,6 +339,15 @@ void vcycle_level(Hierarchy& H, int l, const T* b, T* x, cudaStream_t s) {
     FSI_CHECK_LAUNCH();
     return;
   }
+  {
+    const CoarseRun<T>& run = [&]() -> const CoarseRun<T>& {
+      if constexpr (sizeof(T) == 8) return H.crun64; else return H.crun32;
+    }();
+    if (H.use_cluster && run.first == l && run.cluster > 0) {
+      coarse_vcycle<T>(run, b, x, s);
+      return;
+    }
+  }
   AmgLevel& L = H.levels[l];
   LevelWork<T>& W = work<T>(L);
   const AmgParams& p = H.prm;
@@ -533,6 +542,23 @@ void amg_setup(Hierarchy& H, Bsr&& A0, const double* B0, int k0, const AmgParams
   bsr_to_dense(C.A, dense.p, s);
   require(dense_inverse((int)nc, dense.p, H.cinv64.p, s), "amg_setup: singular coarsest matrix");
   FSI_CUDA(cudaStreamSynchronize(s));
+  const int first = coarse_first_level(H, 8);
+  if (first >= 0 && H.use_cluster) coarse_plan_build<double>(H, first, H.crun64, s);
+}
+
+int coarse_first_level(const Hierarchy& H, int value_bytes) {
+  const int L = (int)H.levels.size();
+  if (L > kCoarseMaxLevels + 64) return -1;
+  int first = L - 1;
+  while (first - 1 >= 0) {
+    const Bsr& A = H.levels[first - 1].A;
+    const double bytes = (double)A.nnzb * A.br * A.bc * value_bytes;
+    if (bytes > kCoarseMaxBytes) break;
+    --first;
+  }
+  if (first >= L - 1) return -1;                  // only the coarsest: nothing to merge
+  if (L - first > kCoarseMaxLevels) first = L - kCoarseMaxLevels;
+  return first;
 }
 
 void amg_make_fp32(Hierarchy& H, cudaStream_t s) {
@@ -546,6 +572,8 @@ void amg_make_fp32(Hierarchy& H, cudaStream_t s) {
   to_f32(H.cinv64.p, H.cinv32, (int64_t)H.ncoarse * H.ncoarse, s);
   H.has_fp32 = true;
   FSI_CUDA(cudaStreamSynchronize(s));
+  const int first = coarse_first_level(H, 4);
+  if (first >= 0 && H.use_cluster) coarse_plan_build<float>(H, first, H.crun32, s);
 }
 
 template <class T>

@@ -57,8 +57,43 @@ struct AmgLevel {
   int64_t n() const { return A.rows(); }
 };
 
+// ---- coarse end of a V-cycle in one cluster launch (coarse.cu)
+constexpr int kCoarseThreads = 512;       // threads per CTA of the cluster kernel
+constexpr int kCoarseMaxLevels = 8;
+constexpr int kCoarseMaxDeg = 16;
+constexpr double kCoarseMaxBytes = 6.0e6; // levels at most this large (matrix bytes) run in the cluster
+
+struct CoarseMat {
+  int nbr = 0, br = 1, bc = 1, tpr = 1;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+  const void* v = nullptr;
+};
+struct CoarseLevel {
+  CoarseMat A, P, R;
+  const void* dinv = nullptr;
+  void* b = nullptr; void* x = nullptr; void* xb = nullptr; void* r = nullptr; void* d = nullptr;
+  double inv_theta = 0.0;
+  double c1[kCoarseMaxDeg] = {}, c2[kCoarseMaxDeg] = {};
+};
+struct CoarsePlan {
+  int nlev = 0, deg = 0, presmooth = 1, postsmooth = 1;
+  CoarseLevel lev[kCoarseMaxLevels];
+  const void* cinv = nullptr;
+  int ncoarse = 0;
+};
+template <class T>
+struct CoarseRun {
+  DBuf<CoarsePlan> plan;
+  int cluster = 0;   // CTAs per cluster (0: not available)
+  int first = -1;    // first level handled by the cluster kernel (-1: none)
+};
+
 struct Hierarchy {
   std::vector<AmgLevel> levels;
+  CoarseRun<double> crun64;
+  CoarseRun<float> crun32;
+  bool use_cluster = false;   // run the small coarse levels in one cluster launch (opt-in)
   int ncoarse = 0;
   DBuf<double> cinv64;
   DBuf<float> cinv32;
@@ -83,6 +118,15 @@ inline double cheb_step_bytes(const Bsr& A, int vb) { return A.spmv_bytes(vb) + 
 void amg_make_fp32(Hierarchy& H, cudaStream_t s);
 // x = V(b): one V-cycle from x = 0 (x, b: level-0 sized, distinct)
 template <class T> void amg_vcycle(Hierarchy& H, const T* b, T* x, cudaStream_t s);
+
+// Plan the cluster launch for levels [first, end) of H (value type T); run.first
+// stays -1 when no cluster launch is possible.
+template <class T> void coarse_plan_build(Hierarchy& H, int first, CoarseRun<T>& run, cudaStream_t s);
+// V-cycle of levels [run.first, end) from x = 0 in one launch (b, x: level run.first sized).
+template <class T> void coarse_vcycle(const CoarseRun<T>& run, const T* b, T* x, cudaStream_t s);
+// First level from which every level is small enough for the cluster kernel, or
+// -1 when that leaves only the dense coarsest level.
+int coarse_first_level(const Hierarchy& H, int value_bytes);
 
 // Chebyshev polynomial smoother/solver on D^-1 A from x = 0 (used for the solid
 // mass matrix): x = p(D^-1 A) D^-1 b with `degree` steps over [lam/ratio, upper*lam].

@@ -323,6 +323,7 @@ void precond_build(Context& C, int precision) {
     DBuf<double> Bst;
     if (!rigid) upload(Bst, translations(Shat.nbr, d), s);
     const int ks = rigid ? (d == 2 ? 3 : 6) : d;
+    for (auto& H : C.H) H.use_cluster = (C.prm.flags & CLUSTER_COARSE) != 0;
     amg_setup(C.H[0], std::move(C.Mblk), Bm.p, d, C.prm.amg, s);
     amg_setup(C.H[1], std::move(Shat), rigid ? C.solid_B.p : Bst.p, ks, C.prm.amg, s);
     amg_setup(C.H[2], std::move(C.Aff), Bf.p, d, C.prm.amg, s);

@@ -21,7 +21,7 @@ struct SolverParams {
   double mass_ratio = 8.0;
 };
 
-enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4 };
+enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8 };
 
 template <class T>
 struct PrecWork {
