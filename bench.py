@@ -192,11 +192,37 @@ def kernel_traffic(profile_name: str, source_files):
         return None
 
 
-def dist_setup(args):
+def dist_setup(args=None):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+# ------------------------------------------------------------------ replicas (N > 1)
+# The solve does not shard: one Jacobian per GPU.  With N ranks each solves its
+# own seeded Jacobians (replicas); the only collectives are the barriers around
+# the timed region and the max of the per-rank step time.
+def replica_seeds(rank: int, states: int):
+    """State seeds of one rank's resident Jacobians (disjoint across ranks)."""
+    return [rank * states + k for k in range(states)]
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank float over the process group (value itself at N = 1)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds_per_solve(step_ms_max: float, world: int) -> float:
+    """Whole-job seconds per solved Jacobian: each of `world` ranks solves one
+    Jacobian per step, the step lasting as long as the slowest rank."""
+    return step_ms_max / 1e3 / world
 
 
 # ------------------------------------------------------------------ our arm
@@ -219,8 +245,8 @@ def bench_ours(args):
 
     systems, solvers = [], []
     setup_s, build_s = [], []
-    for k in range(args.states):
-        cfg = fsigen.CONFIGS[args.workload].with_(state_seed=k + args.states * rank)
+    for seed in replica_seeds(rank, args.states):
+        cfg = fsigen.CONFIGS[args.workload].with_(state_seed=seed)
         s = fsigen.make_system(cfg)
         g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=8.0 if s.dim == 2 else 20.0,
                                                                flags=flags), stream=bs)
@@ -371,12 +397,8 @@ def bench_ours(args):
             cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {err}"}
 
     # ---- max over ranks
-    t_step = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = t_step / 1e3 / world          # seconds per solved Jacobian, whole job
+    t_step = max_over_ranks(ms, dev)
+    value = job_seconds_per_solve(t_step, world)
     line = {
         "metric": METRIC,
         "value": value,

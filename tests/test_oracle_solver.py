@@ -164,3 +164,22 @@ def test_givens_estimate_equals_true_residual_and_lstsq():
     Z = np.column_stack(Zs)
     y, *_ = np.linalg.lstsq((A @ Z), s.rhs, rcond=None)
     assert np.linalg.norm(s.rhs - A @ (Z @ y)) == pytest.approx(true, rel=1e-6)
+
+
+def test_large_amplitude_state_makes_the_solid_block_indefinite():
+    """Why the 1024x512 case runs at amplitude 1e-2: at 5e-2 the seed-0 state
+    compresses the solid so far that the St. Venant-Kirchhoff tangent, and with it
+    S_hat = A_vv + dt A_vu (Alg. 3), is indefinite; the Chebyshev/AMG sub-solve
+    cannot handle that.  At 1e-2 D^-1 S_hat keeps a positive real spectrum."""
+    import scipy.sparse.linalg as spla
+    from oracle.amg import point_dinv
+    lo = {}
+    for amp in (1e-2, 5e-2):
+        s = fsigen.make_system(fsigen.CONFIGS["2d_tiny"].with_(name="amp", n=(32, 16), amplitude=amp))
+        B = oracle.Blocks(s.scipy(), s.offsets, 2)
+        S = oracle.solid_schur(B, 0.01)
+        DS = sp.diags(point_dinv(S)) @ S
+        ev = spla.eigs(DS, k=4, which="SR", return_eigenvectors=False)
+        lo[amp] = float(np.min(ev.real))
+    assert lo[1e-2] > 0.0
+    assert lo[5e-2] < -0.5
