@@ -304,17 +304,26 @@ void cheb_sweep(const Bsr& A, const T* dinv, double lam, int deg, double ratio, 
   const int nsp = zero_start ? deg - 1 : deg;
   T* cur;
   T* oth;
-  if (zero_start) {
-    T* first = (nsp % 2 == 0) ? x : xb;
-    k_cheb_first<T><<<div_up(n, 256), 256, 0, s>>>(n, b, dinv, (T)(1.0 / theta), d, first);
-    FSI_CHECK_LAUNCH();
+  int step0 = 0;
+  if (zero_start && nsp >= 1) {
+    // steps 1 and 2 in one pass: the first iterate dinv b / theta is gathered on the fly
+    T* first = ((nsp - 1) % 2 == 0) ? x : xb;
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    spmv_cheb_from_zero<T>(A, b, dinv, d, first, (T)(1.0 / theta), (T)(rn * rho), (T)(2.0 * rn / delta), s);
+    rho = rn;
     cur = first;
     oth = (first == x) ? xb : x;
+    step0 = 1;
+  } else if (zero_start) {
+    k_cheb_first<T><<<div_up(n, 256), 256, 0, s>>>(n, b, dinv, (T)(1.0 / theta), d, x);
+    FSI_CHECK_LAUNCH();
+    cur = x;
+    oth = xb;
   } else {
     cur = x;
     oth = xb;
   }
-  for (int step = 0; step < nsp; ++step) {
+  for (int step = step0; step < nsp; ++step) {
     double c1, c2;
     if (!zero_start && step == 0) {
       c1 = 0.0; c2 = 1.0 / theta;

@@ -8,17 +8,22 @@ namespace fsi {
 
 namespace {
 
-template <class T, int BR, int BC1, int BC2, class Epi>
-void launch(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const Epi& epi, cudaStream_t s) {
+template <class T, int BR, int BC1, int BC2, class Epi, class G1>
+void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi& epi, cudaStream_t s) {
   if (A1.nbr == 0) return;
   const int tpr = sizeof(T) == 8 ? A1.tpr64 : A1.tpr;
   const int threads = 256;
   const int blocks = div_up((int64_t)A1.nbr * tpr, threads);
   const T* v2 = nullptr; const int* rp2 = nullptr; const int* ci2 = nullptr;
   if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; }
-  k_bsr_spmv<T, BR, BC1, BC2, Epi><<<blocks, threads, 0, s>>>(A1.nbr, tpr, A1.rowptr.p, A1.colind.p, A1.vals<T>(), x1,
-                                                             rp2, ci2, v2, x2, epi);
+  k_bsr_spmv<T, BR, BC1, BC2, Epi, G1><<<blocks, threads, 0, s>>>(A1.nbr, tpr, A1.rowptr.p, A1.colind.p,
+                                                                  A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
   FSI_CHECK_LAUNCH();
+}
+
+template <class T, int BR, int BC1, int BC2, class Epi>
+void launch(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const Epi& epi, cudaStream_t s) {
+  launch_g<T, BR, BC1, BC2, Epi, GatherX<T, BC1>>(A1, GatherX<T, BC1>{x1}, A2, x2, epi, s);
 }
 
 // Calls f.template operator()<BR, BC1, BC2>() for the runtime shape.
@@ -80,12 +85,25 @@ void spmv_dinv(const Bsr& A, const T* x, const T* dinv, T* y, cudaStream_t s) {
   });
 }
 
+template <class T>
+void spmv_cheb_from_zero(const Bsr& A, const T* b, const T* dinv, T* d, T* xo, T inv_theta, T c1, T c2,
+                         cudaStream_t s) {
+  require(A.br == A.bc, "spmv_cheb_from_zero: square blocks only");
+  dispatch(A.br, A.bc, 0, [&]<int BR, int BC1, int BC2>() {
+    if constexpr (BR == BC1) {
+      launch_g<T, BR, BC1, 0>(A, GatherScaled<T, BC1>{b, dinv, inv_theta}, nullptr, (const T*)nullptr,
+                              EpiChebFromZero<T, BR>{b, dinv, d, xo, inv_theta, c1, c2}, s);
+    }
+  });
+}
+
 #define FSI_INST(T)                                                                                         \
   template void spmv_axpby<T>(const Bsr&, const T*, T, T, T*, cudaStream_t);                                \
   template void spmv2_axpby<T>(const Bsr&, const T*, const Bsr*, const T*, T, T, T*, cudaStream_t);         \
   template void spmv2_resid<T>(const Bsr&, const T*, const Bsr*, const T*, const T*, T*, cudaStream_t);     \
   template void spmv_cheb<T>(const Bsr&, const T*, const T*, const T*, T*, T*, T, T, cudaStream_t);         \
-  template void spmv_dinv<T>(const Bsr&, const T*, const T*, T*, cudaStream_t);
+  template void spmv_dinv<T>(const Bsr&, const T*, const T*, T*, cudaStream_t);                             \
+  template void spmv_cheb_from_zero<T>(const Bsr&, const T*, const T*, T*, T*, T, T, T, cudaStream_t);
 FSI_INST(double)
 FSI_INST(float)
 #undef FSI_INST

@@ -63,6 +63,26 @@ __device__ __forceinline__ void load_gather(const T* __restrict__ p, T* out) {
   }
 }
 
+// ------------------------------------------------------------------ gathers
+// x[c] segment of the vector the matrix multiplies.
+template <class T, int BC>
+struct GatherX {
+  const T* x;
+  __device__ __forceinline__ void operator()(int c, T* out) const { load_gather<T, BC>(x + (size_t)c * BC, out); }
+};
+// (dinv * b * s)[c] segment: the first Chebyshev iterate from x = 0, formed on the fly.
+template <class T, int BC>
+struct GatherScaled {
+  const T* b; const T* dinv; T s;
+  __device__ __forceinline__ void operator()(int c, T* out) const {
+    T bv[BC], dv[BC];
+    load_gather<T, BC>(b + (size_t)c * BC, bv);
+    load_gather<T, BC>(dinv + (size_t)c * BC, dv);
+#pragma unroll
+    for (int j = 0; j < BC; ++j) out[j] = dv[j] * bv[j] * s;
+  }
+};
+
 // ------------------------------------------------------------------ epilogues
 // Each epilogue loads its row's own operands (load) before the row product is
 // accumulated, so those loads overlap the gathers, and combines them (store).
@@ -138,6 +158,36 @@ struct EpiCheb {
   }
 };
 
+// Second Chebyshev step from x = 0 with the first step folded in: the gathered
+// vector is x1 = d1 = dinv b / theta (GatherScaled), and
+//   r = dinv (b - A x1);  d = c1 d1 + c2 r;  xo = x1 + d.
+template <class T, int BR>
+struct EpiChebFromZero {
+  const T* b; const T* dinv; T* d; T* xo; T inv_theta; T c1; T c2;
+  struct Pre { T b[BR], dinv[BR]; };
+  __device__ __forceinline__ Pre load(int row) const {
+    Pre p;
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      const size_t k = (size_t)row * BR + i;
+      p.b[i] = b[k];
+      p.dinv[i] = dinv[k];
+    }
+    return p;
+  }
+  __device__ __forceinline__ void store(int row, const T* acc, const Pre& p) const {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      const size_t k = (size_t)row * BR + i;
+      const T d1 = p.dinv[i] * p.b[i] * inv_theta;
+      const T r = p.dinv[i] * (p.b[i] - acc[i]);
+      const T dn = c1 * d1 + c2 * r;
+      d[k] = dn;
+      xo[k] = d1 + dn;
+    }
+  }
+};
+
 // y = dinv * (A x)  (power iteration on D^-1 A)
 template <class T, int BR>
 struct EpiDinv {
@@ -165,10 +215,9 @@ __host__ __device__ constexpr int unroll_for() {
 // acc += sum over the lane's share of row entries [kb, ke) of block * x[col].
 // The U column indices are loaded first, then the U blocks and x segments, so a
 // lane keeps U independent requests in flight before it multiplies.
-template <class T, int BR, int BC>
-__device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const T* __restrict__ v,
-                                               const T* __restrict__ x, int kb, int ke, int lane, int tpr,
-                                               T* acc) {
+template <class T, int BR, int BC, class G>
+__device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const T* __restrict__ v, const G& gx,
+                                               int kb, int ke, int lane, int tpr, T* acc) {
   constexpr int U = unroll_for<T, BR, BC>();
   for (int k0 = kb + lane; k0 < ke; k0 += tpr * U) {
     int col[U];
@@ -182,7 +231,7 @@ __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const
     for (int u = 0; u < U; ++u) {
       if (col[u] >= 0) {
         load_stream<T, BR * BC>(v + (size_t)(k0 + u * tpr) * (BR * BC), blk[u]);
-        load_gather<T, BC>(x + (size_t)col[u] * BC, xv[u]);
+        gx(col[u], xv[u]);
       } else {
 #pragma unroll
         for (int t = 0; t < BR * BC; ++t) blk[u][t] = T(0);
@@ -199,9 +248,9 @@ __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const
   }
 }
 
-template <class T, int BR, int BC1, int BC2, class Epi>
+template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
-    const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, const T* __restrict__ x1,
+    const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, G1 g1,
     const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, const T* __restrict__ x2,
     Epi epi) {
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -214,8 +263,9 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
   typename Epi::Pre pre;
   if (valid && lane == 0) pre = epi.load(row);
   if (valid) {
-    row_accumulate<T, BR, BC1>(ci1, v1, x1, rp1[row], rp1[row + 1], lane, tpr, acc);
-    if constexpr (BC2 > 0) row_accumulate<T, BR, BC2>(ci2, v2, x2, rp2[row], rp2[row + 1], lane, tpr, acc);
+    row_accumulate<T, BR, BC1>(ci1, v1, g1, rp1[row], rp1[row + 1], lane, tpr, acc);
+    if constexpr (BC2 > 0)
+      row_accumulate<T, BR, BC2>(ci2, v2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr, acc);
   }
   for (int off = tpr >> 1; off > 0; off >>= 1)
 #pragma unroll
@@ -234,5 +284,8 @@ template <class T> void spmv2_resid(const Bsr& A1, const T* x1, const Bsr* A2, c
 template <class T> void spmv_cheb(const Bsr& A, const T* x, const T* b, const T* dinv, T* d, T* xo, T c1, T c2, cudaStream_t s);
 // y = dinv * (A x)
 template <class T> void spmv_dinv(const Bsr& A, const T* x, const T* dinv, T* y, cudaStream_t s);
+// Chebyshev steps 1 and 2 from x = 0 in one pass (see EpiChebFromZero)
+template <class T> void spmv_cheb_from_zero(const Bsr& A, const T* b, const T* dinv, T* d, T* xo, T inv_theta, T c1,
+                                            T c2, cudaStream_t s);
 
 }  // namespace fsi
