@@ -92,31 +92,36 @@ struct Bsr {
 template <> inline const double* Bsr::vals<double>() const { return v64.p; }
 template <> inline const float* Bsr::vals<float>() const { return v32.p; }
 
-// Lanes per block row.  Enough lanes that the launch fills about one wave of
-// the GPU (152 SMs x 2048 threads) when the rows are long enough, while each
-// lane keeps at least `min_per_lane` blocks.  FP32 rows stop at two blocks per
-// lane.  FP64 rows keep at least eight: the FP64 pipe of this GPU retires a
-// small fraction of the FP32 rate, and the shuffle reduction across a wide lane
-// group would cost more FP64 instructions than the products themselves.
-inline int lanes_for(int64_t nnzb, int nbr, double min_per_lane) {
+// Lanes per block row.  Enough lanes that a launch fills about `target_threads`
+// threads (default one wave: 152 SMs x 2048) when the rows are long enough,
+// while each lane keeps at least `min_per_lane` blocks.  FP32 rows stop at two
+// blocks per lane.  FP64 rows keep at least eight: the FP64 pipe of this GPU
+// retires a small fraction of the FP32 rate, and the shuffle reduction across a
+// wide lane group would cost more FP64 instructions than the products themselves.
+constexpr double kWaveThreads = 152.0 * 2048.0;
+inline int lanes_for(int64_t nnzb, int nbr, double min_per_lane, double target_threads) {
   const double mean = nbr ? (double)nnzb / nbr : 0.0;
-  const double target_threads = 152.0 * 2048.0;
   int t = 1;
   while (t < 32 && (double)nbr * t < target_threads && mean / (2 * t) >= min_per_lane) t *= 2;
   return t;
 }
-inline int choose_tpr(int64_t nnzb, int nbr) { return lanes_for(nnzb, nbr, 2.0); }
-inline int choose_tpr64(int64_t nnzb, int nbr) { return lanes_for(nnzb, nbr, 8.0); }
 
-// Sets both lane counts of a matrix from its shape.
-inline void set_tpr(struct Bsr& A);
-
-inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+// SpMV launch shape knobs (fsi_params: spmv_wave_fraction, spmv_unroll).
+struct SpmvTuning {
+  double target_threads = kWaveThreads;
+  int unroll = 4;   // blocks each lane loads before multiplying: 4 or 8 (8 only for small blocks)
+};
+inline SpmvTuning& spmv_tuning() {
+  static SpmvTuning t;
+  return t;
+}
 
 inline void set_tpr(Bsr& A) {
-  A.tpr = choose_tpr(A.nnzb, A.nbr);
-  A.tpr64 = choose_tpr64(A.nnzb, A.nbr);
+  A.tpr = lanes_for(A.nnzb, A.nbr, 2.0, spmv_tuning().target_threads);
+  A.tpr64 = lanes_for(A.nnzb, A.nbr, 8.0, spmv_tuning().target_threads);
 }
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // Streams and scratch shared by one context.
 struct Exec {

@@ -54,6 +54,8 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.vc_pressure = p.vcycles_pressure;
   s.mass_degree = p.mass_degree;
   s.mass_ratio = p.mass_ratio;
+  s.spmv_wave_fraction = p.spmv_wave_fraction;
+  s.spmv_unroll = p.spmv_unroll;
 }
 
 void validate_params(const fsi::SolverParams& s) {
@@ -66,6 +68,8 @@ void validate_params(const fsi::SolverParams& s) {
   require(s.vc_mesh >= 1 && s.vc_solid >= 1 && s.vc_fluid >= 1 && s.vc_pressure >= 1, "V-cycle counts");
   require(s.mass_degree >= 1 && s.mass_ratio > 1.0, "mass solve settings");
   require(std::isfinite(s.dt_theta), "dt_theta");
+  require(s.spmv_wave_fraction > 0.0 && s.spmv_wave_fraction <= 64.0, "spmv_wave_fraction must be in (0, 64]");
+  require(s.spmv_unroll == 4 || s.spmv_unroll == 8, "spmv_unroll must be 4 or 8");
 }
 
 void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -116,6 +120,8 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->vcycles_pressure = 1;
   p->mass_degree = 12;
   p->mass_ratio = dim == 3 ? 20.0 : 8.0;
+  p->spmv_wave_fraction = 1.0;
+  p->spmv_unroll = 4;
 }
 
 int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -143,6 +149,8 @@ int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const in
       FSI_CUDA(cudaStreamCreateWithFlags(&ctx->C.s, cudaStreamNonBlocking));
       ctx->C.own_stream = true;
     }
+    fsi::spmv_tuning().target_threads = fsi::kWaveThreads * ctx->C.prm.spmv_wave_fraction;
+    fsi::spmv_tuning().unroll = ctx->C.prm.spmv_unroll;
     fsi::context_setup(ctx->C, rowptr, colind, vals, node_coords);
   });
   if (rc != FSI_OK) {

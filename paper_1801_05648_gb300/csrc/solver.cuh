@@ -19,6 +19,8 @@ struct SolverParams {
   int vc_mesh = 1, vc_solid = 2, vc_fluid = 1, vc_pressure = 1;
   int mass_degree = 12;
   double mass_ratio = 8.0;
+  double spmv_wave_fraction = 1.0;
+  int spmv_unroll = 4;
 };
 
 enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8 };

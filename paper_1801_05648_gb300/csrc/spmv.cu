@@ -16,8 +16,12 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
   const int blocks = div_up((int64_t)A1.nbr * tpr, threads);
   const T* v2 = nullptr; const int* rp2 = nullptr; const int* ci2 = nullptr;
   if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; }
-  k_bsr_spmv<T, BR, BC1, BC2, Epi, G1><<<blocks, threads, 0, s>>>(A1.nbr, tpr, A1.rowptr.p, A1.colind.p,
-                                                                  A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
+  if (spmv_tuning().unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
+    k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8><<<blocks, threads, 0, s>>>(A1.nbr, tpr, A1.rowptr.p, A1.colind.p,
+                                                                       A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
+  else
+    k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4><<<blocks, threads, 0, s>>>(A1.nbr, tpr, A1.rowptr.p, A1.colind.p,
+                                                                       A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
   FSI_CHECK_LAUNCH();
 }
 

@@ -206,19 +206,20 @@ struct EpiDinv {
 };
 
 // ------------------------------------------------------------------ kernel
-// Unroll depth: blocks each lane has in flight per trip (register budget).
-template <class T, int BR, int BC>
+// Unroll depth: blocks each lane has in flight per trip (register budget): the
+// requested depth UREQ (4 or 8) for small blocks, less for large ones.
+template <class T, int BR, int BC, int UREQ>
 __host__ __device__ constexpr int unroll_for() {
-  return (int)(sizeof(T) * (BR * BC + BC)) <= 64 ? 4 : 2;
+  return (int)(sizeof(T) * (BR * BC + BC)) <= 24 ? UREQ : ((int)(sizeof(T) * (BR * BC + BC)) <= 64 ? 4 : 2);
 }
 
 // acc += sum over the lane's share of row entries [kb, ke) of block * x[col].
 // The U column indices are loaded first, then the U blocks and x segments, so a
 // lane keeps U independent requests in flight before it multiplies.
-template <class T, int BR, int BC, class G>
+template <class T, int BR, int BC, int UREQ, class G>
 __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const T* __restrict__ v, const G& gx,
                                                int kb, int ke, int lane, int tpr, T* acc) {
-  constexpr int U = unroll_for<T, BR, BC>();
+  constexpr int U = unroll_for<T, BR, BC, UREQ>();
   for (int k0 = kb + lane; k0 < ke; k0 += tpr * U) {
     int col[U];
 #pragma unroll
@@ -248,7 +249,7 @@ __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const
   }
 }
 
-template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>>
+template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
     const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, G1 g1,
     const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, const T* __restrict__ x2,
@@ -263,9 +264,9 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
   typename Epi::Pre pre;
   if (valid && lane == 0) pre = epi.load(row);
   if (valid) {
-    row_accumulate<T, BR, BC1>(ci1, v1, g1, rp1[row], rp1[row + 1], lane, tpr, acc);
+    row_accumulate<T, BR, BC1, UREQ>(ci1, v1, g1, rp1[row], rp1[row + 1], lane, tpr, acc);
     if constexpr (BC2 > 0)
-      row_accumulate<T, BR, BC2>(ci2, v2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr, acc);
+      row_accumulate<T, BR, BC2, UREQ>(ci2, v2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr, acc);
   }
   for (int off = tpr >> 1; off > 0; off >>= 1)
 #pragma unroll

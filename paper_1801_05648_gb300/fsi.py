@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
                 ("cheb_upper", ctypes.c_double), ("power_iters", ctypes.c_int), ("drop_tol", ctypes.c_double),
                 ("presmooth", ctypes.c_int), ("postsmooth", ctypes.c_int), ("vcycles_mesh", ctypes.c_int),
                 ("vcycles_solid", ctypes.c_int), ("vcycles_fluid", ctypes.c_int),
-                ("vcycles_pressure", ctypes.c_int), ("mass_degree", ctypes.c_int), ("mass_ratio", ctypes.c_double)]
+                ("vcycles_pressure", ctypes.c_int), ("mass_degree", ctypes.c_int), ("mass_ratio", ctypes.c_double),
+                ("spmv_wave_fraction", ctypes.c_double), ("spmv_unroll", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
