@@ -83,6 +83,8 @@ def _load():
             lib.fsigen_residual.argtypes = [vp, f64p, f64p, f64p, f64p]
             lib.fsigen_residual.restype = ctypes.c_int
             lib.fsigen_num_threads.restype = ctypes.c_int
+            lib.fsigen_node_map.argtypes = [vp, i32p, i32p]
+            lib.fsigen_node_map.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -233,6 +235,19 @@ class Problem:
         if rc == 2:
             raise RuntimeError(f"fsigen: state folds the mesh (min J = {minJ.value})")
         return R
+
+    def node_map(self):
+        """2D only: (node_dof [n_q2, 4] int32, patch [n_q2, 9] int32).  node_dof
+        rows: first v DOF, first u DOF, p DOF or -1, flags (1 solid closure,
+        2 v fixed, 4 u fixed, 8 interface, 16 lattice i odd, 32 lattice j odd,
+        64 p row fixed); patch: the 3x3 lattice neighbourhood
+        of each Q2 node (-1 outside the mesh)."""
+        nd = np.empty((self.n_q2, 4), np.int32)
+        pt = np.empty((self.n_q2, 9), np.int32)
+        rc = _load().fsigen_node_map(self._h, _ptr(nd, ctypes.c_int32), _ptr(pt, ctypes.c_int32))
+        if rc != 0:
+            raise ValueError("node_map: 2D problems only")
+        return nd, pt
 
     def solid_node_coords(self) -> np.ndarray:
         """Coordinates of the s_v nodes (one row per node, s_v node order)."""

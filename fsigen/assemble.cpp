@@ -833,6 +833,52 @@ int fsigen_residual(void* h, const double* U, const double* Uold, double* R, dou
   return (*minJ <= 0.0) ? 2 : 0;
 }
 
+// Node map of a 2D mesh for the learned correction stage: per Q2 node (lattice
+// order) node_dof[4] = {first v DOF, first u DOF, p DOF or -1 (not a vertex),
+// flags: bit0 closed solid region, bit1 v fixed, bit2 u fixed, bit3 interface
+// (in the solid closure and in a fluid cell), bit4 i odd, bit5 j odd, bit6 p row
+// fixed}, and patch[9] = the 3x3 lattice
+// neighbourhood (row-major, dx fastest, -1 outside the mesh).  Returns 0, or -1
+// for 3D problems.
+int fsigen_node_map(void* h, int32_t* node_dof, int32_t* patch) {
+  Problem* p = static_cast<Problem*>(h);
+  if (p->dim != 2) return -1;
+  const int nx = p->nq2[0], ny = p->nq2[1];
+  for (int64_t a = 0; a < p->n_q2; ++a) {
+    const int i = (int)(a % nx), j = (int)(a / nx);
+    node_dof[a * 4 + 0] = (int32_t)p->dof_v[a];
+    node_dof[a * 4 + 1] = (int32_t)p->dof_u[a];
+    int32_t pd = -1;
+    if (i % 2 == 0 && j % 2 == 0) pd = (int32_t)p->dof_p[(int64_t)(j / 2) * p->nq1[0] + i / 2];
+    node_dof[a * 4 + 2] = pd;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    cells_of_q2(i, p->P.n[0], lo[0], hi[0]);
+    cells_of_q2(j, p->P.n[1], lo[1], hi[1]);
+    bool fluid_cell = false;
+    for (int cj = lo[1]; cj <= hi[1]; ++cj)
+      for (int ci = lo[0]; ci <= hi[0]; ++ci) {
+        const int c[3] = {ci, cj, 0};
+        if (!p->cell_solid[cell_index(*p, c)]) fluid_cell = true;
+      }
+    int32_t flags = 0;
+    if (p->node_solid[a]) flags |= 1;
+    if (p->node_vdir[a]) flags |= 2;
+    if (p->node_udir[a]) flags |= 4;
+    if (p->node_solid[a] && fluid_cell) flags |= 8;
+    flags |= (i % 2) << 4;
+    flags |= (j % 2) << 5;
+    if (pd >= 0 && p->row_fixed[pd]) flags |= 64;
+    node_dof[a * 4 + 3] = flags;
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di, jj = j + dj;
+        const int slot = (dj + 1) * 3 + (di + 1);
+        patch[a * 9 + slot] = (ii >= 0 && ii < nx && jj >= 0 && jj < ny) ? (int32_t)((int64_t)jj * nx + ii) : -1;
+      }
+  }
+  return 0;
+}
+
 int fsigen_num_threads() {
 #ifdef _OPENMP
   return omp_get_max_threads();

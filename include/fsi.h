@@ -54,9 +54,11 @@ enum {
   FSI_X0_GIVEN = 1,        /* fsi_solve starts from the x passed in (else from 0) */
   FSI_USE_GRAPHS = 2,      /* replay each FGMRES iteration as one captured CUDA graph */
   FSI_NO_RIGID_MODES = 4,  /* solid AMG with translations only, even when coordinates are given */
-  FSI_CLUSTER_COARSE = 8   /* run the coarse AMG levels (matrices <= 6 MB) of each V-cycle in one
+  FSI_CLUSTER_COARSE = 8,  /* run the coarse AMG levels (matrices <= 6 MB) of each V-cycle in one
                               16-CTA thread-block-cluster launch instead of one launch per step
                               (fewer launches, but slower on the 256x128 case: 26.7 vs 15.7 ms) */
+  FSI_LEARNED = 16         /* apply the learned correction stage after P^-1 in every FGMRES
+                              iteration (needs fsi_learned_setup and weights; see below) */
 };
 
 typedef struct fsi_params {
@@ -85,6 +87,9 @@ typedef struct fsi_params {
      multiplying (4).  Process-wide: the last fsi_setup's values apply. */
   double spmv_wave_fraction;
   int spmv_unroll;
+  /* learned stage: take the correction only when ||r' - A c|| < learned_accept * ||r'||
+     (0.1; at 0.3 and above the trained stage's accepted corrections stall FGMRES) */
+  double learned_accept;
 } fsi_params;
 
 typedef struct fsi_stats {
@@ -100,6 +105,7 @@ typedef struct fsi_stats {
   const double* relres_hist;/* |g_{j+1}|/||b|| per iteration; owned by the context, valid until the next solve */
   int hist_len;
   int64_t kernel_launches;  /* CUDA kernels the solve executed (graph replays counted per kernel node) */
+  int learned_accepted;     /* FSI_LEARNED: iterations whose learned correction was taken */
 } fsi_stats;
 
 typedef struct fsi_ctx fsi_ctx;
@@ -138,7 +144,8 @@ int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const in
  *               while the outer SpMV, Gram-Schmidt and Givens stay FP64.
  *               May be called again to switch precision (the FP64 hierarchy is
  *               built once).
- *   learned_weights  must be NULL (reserved).
+ *   learned_weights  nullable: path of a weights file for the learned stage
+ *               (as fsi_learned_load; needs fsi_learned_setup first).
  */
 int fsi_precond_build(fsi_ctx* ctx, int precision, const char* learned_weights);
 
@@ -156,7 +163,9 @@ int fsi_solve(fsi_ctx* ctx, const double* rhs_dev, double* x_dev, double rtol, f
 /* Release every device and host resource of the context (NULL is ignored). */
 void fsi_free(fsi_ctx* ctx);
 
-/* Message of the last failed call on ctx ("" if none; static text for NULL). */
+/* Message of the last failed call on ctx ("" if none).  For ctx = NULL: the
+ * last failure on this thread of a call made without a context (fsi_setup,
+ * fsi_trainer_create / _set_master / _get / _save). */
 const char* fsi_last_error(const fsi_ctx* ctx);
 
 /* ------------------------------------------------------------------------
@@ -230,6 +239,105 @@ int fsi_amg_export(fsi_ctx* ctx, int which, int level, int what, void* dst);
  * the context's stream without waiting.
  */
 int fsi_mass_solve_noalloc(fsi_ctx* ctx, const double* in_dev, double* out_dev);
+
+/* ------------------------------------------------------------------------
+ * Learned correction stage (2D meshes).  The paper has no such stage: it is an
+ * extra smoothing step after Alg. 2 inside each FGMRES iteration.  With
+ * z_j = P^-1 v_j and q = A z_j:
+ *     r' = v_j - q,  c = MLP(r'),  t = A c;
+ *     if ||r' - t||_2 < tau ||r'||_2:  z_j <- z_j + c,  w = q + t   (accepted;
+ *                                  tau = fsi_params.learned_accept, default 0.1)
+ *     else:                        w = q                        (plain preconditioner)
+ * so the stage changes the search space of FGMRES but never its answer.  One
+ * more FP64 outer SpMV and one MLP pass per iteration.
+ *
+ * MLP (per Q2 node a, 3x3 lattice patch N(a), slots s = 3 (dj+1) + (di+1)):
+ *   x_{s,k} = r'[dof_k(N_s(a))] / sigma_in[class]   k = v_x v_y u_x u_y p
+ *             (0 outside the mesh and for p at a node that carries no p)
+ *   rho_a   = sqrt(sum of the 45 squares / 45)
+ *   f_a     = [x / rho_a (45), one-hot of (i odd) + 2 (j odd) (4),
+ *              flags solid, v fixed, u fixed, interface (4)]              53 inputs
+ *   y_a     = W3^T gelu(W2^T gelu(W1^T f_a + b1) + b2) + b3                64, 64, 5
+ *   c[dof_k(a)] = y_{a,k} rho_a sigma_out[class]  (0 on fixed rows, at rho_a = 0)
+ * Classes are m, s_v, s_u, f_v, f_p (0..4).  Weights bfloat16 (round to nearest
+ * even), arithmetic FP32, c written in FP64.  The parameter vector (7,941
+ * values) is W1 [53][64], b1 [64], W2 [64][64], b2 [64], W3 [64][5], b3 [5],
+ * row-major, W_l mapping its layer's input (rows) to output (columns).
+ * Weights file: 8 bytes "FSIMLP01", int32 {53, 64, 5, 0}, float32 sigma_in[5],
+ * sigma_out[5], then the 7,941 bfloat16 parameters, little endian.
+ */
+#define FSI_MLP_PARAMS 7941
+#define FSI_MLP_INPUTS 53
+
+/*
+ * fsi_learned_setup - the node map of the context's mesh (host arrays, copied):
+ *   n_nodes    Q2 nodes
+ *   node_dof   n_nodes x 4 int32: first v DOF (v_y follows), first u DOF (u_y
+ *              follows), p DOF or -1, flags (1 solid closure, 2 v fixed, 4 u
+ *              fixed, 8 interface, 16 lattice i odd, 32 lattice j odd, 64 p row
+ *              fixed)
+ *   patch      n_nodes x 9 int32: the 3x3 lattice neighbourhood (row-major, i
+ *              fastest), -1 outside the mesh
+ * Every DOF must belong to exactly one node (FSI_EINVAL otherwise).
+ */
+int fsi_learned_setup(fsi_ctx* ctx, int64_t n_nodes, const int32_t* node_dof, const int32_t* patch);
+/* Load the stage's weights from a file (format above). */
+int fsi_learned_load(fsi_ctx* ctx, const char* path);
+/* Set the stage's weights from host memory: sigma_in[5], sigma_out[5] (> 0), params[FSI_MLP_PARAMS] bfloat16. */
+int fsi_learned_set_weights(fsi_ctx* ctx, const float* sigma_in, const float* sigma_out, const uint16_t* params);
+/* c = MLP(r') (device, n doubles each; every entry of c written).  Enqueued without waiting. */
+int fsi_learned_apply(fsi_ctx* ctx, const double* r_dev, double* c_dev);
+/* Features f_a (device, n_nodes x 53 floats, node-major) and rho_a (n_nodes floats) of r'.  Enqueued. */
+int fsi_learned_features(fsi_ctx* ctx, const double* r_dev, float* feat_dev, float* rho_dev);
+/* Change fsi_params.learned_accept (in (0, 1]) of a context. */
+int fsi_set_learned_accept(fsi_ctx* ctx, double tau);
+/* Change the run-time flags of a context (FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_LEARNED);
+ * FSI_NO_RIGID_MODES and FSI_CLUSTER_COARSE are fixed at fsi_setup (FSI_EINVAL if they differ). */
+int fsi_set_flags(fsi_ctx* ctx, int flags);
+/*
+ * fsi_set_harvest - during later fsi_solve calls, store the preconditioned
+ * residual r'_j = v_j - A P^-1 v_j of iterations j < nvec of each restart cycle
+ * (a later cycle overwrites) into buf_dev + j*n (device, nvec x n doubles, owned
+ * by the caller and kept valid while set).  nvec = 0 (or buf_dev NULL) stops it.
+ */
+int fsi_set_harvest(fsi_ctx* ctx, double* buf_dev, int nvec);
+
+/*
+ * Training of the stage on residuals r' of one or more contexts.  Loss per
+ * residual: L = ||r' - A c(r')||^2 / ||r'||^2 (A of the context given), i.e. the
+ * error e - c of the pair (r', e = A^-1 r') in the residual norm that the accept
+ * test compares.  Gradients by backpropagation (dL/dc = -2 A^T (r' - A c) /
+ * ||r'||^2, FP64; through the MLP in FP32 with the bfloat16 weights), AdamW
+ * (decoupled weight decay) on FP32 master weights; the forward pass uses their
+ * bfloat16 rounding.  Initial weights: Glorot uniform from SplitMix64
+ * (draw i: splitmix64((seed << 32) + i), top 53 bits as a uniform in [0, 1)),
+ * the last layer scaled by init_out_scale, biases zero.
+ */
+typedef struct fsi_train_params {
+  double lr, beta1, beta2, eps, weight_decay;   /* AdamW (1e-3, 0.9, 0.999, 1e-8, 0) */
+  uint64_t seed;
+  double init_out_scale;                        /* (0.01) */
+  float sigma_in[5], sigma_out[5];              /* class scales, > 0 */
+} fsi_train_params;
+typedef struct fsi_trainer fsi_trainer;
+
+void fsi_default_train_params(fsi_train_params* p);
+int fsi_trainer_create(fsi_trainer** out, const fsi_train_params* p);
+/* Add the gradient of L for r' (device, n doubles of ctx, which needs fsi_learned_setup); *loss
+ * (nullable) receives L.  Runs on ctx's stream and waits for it. */
+int fsi_trainer_step(fsi_trainer* tr, fsi_ctx* ctx, const double* rprime_dev, double* loss);
+/* L for r' with the current weights, no gradient (validation).  Waits. */
+int fsi_trainer_loss(fsi_trainer* tr, fsi_ctx* ctx, const double* rprime_dev, double* loss);
+/* One AdamW step with the mean of the gradients added since the last update, at
+ * learning rate lr (lr <= 0: the fsi_train_params rate), on ctx's stream; waits. */
+int fsi_trainer_update(fsi_trainer* tr, fsi_ctx* ctx, double lr);
+/* Replace the master weights (host, FSI_MLP_PARAMS floats); resets the AdamW moments and gradients. */
+int fsi_trainer_set_master(fsi_trainer* tr, const float* params);
+/* Copy out (host, nullable each): master weights (floats), bfloat16 weights, accumulated gradient (floats). */
+int fsi_trainer_get(fsi_trainer* tr, float* master, uint16_t* params_bf16, float* grad);
+/* Write the current weights with the trainer's class scales as a weights file. */
+int fsi_trainer_save(fsi_trainer* tr, const char* path);
+void fsi_trainer_free(fsi_trainer* tr);
 
 #ifdef __cplusplus
 }

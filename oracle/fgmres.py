@@ -26,10 +26,15 @@ class FGMRESResult:
     history: list = field(default_factory=list)   # |g_{j+1}| / ||b|| per iteration
     breakdown: bool = False
     cycle_starts: list = field(default_factory=list)   # index into history where each cycle starts
+    accepted: int = 0                                  # learned-stage corrections taken
 
 
-def fgmres(A, M, b, tol=1e-8, restart=100, maxit=1000, x0=None) -> FGMRESResult:
-    """Solve A x = b; A(x) and M(r) are callables (matrix-vector and P^-1)."""
+def fgmres(A, M, b, tol=1e-8, restart=100, maxit=1000, x0=None, correct=None, accept=1.0) -> FGMRESResult:
+    """Solve A x = b; A(x) and M(r) are callables (matrix-vector and P^-1).
+
+    correct(r') -> c, if given, is the learned stage: with q = A z_j and
+    r' = v_j - q, the correction c is taken (z_j += c, w = q + A c) only when
+    ||r' - A c|| < accept * ||r'||; otherwise w = q as without the stage."""
     n = b.shape[0]
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
     bnorm = np.sqrt(np.dot(b, b))
@@ -40,13 +45,14 @@ def fgmres(A, M, b, tol=1e-8, restart=100, maxit=1000, x0=None) -> FGMRESResult:
     total = 0
     cycles = 0
     breakdown = False
+    accepted = 0
     while True:
         r = b - A(x)
         beta = np.sqrt(np.dot(r, r))
         if beta / bnorm <= tol:
-            return FGMRESResult(x, total, cycles, True, beta / bnorm, hist, breakdown, starts)
+            return FGMRESResult(x, total, cycles, True, beta / bnorm, hist, breakdown, starts, accepted)
         if total >= maxit:
-            return FGMRESResult(x, total, cycles, False, beta / bnorm, hist, breakdown, starts)
+            return FGMRESResult(x, total, cycles, False, beta / bnorm, hist, breakdown, starts, accepted)
         starts.append(len(hist))
         m = restart
         V = np.zeros((m + 1, n))
@@ -61,6 +67,15 @@ def fgmres(A, M, b, tol=1e-8, restart=100, maxit=1000, x0=None) -> FGMRESResult:
         for j in range(m):
             Z[j] = M(V[j])
             w = A(Z[j])
+            if correct is not None:
+                rp = V[j] - w
+                c = correct(rp)
+                t = A(c)
+                d = rp - t
+                if np.dot(d, d) < accept * accept * np.dot(rp, rp):
+                    Z[j] = Z[j] + c
+                    w = w + t
+                    accepted += 1
             wnorm0 = np.sqrt(np.dot(w, w))
             for _ in range(2):                      # classical Gram-Schmidt, twice
                 h = V[:j + 1] @ w
@@ -99,4 +114,4 @@ def fgmres(A, M, b, tol=1e-8, restart=100, maxit=1000, x0=None) -> FGMRESResult:
         if breakdown:
             r = b - A(x)
             rel = np.sqrt(np.dot(r, r)) / bnorm
-            return FGMRESResult(x, total, cycles, rel <= tol, rel, hist, breakdown, starts)
+            return FGMRESResult(x, total, cycles, rel <= tol, rel, hist, breakdown, starts, accepted)

@@ -25,8 +25,9 @@ class OracleSolver:
         return cls(system.rowptr, system.colind, system.vals, system.offsets, system.dim,
                    system.solid_coords, params, exact)
 
-    def solve(self, b, tol=1e-8, restart=100, maxit=1000, x0=None):
+    def solve(self, b, tol=1e-8, restart=100, maxit=1000, x0=None, correct=None, accept=1.0):
         t0 = time.perf_counter()
-        res = fgmres(lambda v: self.A @ v, self.P, np.asarray(b, np.float64), tol, restart, maxit, x0)
+        res = fgmres(lambda v: self.A @ v, self.P, np.asarray(b, np.float64), tol, restart, maxit, x0, correct,
+                     accept)
         res.solve_s = time.perf_counter() - t0
         return res

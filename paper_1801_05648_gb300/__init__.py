@@ -2,12 +2,13 @@
 Jacobians (Jodlbauer, Langer & Wick, arXiv:1801.05648, Sec. 4).
 
 The solver lives in ``libfsi.so`` (CUDA, sm_103a) behind the C ABI of
-``include/fsi.h``; ``fsi.py`` is its ctypes binding.
+``include/fsi.h``; ``fsi.py`` is its ctypes binding and ``learned.py`` the
+training / evaluation driver of the learned correction stage.
 """
-from .fsi import (FSISolver, FSIError, Params, SolveStats, default_params, load_library, BLOCKS, EXPORTED,
-                  FSI_FP64, FSI_FP32_AMG, FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE,
-                  LIB_PATH)
+from .fsi import (FSISolver, FSIError, Params, SolveStats, Trainer, TrainParams, default_params,
+                  default_train_params, load_library, BLOCKS, EXPORTED, FSI_FP64, FSI_FP32_AMG, FSI_X0_GIVEN,
+                  FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_LEARNED, FSI_MLP_PARAMS, LIB_PATH)
 
-__all__ = ["FSISolver", "FSIError", "Params", "SolveStats", "default_params", "load_library", "BLOCKS", "EXPORTED",
-           "FSI_FP64", "FSI_FP32_AMG", "FSI_X0_GIVEN", "FSI_USE_GRAPHS", "FSI_NO_RIGID_MODES",
-           "FSI_CLUSTER_COARSE", "LIB_PATH"]
+__all__ = ["FSISolver", "FSIError", "Params", "SolveStats", "Trainer", "TrainParams", "default_params",
+           "default_train_params", "load_library", "BLOCKS", "EXPORTED", "FSI_FP64", "FSI_FP32_AMG", "FSI_X0_GIVEN",
+           "FSI_USE_GRAPHS", "FSI_NO_RIGID_MODES", "FSI_CLUSTER_COARSE", "FSI_LEARNED", "FSI_MLP_PARAMS", "LIB_PATH"]

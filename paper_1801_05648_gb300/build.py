@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build", "fsi")
 LIB = os.path.join(HERE, "libfsi.so")
-SOURCES = ["spmv.cu", "vec.cu", "sparse_util.cu", "amg.cu", "solver.cu", "fsi_api.cu", "noalloc.cu", "coarse.cu"]
+SOURCES = ["spmv.cu", "vec.cu", "sparse_util.cu", "amg.cu", "solver.cu", "fsi_api.cu", "noalloc.cu", "coarse.cu", "learned.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -6,29 +6,37 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 struct fsi_ctx {
   fsi::Context C;
+};
+
+struct fsi_trainer {
+  fsi::Trainer T;
 };
 
 namespace {
 
 thread_local std::string g_setup_error;
 
+// Run f, turning exceptions into status codes; the message goes to the context
+// (or, for calls without one, to the thread's fsi_last_error(NULL) text).
 template <class F>
 int guarded(fsi_ctx* ctx, F&& f) {
+  std::string& err = ctx ? ctx->C.err : g_setup_error;
   try {
     f();
-    if (ctx) ctx->C.err.clear();
+    err.clear();
     return FSI_OK;
   } catch (const fsi::Error& e) {
-    if (ctx) ctx->C.err = e.what();
+    err = e.what();
     return e.code;
   } catch (const std::bad_alloc&) {
-    if (ctx) ctx->C.err = "host allocation failed";
+    err = "host allocation failed";
     return FSI_ENOMEM;
   } catch (const std::exception& e) {
-    if (ctx) ctx->C.err = e.what();
+    err = e.what();
     return FSI_ECUDA;
   }
 }
@@ -56,6 +64,7 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.mass_ratio = p.mass_ratio;
   s.spmv_wave_fraction = p.spmv_wave_fraction;
   s.spmv_unroll = p.spmv_unroll;
+  s.learned_accept = p.learned_accept;
 }
 
 void validate_params(const fsi::SolverParams& s) {
@@ -70,6 +79,7 @@ void validate_params(const fsi::SolverParams& s) {
   require(std::isfinite(s.dt_theta), "dt_theta");
   require(s.spmv_wave_fraction > 0.0 && s.spmv_wave_fraction <= 64.0, "spmv_wave_fraction must be in (0, 64]");
   require(s.spmv_unroll == 4 || s.spmv_unroll == 8, "spmv_unroll must be 4 or 8");
+  require(s.learned_accept > 0.0 && s.learned_accept <= 1.0, "learned_accept must be in (0, 1]");
 }
 
 void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -90,6 +100,15 @@ void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* coli
       require(k == rowptr[r] || colind[k] > colind[k - 1], "columns must be strictly increasing within a row");
       require(std::isfinite(vals[k]), "non-finite matrix value");
     }
+  }
+}
+
+// The captured FGMRES iteration holds the learned stage's buffers and class
+// scales by value: any change to them drops the graph (re-captured on the next solve).
+void drop_graph(fsi::Context& C) {
+  if (C.iter_graph) {
+    cudaGraphExecDestroy(C.iter_graph);
+    C.iter_graph = nullptr;
   }
 }
 
@@ -122,6 +141,7 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->mass_ratio = dim == 3 ? 20.0 : 8.0;
   p->spmv_wave_fraction = 1.0;
   p->spmv_unroll = 4;
+  p->learned_accept = 0.1;
 }
 
 int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -166,8 +186,12 @@ int fsi_precond_build(fsi_ctx* ctx, int precision, const char* learned_weights) 
   if (!ctx) return FSI_EINVAL;
   return guarded(ctx, [&] {
     fsi::require(precision == FSI_FP64 || precision == FSI_FP32_AMG, "precision must be FSI_FP64 or FSI_FP32_AMG");
-    fsi::require(learned_weights == nullptr, "learned_weights must be NULL");
     fsi::precond_build(ctx->C, precision);
+    if (learned_weights) {
+      fsi::require(ctx->C.learned.n_nodes > 0, "learned_weights given before fsi_learned_setup");
+      drop_graph(ctx->C);
+      fsi::learned_load_file(ctx->C.learned, learned_weights, ctx->C.s);
+    }
   });
 }
 
@@ -196,6 +220,7 @@ int fsi_solve(fsi_ctx* ctx, const double* rhs_dev, double* x_dev, double rtol, f
     out->relres_hist = C.hist.empty() ? nullptr : C.hist.data();
     out->hist_len = (int)C.hist.size();
     out->kernel_launches = C.last_launches;
+    out->learned_accepted = C.last_accepted;
   }
   if (rc != FSI_OK) return rc;
   if (status == fsi::ENOTCONV_) C.err = "FGMRES reached maxit before rtol";
@@ -299,5 +324,179 @@ int fsi_amg_export(fsi_ctx* ctx, int which, int level, int what, void* dst) {
     FSI_CUDA(cudaStreamSynchronize(C.s));
   });
 }
+
+int fsi_learned_setup(fsi_ctx* ctx, int64_t n_nodes, const int32_t* node_dof, const int32_t* patch) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(ctx->C.dim == 2, "the learned stage is defined for 2D meshes");
+    drop_graph(ctx->C);
+    fsi::learned_set_geometry(ctx->C.learned, ctx->C.n, n_nodes, node_dof, patch, ctx->C.s);
+  });
+}
+
+int fsi_learned_load(fsi_ctx* ctx, const char* path) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(path != nullptr, "null path");
+    drop_graph(ctx->C);
+    fsi::learned_load_file(ctx->C.learned, path, ctx->C.s);
+  });
+}
+
+int fsi_learned_set_weights(fsi_ctx* ctx, const float* sigma_in, const float* sigma_out, const uint16_t* params) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(sigma_in && sigma_out && params, "null argument");
+    drop_graph(ctx->C);
+    fsi::learned_set_weights(ctx->C.learned, sigma_in, sigma_out, params, ctx->C.s);
+  });
+}
+
+int fsi_learned_apply(fsi_ctx* ctx, const double* r_dev, double* c_dev) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::Learned& L = ctx->C.learned;
+    fsi::require(L.n_nodes > 0 && L.has_weights, "fsi_learned_apply needs fsi_learned_setup and weights");
+    fsi::require(r_dev && c_dev, "null vector");
+    fsi::mlp_apply(fsi::learned_geom(L, ctx->C.off), L.w16.p, r_dev, c_dev, ctx->C.s);
+  });
+}
+
+int fsi_learned_features(fsi_ctx* ctx, const double* r_dev, float* feat_dev, float* rho_dev) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::Learned& L = ctx->C.learned;
+    fsi::require(L.n_nodes > 0, "fsi_learned_features needs fsi_learned_setup");
+    fsi::require(r_dev && feat_dev && rho_dev, "null vector");
+    fsi::mlp_features(fsi::learned_geom(L, ctx->C.off), r_dev, feat_dev, rho_dev, ctx->C.s);
+  });
+}
+
+int fsi_set_learned_accept(fsi_ctx* ctx, double tau) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(tau > 0.0 && tau <= 1.0, "learned_accept must be in (0, 1]");
+    drop_graph(ctx->C);
+    ctx->C.prm.learned_accept = tau;
+  });
+}
+
+int fsi_set_flags(fsi_ctx* ctx, int flags) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    constexpr int fixed = FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE;
+    constexpr int known = FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED;
+    fsi::require((flags & ~known) == 0, "unknown flag bits");
+    fsi::require((flags & fixed) == (ctx->C.prm.flags & fixed),
+                 "FSI_NO_RIGID_MODES and FSI_CLUSTER_COARSE are fixed at fsi_setup");
+    ctx->C.prm.flags = flags;
+  });
+}
+
+int fsi_set_harvest(fsi_ctx* ctx, double* buf_dev, int nvec) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(nvec >= 0, "nvec must be >= 0");
+    if (!buf_dev || nvec == 0) {
+      ctx->C.harvest = nullptr;
+      ctx->C.harvest_n = 0;
+    } else {
+      ctx->C.harvest = buf_dev;
+      ctx->C.harvest_n = nvec;
+    }
+  });
+}
+
+void fsi_default_train_params(fsi_train_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->lr = 1e-3;
+  p->beta1 = 0.9;
+  p->beta2 = 0.999;
+  p->eps = 1e-8;
+  p->weight_decay = 0.0;
+  p->seed = 0;
+  p->init_out_scale = 0.01;
+  for (int k = 0; k < 5; ++k) p->sigma_in[k] = p->sigma_out[k] = 1.0f;
+}
+
+int fsi_trainer_create(fsi_trainer** out, const fsi_train_params* p) {
+  if (!out) return FSI_EINVAL;
+  *out = nullptr;
+  fsi_trainer* tr = nullptr;
+  try {
+    tr = new fsi_trainer();
+  } catch (...) {
+    return FSI_ENOMEM;
+  }
+  int rc = guarded(nullptr, [&] {
+    fsi_train_params def;
+    fsi_default_train_params(&def);
+    const fsi_train_params& q = p ? *p : def;
+    fsi::TrainParams tp;
+    tp.lr = q.lr; tp.beta1 = q.beta1; tp.beta2 = q.beta2; tp.eps = q.eps; tp.weight_decay = q.weight_decay;
+    tp.seed = q.seed;
+    tp.init_out_scale = q.init_out_scale;
+    for (int k = 0; k < 5; ++k) { tp.sig_in[k] = q.sigma_in[k]; tp.sig_out[k] = q.sigma_out[k]; }
+    fsi::trainer_init(tr->T, tp);
+  });
+  if (rc != FSI_OK) {
+    delete tr;
+    return rc;
+  }
+  *out = tr;
+  return FSI_OK;
+}
+
+int fsi_trainer_step(fsi_trainer* tr, fsi_ctx* ctx, const double* rprime_dev, double* loss) {
+  if (!tr || !ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(rprime_dev != nullptr, "null vector");
+    const double L = fsi::trainer_step(tr->T, ctx->C, rprime_dev);
+    if (loss) *loss = L;
+  });
+}
+
+int fsi_trainer_loss(fsi_trainer* tr, fsi_ctx* ctx, const double* rprime_dev, double* loss) {
+  if (!tr || !ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(rprime_dev != nullptr, "null vector");
+    const double L = fsi::trainer_step(tr->T, ctx->C, rprime_dev, false);
+    if (loss) *loss = L;
+  });
+}
+
+int fsi_trainer_update(fsi_trainer* tr, fsi_ctx* ctx, double lr) {
+  if (!tr || !ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] { fsi::trainer_update(tr->T, ctx->C.s, lr); });
+}
+
+int fsi_trainer_set_master(fsi_trainer* tr, const float* params) {
+  if (!tr || !params) return FSI_EINVAL;
+  return guarded(nullptr, [&] { fsi::trainer_set_master(tr->T, params); });
+}
+
+int fsi_trainer_get(fsi_trainer* tr, float* master, uint16_t* params_bf16, float* grad) {
+  if (!tr) return FSI_EINVAL;
+  return guarded(nullptr, [&] {
+    FSI_CUDA(cudaDeviceSynchronize());
+    if (master) FSI_CUDA(cudaMemcpy(master, tr->T.master.p, sizeof(float) * fsi::kMlpParams, cudaMemcpyDeviceToHost));
+    if (params_bf16)
+      FSI_CUDA(cudaMemcpy(params_bf16, tr->T.w16.p, sizeof(uint16_t) * fsi::kMlpParams, cudaMemcpyDeviceToHost));
+    if (grad) FSI_CUDA(cudaMemcpy(grad, tr->T.grad.p, sizeof(float) * fsi::kMlpParams, cudaMemcpyDeviceToHost));
+  });
+}
+
+int fsi_trainer_save(fsi_trainer* tr, const char* path) {
+  if (!tr || !path) return FSI_EINVAL;
+  return guarded(nullptr, [&] {
+    std::vector<uint16_t> h(fsi::kMlpParams);
+    FSI_CUDA(cudaDeviceSynchronize());
+    FSI_CUDA(cudaMemcpy(h.data(), tr->T.w16.p, sizeof(uint16_t) * fsi::kMlpParams, cudaMemcpyDeviceToHost));
+    fsi::learned_save_file(path, tr->T.prm.sig_in, tr->T.prm.sig_out, h.data());
+  });
+}
+
+void fsi_trainer_free(fsi_trainer* tr) { delete tr; }
 
 }  // extern "C"

@@ -1,0 +1,779 @@
+// Learned correction stage: per-node MLP inference, the FGMRES accept/fallback
+// step, residual harvest, and the training kernels (forward with stored
+// activations, backward through the MLP, weight-gradient sums, AdamW).
+#include "learned.cuh"
+#include "solver.cuh"
+#include "vec.cuh"
+#include "spmv.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <fstream>
+#include <vector>
+
+namespace fsi {
+
+namespace {
+
+constexpr int kNodeThreads = 128;
+constexpr int kParamsPadded = (kMlpParams + 3) / 4 * 4;
+static_assert(kB1 % 4 == 0 && kW2 % 4 == 0 && kB2 % 4 == 0 && kW3 % 4 == 0, "float4 rows");
+
+__host__ __device__ inline float bf16_to_f32(uint16_t h) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float((uint32_t)h << 16);
+#else
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+
+__host__ __device__ inline uint16_t f32_to_bf16(float f) {   // round to nearest, ties to even
+#ifdef __CUDA_ARCH__
+  uint32_t u = __float_as_uint(f);
+#else
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+#endif
+  const uint32_t lsb = (u >> 16) & 1u;
+  return (uint16_t)((u + 0x7FFFu + lsb) >> 16);
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ int cls_of(const MlpGeom& g, int64_t d) {
+  return (d >= g.off1) + (d >= g.off2) + (d >= g.off3) + (d >= g.off4);
+}
+
+// a[k] for a per-class array held in the kernel parameters
+__device__ __forceinline__ float pick5(const float (&a)[5], int k) {
+  return k == 0 ? a[0] : k == 1 ? a[1] : k == 2 ? a[2] : k == 3 ? a[3] : a[4];
+}
+
+__device__ __forceinline__ void load_weights(float* W, const uint16_t* __restrict__ w16) {
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) W[i] = bf16_to_f32(w16[i]);
+  __syncthreads();
+}
+
+enum { MODE_APPLY = 0, MODE_FEATURES = 1, MODE_TRAIN = 2 };
+
+// One thread per node: gather the patch, normalise, run the MLP (MODE_APPLY,
+// MODE_TRAIN) and scatter the correction; MODE_TRAIN also stores the features
+// and pre-activations column-major (row k of node a at [k * ld + a]).
+template <int MODE>
+__global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t* __restrict__ w16,
+                                                      const double* __restrict__ rp, double* __restrict__ c,
+                                                      float* __restrict__ F, float* __restrict__ rho_out,
+                                                      float* __restrict__ H1, float* __restrict__ H2, int64_t ld) {
+  __shared__ __align__(16) float W[kParamsPadded];
+  if (MODE != MODE_FEATURES) load_weights(W, w16);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < g.n_nodes; a += stride) {
+    const int4 me = g.node_dof[a];
+    const int fl = me.w;
+    float x[kMlpPatch];
+    float ss = 0.f;
+#pragma unroll
+    for (int s = 0; s < kMlpSlots; ++s) {
+      const int q = g.patch[a * kMlpSlots + s];
+      float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, e4 = 0.f;
+      if (q >= 0) {
+        const int4 r = g.node_dof[q];
+        const float iv = pick5(g.inv_in, cls_of(g, r.x));
+        const float iu = pick5(g.inv_in, cls_of(g, r.y));
+        e0 = (float)rp[r.x] * iv;
+        e1 = (float)rp[r.x + 1] * iv;
+        e2 = (float)rp[r.y] * iu;
+        e3 = (float)rp[r.y + 1] * iu;
+        if (r.z >= 0) e4 = (float)rp[r.z] * pick5(g.inv_in, cls_of(g, r.z));
+      }
+      x[5 * s + 0] = e0; x[5 * s + 1] = e1; x[5 * s + 2] = e2; x[5 * s + 3] = e3; x[5 * s + 4] = e4;
+      ss += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3 + e4 * e4;
+    }
+    const float rho = sqrtf(ss * (1.0f / kMlpPatch));
+    const bool live = rho > 0.f;
+    const float inv_rho = live ? 1.0f / rho : 0.f;
+#pragma unroll
+    for (int k = 0; k < kMlpPatch; ++k) x[k] *= inv_rho;
+    const int par = ((fl >> 4) & 1) | (((fl >> 5) & 1) << 1);
+    const float fbit[4] = {(fl & NF_SOLID) ? 1.f : 0.f, (fl & NF_VFIX) ? 1.f : 0.f, (fl & NF_UFIX) ? 1.f : 0.f,
+                           (fl & NF_IFACE) ? 1.f : 0.f};
+    if (MODE == MODE_FEATURES) {
+      float* row = F + a * kMlpIn;
+#pragma unroll
+      for (int k = 0; k < kMlpPatch; ++k) row[k] = x[k];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) row[kMlpPatch + k] = (k == par) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) row[kMlpPatch + 4 + k] = fbit[k];
+      rho_out[a] = rho;
+      continue;
+    }
+    if (MODE == MODE_TRAIN) {
+#pragma unroll
+      for (int k = 0; k < kMlpPatch; ++k) F[k * ld + a] = x[k];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) F[(kMlpPatch + k) * ld + a] = (k == par) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) F[(kMlpPatch + 4 + k) * ld + a] = fbit[k];
+      rho_out[a] = rho;
+    }
+    // layer 1: h = W1^T f + b1
+    float h[kMlpHidden];
+#pragma unroll
+    for (int j = 0; j < kMlpHidden; ++j) h[j] = W[kB1 + j];
+#pragma unroll
+    for (int i = 0; i < kMlpPatch; ++i) {
+      const float xi = x[i];
+      const float4* w4 = reinterpret_cast<const float4*>(W + kW1 + i * kMlpHidden);
+#pragma unroll
+      for (int q = 0; q < kMlpHidden / 4; ++q) {
+        const float4 w = w4[q];
+        h[4 * q + 0] += xi * w.x; h[4 * q + 1] += xi * w.y; h[4 * q + 2] += xi * w.z; h[4 * q + 3] += xi * w.w;
+      }
+    }
+    {
+      const float* wp = W + kW1 + (kMlpPatch + par) * kMlpHidden;
+#pragma unroll
+      for (int j = 0; j < kMlpHidden; ++j) h[j] += wp[j];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (fbit[k] != 0.f) {
+          const float* wf = W + kW1 + (kMlpPatch + 4 + k) * kMlpHidden;
+#pragma unroll
+          for (int j = 0; j < kMlpHidden; ++j) h[j] += wf[j];
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMlpHidden; ++j) {
+      if (MODE == MODE_TRAIN) H1[j * ld + a] = h[j];
+      h[j] = gelu(h[j]);
+    }
+    // layers 2 and 3, 16 hidden units at a time
+    float y[kMlpOut];
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) y[o] = W[kB3 + o];
+#pragma unroll
+    for (int j0 = 0; j0 < kMlpHidden; j0 += 16) {
+      float acc[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[k] = W[kB2 + j0 + k];
+#pragma unroll
+      for (int i = 0; i < kMlpHidden; ++i) {
+        const float hv = h[i];
+        const float4* w4 = reinterpret_cast<const float4*>(W + kW2 + i * kMlpHidden + j0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 w = w4[q];
+          acc[4 * q + 0] += hv * w.x; acc[4 * q + 1] += hv * w.y; acc[4 * q + 2] += hv * w.z; acc[4 * q + 3] += hv * w.w;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (MODE == MODE_TRAIN) H2[(j0 + k) * ld + a] = acc[k];
+        const float a2 = gelu(acc[k]);
+#pragma unroll
+        for (int o = 0; o < kMlpOut; ++o) y[o] += a2 * W[kW3 + (j0 + k) * kMlpOut + o];
+      }
+    }
+    // scatter c = y rho sigma_out on the node's free DOFs
+    const double rr = (double)rho;
+    const double sv = live && !(fl & NF_VFIX) ? rr * (double)pick5(g.sig_out, cls_of(g, me.x)) : 0.0;
+    const double su = live && !(fl & NF_UFIX) ? rr * (double)pick5(g.sig_out, cls_of(g, me.y)) : 0.0;
+    c[me.x] = sv != 0.0 ? (double)y[0] * sv : 0.0;
+    c[me.x + 1] = sv != 0.0 ? (double)y[1] * sv : 0.0;
+    c[me.y] = su != 0.0 ? (double)y[2] * su : 0.0;
+    c[me.y + 1] = su != 0.0 ? (double)y[3] * su : 0.0;
+    if (me.z >= 0) {
+      const double sp = live && !(fl & NF_PFIX) ? rr * (double)pick5(g.sig_out, cls_of(g, me.z)) : 0.0;
+      c[me.z] = sp != 0.0 ? (double)y[4] * sp : 0.0;
+    }
+  }
+}
+
+// Backward through the MLP for one node: dY from dL/dc, then dH2 and dH1.
+__global__ void __launch_bounds__(kNodeThreads) k_mlp_bwd(MlpGeom g, const uint16_t* __restrict__ w16,
+                                                          const double* __restrict__ gc, const float* __restrict__ rho_s,
+                                                          const float* __restrict__ H1, const float* __restrict__ H2,
+                                                          float* __restrict__ dY, float* __restrict__ dH1,
+                                                          float* __restrict__ dH2, int64_t ld) {
+  __shared__ __align__(16) float W[kParamsPadded];
+  load_weights(W, w16);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < g.n_nodes; a += stride) {
+    const int4 me = g.node_dof[a];
+    const int fl = me.w;
+    const double rr = (double)rho_s[a];
+    const bool live = rr > 0.0;
+    float dy[kMlpOut] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (live) {
+      if (!(fl & NF_VFIX)) {
+        const double sv = rr * (double)pick5(g.sig_out, cls_of(g, me.x));
+        dy[0] = (float)(gc[me.x] * sv);
+        dy[1] = (float)(gc[me.x + 1] * sv);
+      }
+      if (!(fl & NF_UFIX)) {
+        const double su = rr * (double)pick5(g.sig_out, cls_of(g, me.y));
+        dy[2] = (float)(gc[me.y] * su);
+        dy[3] = (float)(gc[me.y + 1] * su);
+      }
+      if (me.z >= 0 && !(fl & NF_PFIX)) dy[4] = (float)(gc[me.z] * rr * (double)pick5(g.sig_out, cls_of(g, me.z)));
+    }
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) dY[o * ld + a] = dy[o];
+    float d2[kMlpHidden];
+#pragma unroll
+    for (int j = 0; j < kMlpHidden; ++j) {
+      float s = 0.f;
+#pragma unroll
+      for (int o = 0; o < kMlpOut; ++o) s += W[kW3 + j * kMlpOut + o] * dy[o];
+      d2[j] = s * gelu_grad(H2[j * ld + a]);
+      dH2[j * ld + a] = d2[j];
+    }
+#pragma unroll 4
+    for (int i = 0; i < kMlpHidden; ++i) {
+      const float4* w4 = reinterpret_cast<const float4*>(W + kW2 + i * kMlpHidden);
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < kMlpHidden / 4; ++q) {
+        const float4 w = w4[q];
+        s += w.x * d2[4 * q] + w.y * d2[4 * q + 1] + w.z * d2[4 * q + 2] + w.w * d2[4 * q + 3];
+      }
+      dH1[i * ld + a] = s * gelu_grad(H1[i * ld + a]);
+    }
+  }
+}
+
+// partial[b][(P+1) x Q] = sum over block b's nodes of [X; 1] Y^T  (X: P rows,
+// optionally through gelu; Y: Q rows; column-major with leading dimension ld).
+constexpr int kOuterThreads = 256;
+template <bool GX>
+__global__ void __launch_bounds__(kOuterThreads) k_outer(int P, int Q, const float* __restrict__ X,
+                                                         const float* __restrict__ Y, int64_t ld, int64_t n,
+                                                         int64_t chunk, float* __restrict__ partial) {
+  __shared__ float xs[kMlpHidden][33];
+  __shared__ float ys[kMlpHidden][33];
+  const int t = threadIdx.x, tq = t & 15, tp = t >> 4;
+  float acc[5][4];
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[k][u] = 0.f;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  for (int64_t base = lo; base < hi; base += 32) {
+    const int cnt = (int)(hi - base < 32 ? hi - base : 32);
+    __syncthreads();
+    for (int e = t; e < P * 32; e += kOuterThreads) {
+      const int r = e >> 5, k = e & 31;
+      float v = k < cnt ? X[r * ld + base + k] : 0.f;
+      if (GX) v = gelu(v);
+      xs[r][k] = v;
+    }
+    for (int e = t; e < Q * 32; e += kOuterThreads) {
+      const int r = e >> 5, k = e & 31;
+      ys[r][k] = k < cnt ? Y[r * ld + base + k] : 0.f;
+    }
+    __syncthreads();
+    for (int k = 0; k < cnt; ++k) {
+      float yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = tq * 4 + u;
+        yv[u] = q < Q ? ys[q][k] : 0.f;
+      }
+#pragma unroll
+      for (int kk = 0; kk < 5; ++kk) {
+        const int p = tp + 16 * kk;
+        const float xv = p < P ? xs[p][k] : (p == P ? 1.f : 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[kk][u] += xv * yv[u];
+      }
+    }
+  }
+  float* out = partial + (size_t)blockIdx.x * (P + 1) * Q;
+#pragma unroll
+  for (int kk = 0; kk < 5; ++kk)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int p = tp + 16 * kk, q = tq * 4 + u;
+      if (p <= P && q < Q) out[p * Q + q] = acc[kk][u];
+    }
+}
+
+// grad[param(p, q)] += sum_b partial[b][p][q] in block order (FP64 sum)
+__global__ void k_reduce_grad(const float* __restrict__ partial, int G, int P, int Q, int wofs, int bofs,
+                              float* __restrict__ grad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int total = (P + 1) * Q;
+  if (e >= total) return;
+  double s = 0.0;
+  for (int b = 0; b < G; ++b) s += (double)partial[(size_t)b * total + e];
+  const int p = e / Q, q = e % Q;
+  const int idx = p < P ? wofs + p * Q + q : bofs + q;
+  grad[idx] += (float)s;
+}
+
+__global__ void k_adamw(int np, float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                        float* __restrict__ grad, uint16_t* __restrict__ w16, float lr, float b1, float b2, float eps,
+                        float wd, float bc1, float bc2, float inv_count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const float gi = grad[i] * inv_count;
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float mhat = mi / bc1, vhat = vi / bc2;
+  const float wi = w[i] - lr * (mhat / (sqrtf(vhat) + eps) + wd * w[i]);
+  w[i] = wi;
+  w16[i] = f32_to_bf16(wi);
+  grad[i] = 0.f;
+}
+
+// ---------------------------------------------------------------- FGMRES stage
+constexpr int kRT = kRedThreads;
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (threadIdx.x < (blockDim.x >> 5)) v = sh[threadIdx.x];
+  if (w == 0)
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// rp = V_j - w; part[blk] = sum of rp^2 over the block's contiguous chunk
+__global__ void __launch_bounds__(kRT) k_learned_residual(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                                          const int* __restrict__ jdev, const double* __restrict__ w,
+                                                          double* __restrict__ rp, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const double* v = V + (int64_t)(*jdev) * ldv;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double r = v[i] - w[i];
+    rp[i] = r;
+    acc += r * r;
+  }
+  acc = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// part[blk] = sum of (rp - t)^2; optionally res = rp - t
+__global__ void __launch_bounds__(kRT) k_diff_sq(int64_t n, const double* __restrict__ rp,
+                                                 const double* __restrict__ t, double* __restrict__ res,
+                                                 double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double d = rp[i] - t[i];
+    if (res) res[i] = d;
+    acc += d * d;
+  }
+  acc = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// sums of both partial arrays (fixed order); accept iff ||rp - t||^2 < tau^2 ||rp||^2
+__global__ void __launch_bounds__(kRT) k_learned_decide(const double* __restrict__ part, int np, double tau2,
+                                                        int* counters) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    a += part[k];
+    b += part[np + k];
+  }
+  a = block_sum_d(a, sh);
+  b = block_sum_d(b, sh);
+  if (threadIdx.x == 0) {
+    const int acc = (isfinite(a) && isfinite(b) && b < tau2 * a) ? 1 : 0;
+    counters[0] = acc;
+    counters[1] += acc;
+  }
+}
+
+__global__ void k_learned_commit(int64_t n, const int* __restrict__ counters, const double* __restrict__ c,
+                                 const double* __restrict__ t, double* __restrict__ Z, int64_t ldz,
+                                 const int* __restrict__ jdev, double* __restrict__ w) {
+  if (counters[0] == 0) return;
+  double* z = Z + (int64_t)(*jdev) * ldz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    z[i] += c[i];
+    w[i] += t[i];
+  }
+}
+
+__global__ void k_harvest(int64_t n, const double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev,
+                          const double* __restrict__ w, double* __restrict__ buf, int nvec) {
+  const int j = *jdev;
+  if (j >= nvec) return;
+  const double* v = V + (int64_t)j * ldv;
+  double* out = buf + (int64_t)j * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = v[i] - w[i];
+}
+
+// loss pieces: scal[0] = sum a, scal[1] = sum b, scal[2] = -2 / scal[0]
+__global__ void __launch_bounds__(kRT) k_loss_finish(const double* __restrict__ part, int np, double* scal) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    a += part[k];
+    b += part[np + k];
+  }
+  a = block_sum_d(a, sh);
+  b = block_sum_d(b, sh);
+  if (threadIdx.x == 0) {
+    scal[0] = a;
+    scal[1] = b;
+    scal[2] = a > 0.0 ? -2.0 / a : 0.0;
+  }
+}
+
+__global__ void k_scale_dev(int64_t n, const double* __restrict__ alpha, double* __restrict__ x) {
+  const double a = *alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
+__global__ void k_square_partial(int64_t n, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += x[i] * x[i];
+  acc = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+inline int grid_elem(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  return (int)(b < 1 ? 1 : b);
+}
+
+inline int grid_nodes(int64_t n_nodes) {
+  int64_t b = (n_nodes + kNodeThreads - 1) / kNodeThreads;
+  if (b > 152 * 8) b = 152 * 8;
+  return (int)(b < 1 ? 1 : b);
+}
+
+uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host API
+void learned_set_geometry(Learned& L, int64_t n, int64_t n_nodes, const int32_t* node_dof, const int32_t* patch,
+                          cudaStream_t s) {
+  require(n_nodes > 0 && node_dof && patch, "learned stage: empty node map");
+  std::vector<uint8_t> seen((size_t)n, 0);
+  auto mark = [&](int64_t d) {
+    require(d >= 0 && d < n, "learned stage: node DOF out of range");
+    require(!seen[(size_t)d], "learned stage: DOF owned by two nodes");
+    seen[(size_t)d] = 1;
+  };
+  for (int64_t a = 0; a < n_nodes; ++a) {
+    const int32_t* r = node_dof + 4 * a;
+    mark(r[0]); mark((int64_t)r[0] + 1); mark(r[1]); mark((int64_t)r[1] + 1);
+    if (r[2] >= 0) mark(r[2]);
+    else require(r[2] == -1, "learned stage: p DOF must be >= 0 or -1");
+    for (int k = 0; k < kMlpSlots; ++k) {
+      const int32_t q = patch[kMlpSlots * a + k];
+      require(q >= -1 && q < n_nodes, "learned stage: patch entry out of range");
+    }
+  }
+  for (int64_t d = 0; d < n; ++d) require(seen[(size_t)d], "learned stage: a DOF belongs to no node");
+  L.n_nodes = n_nodes;
+  L.node_dof.alloc((size_t)n_nodes);
+  L.patch.alloc((size_t)n_nodes * kMlpSlots);
+  FSI_CUDA(cudaMemcpyAsync(L.node_dof.p, node_dof, sizeof(int4) * n_nodes, cudaMemcpyHostToDevice, s));
+  FSI_CUDA(cudaMemcpyAsync(L.patch.p, patch, sizeof(int) * kMlpSlots * n_nodes, cudaMemcpyHostToDevice, s));
+  L.rp.alloc((size_t)n);
+  L.c.alloc((size_t)n);
+  L.t.alloc((size_t)n);
+  L.part.alloc(2 * kRedBlocks);
+  L.counters.alloc(2);
+  FSI_CUDA(cudaMemsetAsync(L.counters.p, 0, 2 * sizeof(int), s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+}
+
+void learned_set_weights(Learned& L, const float* sig_in, const float* sig_out, const uint16_t* params,
+                         cudaStream_t s) {
+  for (int k = 0; k < 5; ++k) {
+    require(std::isfinite(sig_in[k]) && sig_in[k] > 0.f && std::isfinite(sig_out[k]) && sig_out[k] > 0.f,
+            "learned stage: class scales must be finite and positive");
+    L.sig_in[k] = sig_in[k];
+    L.sig_out[k] = sig_out[k];
+  }
+  for (int i = 0; i < kMlpParams; ++i)
+    require(std::isfinite(bf16_to_f32(params[i])), "learned stage: non-finite weight");
+  if (!L.w16.p) L.w16.alloc(kMlpParams);
+  FSI_CUDA(cudaMemcpyAsync(L.w16.p, params, sizeof(uint16_t) * kMlpParams, cudaMemcpyHostToDevice, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  L.has_weights = true;
+}
+
+namespace {
+const char kMagic[8] = {'F', 'S', 'I', 'M', 'L', 'P', '0', '1'};
+}
+
+void learned_load_file(Learned& L, const char* path, cudaStream_t s) {
+  std::ifstream f(path, std::ios::binary);
+  require((bool)f, std::string("learned stage: cannot open ") + path);
+  char magic[8];
+  int32_t shape[4];
+  float scales[10];
+  std::vector<uint16_t> params(kMlpParams);
+  f.read(magic, 8);
+  f.read(reinterpret_cast<char*>(shape), sizeof(shape));
+  f.read(reinterpret_cast<char*>(scales), sizeof(scales));
+  f.read(reinterpret_cast<char*>(params.data()), sizeof(uint16_t) * kMlpParams);
+  require((bool)f && std::memcmp(magic, kMagic, 8) == 0, "learned stage: not a weights file");
+  require(shape[0] == kMlpIn && shape[1] == kMlpHidden && shape[2] == kMlpOut, "learned stage: unexpected MLP shape");
+  learned_set_weights(L, scales, scales + 5, params.data(), s);
+}
+
+void learned_save_file(const char* path, const float* sig_in, const float* sig_out, const uint16_t* params) {
+  std::ofstream f(path, std::ios::binary | std::ios::trunc);
+  require((bool)f, std::string("learned stage: cannot write ") + path);
+  const int32_t shape[4] = {kMlpIn, kMlpHidden, kMlpOut, 0};
+  f.write(kMagic, 8);
+  f.write(reinterpret_cast<const char*>(shape), sizeof(shape));
+  f.write(reinterpret_cast<const char*>(sig_in), 5 * sizeof(float));
+  f.write(reinterpret_cast<const char*>(sig_out), 5 * sizeof(float));
+  f.write(reinterpret_cast<const char*>(params), sizeof(uint16_t) * kMlpParams);
+  require((bool)f, std::string("learned stage: write failed for ") + path);
+}
+
+MlpGeom learned_geom(const Learned& L, const int64_t off[6]) {
+  MlpGeom g;
+  g.n_nodes = L.n_nodes;
+  g.node_dof = L.node_dof.p;
+  g.patch = L.patch.p;
+  g.off1 = off[1]; g.off2 = off[2]; g.off3 = off[3]; g.off4 = off[4];
+  for (int k = 0; k < 5; ++k) {
+    g.sig_in[k] = L.sig_in[k];
+    g.inv_in[k] = 1.0f / L.sig_in[k];
+    g.sig_out[k] = L.sig_out[k];
+  }
+  return g;
+}
+
+
+void mlp_apply(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, cudaStream_t s) {
+  k_mlp<MODE_APPLY><<<grid_nodes(g.n_nodes), kNodeThreads, 0, s>>>(g, w16, rp, c, nullptr, nullptr, nullptr, nullptr,
+                                                                   0);
+  FSI_CHECK_LAUNCH();
+}
+
+void mlp_features(const MlpGeom& g, const double* rp, float* F, float* rho, cudaStream_t s) {
+  k_mlp<MODE_FEATURES><<<grid_nodes(g.n_nodes), kNodeThreads, 0, s>>>(g, nullptr, rp, nullptr, F, rho, nullptr,
+                                                                      nullptr, 0);
+  FSI_CHECK_LAUNCH();
+}
+
+void learned_residual(int64_t n, const double* V, int64_t ldv, const int* jdev, const double* w, double* rp,
+                      double* part, cudaStream_t s) {
+  k_learned_residual<<<kRedBlocks, kRT, 0, s>>>(n, V, ldv, jdev, w, rp, part);
+  FSI_CHECK_LAUNCH();
+}
+
+void learned_decide(int64_t n, const double* rp, const double* t, double tau, double* part, int* counters,
+                    cudaStream_t s) {
+  k_diff_sq<<<kRedBlocks, kRT, 0, s>>>(n, rp, t, nullptr, part + kRedBlocks);
+  FSI_CHECK_LAUNCH();
+  k_learned_decide<<<1, kRT, 0, s>>>(part, kRedBlocks, tau * tau, counters);
+  FSI_CHECK_LAUNCH();
+}
+
+void learned_commit(int64_t n, const int* counters, const double* c, const double* t, double* Z, int64_t ldz,
+                    const int* jdev, double* w, cudaStream_t s) {
+  k_learned_commit<<<grid_elem(n), 256, 0, s>>>(n, counters, c, t, Z, ldz, jdev, w);
+  FSI_CHECK_LAUNCH();
+}
+
+void harvest_residual(int64_t n, const double* V, int64_t ldv, const int* jdev, const double* w, double* buf,
+                      int nvec, cudaStream_t s) {
+  k_harvest<<<grid_elem(n), 256, 0, s>>>(n, V, ldv, jdev, w, buf, nvec);
+  FSI_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------- training
+Trainer::~Trainer() {
+  if (pinned) cudaFreeHost(pinned);
+}
+
+void trainer_init(Trainer& T, const TrainParams& p) {
+  for (int k = 0; k < 5; ++k)
+    require(std::isfinite(p.sig_in[k]) && p.sig_in[k] > 0.f && std::isfinite(p.sig_out[k]) && p.sig_out[k] > 0.f,
+            "trainer: class scales must be finite and positive");
+  require(p.lr > 0 && p.beta1 >= 0 && p.beta1 < 1 && p.beta2 >= 0 && p.beta2 < 1 && p.eps > 0 && p.weight_decay >= 0,
+          "trainer: bad AdamW parameters");
+  T.prm = p;
+  // Glorot-uniform weights from a SplitMix64 stream (one draw per parameter
+  // index), biases zero, last layer scaled by init_out_scale
+  std::vector<float> w(kMlpParams, 0.f);
+  auto fill = [&](int ofs, int fan_in, int fan_out, double scale) {
+    const double lim = std::sqrt(6.0 / (fan_in + fan_out)) * scale;
+    for (int i = 0; i < fan_in * fan_out; ++i) {
+      const uint64_t r = splitmix64((p.seed << 32) + (uint64_t)(ofs + i));
+      const double u = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+      w[ofs + i] = (float)((2.0 * u - 1.0) * lim);
+    }
+  };
+  fill(kW1, kMlpIn, kMlpHidden, 1.0);
+  fill(kW2, kMlpHidden, kMlpHidden, 1.0);
+  fill(kW3, kMlpHidden, kMlpOut, p.init_out_scale);
+  T.master.alloc(kMlpParams);
+  T.m.alloc(kMlpParams);
+  T.v.alloc(kMlpParams);
+  T.grad.alloc(kMlpParams);
+  T.w16.alloc(kMlpParams);
+  T.scal.alloc(4);
+  T.part.alloc(2 * kRedBlocks);
+  if (!T.pinned) FSI_CUDA(cudaMallocHost(&T.pinned, 4 * sizeof(double)));
+  trainer_set_master(T, w.data());
+}
+
+void trainer_set_master(Trainer& T, const float* w) {
+  std::vector<uint16_t> h(kMlpParams);
+  for (int i = 0; i < kMlpParams; ++i) {
+    require(std::isfinite(w[i]), "trainer: non-finite weight");
+    h[i] = f32_to_bf16(w[i]);
+  }
+  FSI_CUDA(cudaMemcpy(T.master.p, w, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice));
+  FSI_CUDA(cudaMemcpy(T.w16.p, h.data(), sizeof(uint16_t) * kMlpParams, cudaMemcpyHostToDevice));
+  FSI_CUDA(cudaMemset(T.m.p, 0, sizeof(float) * kMlpParams));
+  FSI_CUDA(cudaMemset(T.v.p, 0, sizeof(float) * kMlpParams));
+  FSI_CUDA(cudaMemset(T.grad.p, 0, sizeof(float) * kMlpParams));
+  T.grads = 0;
+  T.steps = 0;
+}
+
+void apply_operator_t(Context& C, const double* x, double* y) {
+  if (!C.At_built) {
+    bsr_transpose(C.AVV, C.AVVt, C.s);
+    bsr_transpose(C.AVP, C.AVPt, C.s);
+    bsr_transpose(C.APV, C.APVt, C.s);
+    bsr_transpose(C.APP, C.APPt, C.s);
+    FSI_CUDA(cudaStreamSynchronize(C.s));
+    C.At_built = true;
+  }
+  const int64_t nv = C.off[4];
+  // A^T = [[AVV^T, APV^T], [AVP^T, APP^T]]
+  spmv2_axpby<double>(C.AVVt, x, &C.APVt, x + nv, 1.0, 0.0, y, C.s);
+  spmv2_axpby<double>(C.AVPt, x, &C.APPt, x + nv, 1.0, 0.0, y + nv, C.s);
+}
+
+double trainer_step(Trainer& T, Context& C, const double* rp, bool grad) {
+  Learned& L = C.learned;
+  require(L.n_nodes > 0, "trainer: fsi_learned_setup has not been called on this context");
+  const int64_t n = C.n, nn = L.n_nodes;
+  cudaStream_t s = C.s;
+  if (T.cap_nodes < nn) {
+    T.cap_nodes = nn;
+    T.F.alloc((size_t)kMlpIn * nn);
+    T.rho.alloc((size_t)nn);
+    T.H1.alloc((size_t)kMlpHidden * nn);
+    T.H2.alloc((size_t)kMlpHidden * nn);
+    T.dY.alloc((size_t)kMlpOut * nn);
+    T.dH1.alloc((size_t)kMlpHidden * nn);
+    T.dH2.alloc((size_t)kMlpHidden * nn);
+  }
+  if (T.cap_n < n) {
+    T.cap_n = n;
+    T.c.alloc((size_t)n);
+    T.t.alloc((size_t)n);
+    T.res.alloc((size_t)n);
+    T.g.alloc((size_t)n);
+  }
+  MlpGeom g = learned_geom(L, C.off);
+  for (int k = 0; k < 5; ++k) {
+    g.sig_in[k] = T.prm.sig_in[k];
+    g.inv_in[k] = 1.0f / T.prm.sig_in[k];
+    g.sig_out[k] = T.prm.sig_out[k];
+  }
+  const int64_t ld = T.cap_nodes;
+  k_mlp<MODE_TRAIN><<<grid_nodes(nn), kNodeThreads, 0, s>>>(g, T.w16.p, rp, T.c.p, T.F.p, T.rho.p, T.H1.p, T.H2.p,
+                                                            ld);
+  FSI_CHECK_LAUNCH();
+  apply_operator(C, T.c.p, T.t.p);
+  k_square_partial<<<kRedBlocks, kRT, 0, s>>>(n, rp, T.part.p);
+  FSI_CHECK_LAUNCH();
+  k_diff_sq<<<kRedBlocks, kRT, 0, s>>>(n, rp, T.t.p, T.res.p, T.part.p + kRedBlocks);
+  FSI_CHECK_LAUNCH();
+  k_loss_finish<<<1, kRT, 0, s>>>(T.part.p, kRedBlocks, T.scal.p);
+  FSI_CHECK_LAUNCH();
+  if (!grad) {
+    FSI_CUDA(cudaMemcpyAsync(T.pinned, T.scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FSI_CUDA(cudaStreamSynchronize(s));
+    return T.pinned[0] > 0.0 ? T.pinned[1] / T.pinned[0] : 0.0;
+  }
+  k_scale_dev<<<grid_elem(n), 256, 0, s>>>(n, T.scal.p + 2, T.res.p);   // res = -2 (r' - A c) / ||r'||^2
+  FSI_CHECK_LAUNCH();
+  apply_operator_t(C, T.res.p, T.g.p);                                     // dL/dc
+  k_mlp_bwd<<<grid_nodes(nn), kNodeThreads, 0, s>>>(g, T.w16.p, T.g.p, T.rho.p, T.H1.p, T.H2.p, T.dY.p, T.dH1.p,
+                                                    T.dH2.p, ld);
+  FSI_CHECK_LAUNCH();
+  // weight gradients: dW1 = [F;1] dH1^T, dW2 = [gelu(H1);1] dH2^T, dW3 = [gelu(H2);1] dY^T
+  const int G = (int)std::min<int64_t>(2 * 152, std::max<int64_t>(1, (nn + 255) / 256));
+  const int64_t chunk = ((nn + G - 1) / G + 31) / 32 * 32;
+  const size_t need = (size_t)G * (kMlpHidden + 1) * kMlpHidden;
+  if (T.partial.n < need) T.partial.alloc(need);
+  struct Lyr { int P, Q; const float* X; const float* Y; bool gx; int wofs, bofs; };
+  const Lyr lyr[3] = {{kMlpIn, kMlpHidden, T.F.p, T.dH1.p, false, kW1, kB1},
+                      {kMlpHidden, kMlpHidden, T.H1.p, T.dH2.p, true, kW2, kB2},
+                      {kMlpHidden, kMlpOut, T.H2.p, T.dY.p, true, kW3, kB3}};
+  for (const Lyr& l : lyr) {
+    if (l.gx) k_outer<true><<<G, kOuterThreads, 0, s>>>(l.P, l.Q, l.X, l.Y, ld, nn, chunk, T.partial.p);
+    else k_outer<false><<<G, kOuterThreads, 0, s>>>(l.P, l.Q, l.X, l.Y, ld, nn, chunk, T.partial.p);
+    FSI_CHECK_LAUNCH();
+    const int total = (l.P + 1) * l.Q;
+    k_reduce_grad<<<div_up(total, 256), 256, 0, s>>>(T.partial.p, G, l.P, l.Q, l.wofs, l.bofs, T.grad.p);
+    FSI_CHECK_LAUNCH();
+  }
+  ++T.grads;
+  FSI_CUDA(cudaMemcpyAsync(T.pinned, T.scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  return T.pinned[0] > 0.0 ? T.pinned[1] / T.pinned[0] : 0.0;
+}
+
+void trainer_update(Trainer& T, cudaStream_t s, double lr) {
+  require(T.grads > 0, "trainer: no gradient accumulated since the last update");
+  require(std::isfinite(lr), "trainer: learning rate must be finite");
+  if (lr <= 0.0) lr = T.prm.lr;
+  ++T.steps;
+  const double bc1 = 1.0 - std::pow(T.prm.beta1, (double)T.steps);
+  const double bc2 = 1.0 - std::pow(T.prm.beta2, (double)T.steps);
+  k_adamw<<<div_up(kMlpParams, 256), 256, 0, s>>>(kMlpParams, T.master.p, T.m.p, T.v.p, T.grad.p, T.w16.p,
+                                                  (float)lr, (float)T.prm.beta1, (float)T.prm.beta2,
+                                                  (float)T.prm.eps, (float)T.prm.weight_decay, (float)bc1, (float)bc2,
+                                                  1.0f / (float)T.grads);
+  FSI_CHECK_LAUNCH();
+  T.grads = 0;
+  FSI_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace fsi

@@ -1,0 +1,109 @@
+// Learned correction stage of the FGMRES solve (the learned form; an extra
+// smoothing step after the Alg. 2 preconditioner, not part of the paper).
+//
+// Per Q2 node a of a 2D mesh, with its 3x3 lattice patch N(a):
+//   x_{s,k} = r'[dof_k(N_s(a))] / sigma_in[class]   k = v_x v_y u_x u_y p (0 if absent)
+//   rho_a   = sqrt(mean of the 45 squares)
+//   f_a     = [x / rho_a, one-hot lattice parity (4), solid / v fixed / u fixed / interface (4)]
+//   y_a     = W3^T gelu(W2^T gelu(W1^T f_a + b1) + b2) + b3        (53 -> 64 -> 64 -> 5)
+//   c[dof_k(a)] = y_{a,k} rho_a sigma_out[class]     (0 on fixed rows and at rho_a = 0)
+// Weights are bfloat16, products and sums FP32; the correction is written in FP64.
+//
+// Training minimises the residual left by the correction, ||r' - A c(r')||^2 / ||r'||^2
+// (the error e - c of the pair (r', e = A^-1 r') measured in the residual norm that
+// FGMRES's acceptance test compares), by backpropagation through the MLP with the
+// gradient dL/dc = -2 A^T (r' - A c) / ||r'||^2, and AdamW on FP32 master weights.
+#pragma once
+#include "common.cuh"
+
+#include <cstdint>
+
+namespace fsi {
+
+constexpr int kMlpIn = 53, kMlpHidden = 64, kMlpOut = 5, kMlpPatch = 45, kMlpSlots = 9;
+constexpr int kW1 = 0, kB1 = kW1 + kMlpIn * kMlpHidden, kW2 = kB1 + kMlpHidden,
+              kB2 = kW2 + kMlpHidden * kMlpHidden, kW3 = kB2 + kMlpHidden,
+              kB3 = kW3 + kMlpHidden * kMlpOut, kMlpParams = kB3 + kMlpOut;
+
+// Node flags (fourth entry of a node's int4 record).
+enum NodeFlags { NF_SOLID = 1, NF_VFIX = 2, NF_UFIX = 4, NF_IFACE = 8, NF_IODD = 16, NF_JODD = 32, NF_PFIX = 64 };
+
+// Everything the per-node kernels read besides the vectors (passed by value).
+struct MlpGeom {
+  int64_t n_nodes = 0;
+  const int4* node_dof = nullptr;   // {first v DOF, first u DOF, p DOF or -1, flags}
+  const int* patch = nullptr;       // 9 per node, -1 outside the mesh
+  int64_t off1 = 0, off2 = 0, off3 = 0, off4 = 0;   // class boundaries s_v, s_u, f_v, f_p
+  float sig_in[5] = {1, 1, 1, 1, 1};
+  float inv_in[5] = {1, 1, 1, 1, 1};   // 1 / sig_in
+  float sig_out[5] = {1, 1, 1, 1, 1};
+};
+
+// The stage as one context holds it.
+struct Learned {
+  int64_t n_nodes = 0;
+  DBuf<int4> node_dof;
+  DBuf<int> patch;
+  DBuf<uint16_t> w16;          // kMlpParams bfloat16 parameters
+  float sig_in[5] = {1, 1, 1, 1, 1}, sig_out[5] = {1, 1, 1, 1, 1};
+  bool has_weights = false;
+  DBuf<double> rp, c, t;       // r', correction, A c (length n)
+  DBuf<double> part;           // 2 x kRedBlocks reduction partials
+  DBuf<int> counters;          // [0] accept flag of the current iteration, [1] corrections accepted
+};
+
+// Validate and upload the node map (host arrays) of a system with n DOFs.
+void learned_set_geometry(Learned& L, int64_t n, int64_t n_nodes, const int32_t* node_dof, const int32_t* patch,
+                          cudaStream_t s);
+// Set weights (host bfloat16 parameters and class scales).
+void learned_set_weights(Learned& L, const float* sig_in, const float* sig_out, const uint16_t* params,
+                         cudaStream_t s);
+// Read a weights file (8-byte magic "FSIMLP01", int32 n_in n_hidden n_out 0,
+// float32 sigma_in[5] sigma_out[5], then the bfloat16 parameters, little endian).
+void learned_load_file(Learned& L, const char* path, cudaStream_t s);
+void learned_save_file(const char* path, const float* sig_in, const float* sig_out, const uint16_t* params);
+MlpGeom learned_geom(const Learned& L, const int64_t off[6]);
+
+// c = MLP(r'), every DOF of c written.
+void mlp_apply(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, cudaStream_t s);
+// Feature rows (node-major [n_nodes][53]) and rho of r'.
+void mlp_features(const MlpGeom& g, const double* rp, float* F, float* rho, cudaStream_t s);
+
+// FGMRES stage pieces (the column index j is read on the device):
+// rp = V_j - w and per-block sums of rp^2 into part[0, kRedBlocks)
+void learned_residual(int64_t n, const double* V, int64_t ldv, const int* jdev, const double* w, double* rp,
+                      double* part, cudaStream_t s);
+// per-block sums of (rp - t)^2 into part[kRedBlocks, 2 kRedBlocks); then the
+// accept flag (sum_b < tau^2 sum_a, both finite) into counters[0], counters[1] += flag
+void learned_decide(int64_t n, const double* rp, const double* t, double tau, double* part, int* counters,
+                    cudaStream_t s);
+// if counters[0]: Z_j += c, w += t
+void learned_commit(int64_t n, const int* counters, const double* c, const double* t, double* Z, int64_t ldz,
+                    const int* jdev, double* w, cudaStream_t s);
+// buf[j*n + i] = V_j[i] - w[i] for j < nvec (harvest of the preconditioned residuals)
+void harvest_residual(int64_t n, const double* V, int64_t ldv, const int* jdev, const double* w, double* buf,
+                      int nvec, cudaStream_t s);
+
+// ---------------------------------------------------------------- training
+struct TrainParams {
+  double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8, weight_decay = 0.0;
+  uint64_t seed = 0;
+  double init_out_scale = 0.01;   // last layer initialised this much smaller than Glorot
+  float sig_in[5] = {1, 1, 1, 1, 1}, sig_out[5] = {1, 1, 1, 1, 1};
+};
+
+struct Trainer {
+  TrainParams prm;
+  int64_t cap_nodes = 0, cap_n = 0;
+  DBuf<float> master, m, v, grad;  // kMlpParams each
+  DBuf<uint16_t> w16;
+  DBuf<float> F, rho, H1, H2, dY, dH1, dH2;   // column-major: row k of node a at [k * cap_nodes + a]
+  DBuf<float> partial;
+  DBuf<double> c, t, res, g, part, scal;
+  int grads = 0;        // gradient contributions since the last update
+  int64_t steps = 0;    // AdamW steps taken
+  double* pinned = nullptr;
+  ~Trainer();
+};
+
+}  // namespace fsi

@@ -465,6 +465,17 @@ void iteration_body(Context& C) {
   k_col_out<T><<<grid_n(n), 256, 0, C.s>>>(n, W.out.p, C.zfix.p, C.Z.p, n, C.jdev.p);
   FSI_CHECK_LAUNCH();
   apply_operator(C, C.zfix.p, C.wfix.p);
+  if (C.harvest) harvest_residual(n, C.V.p, n, C.jdev.p, C.wfix.p, C.harvest, C.harvest_n, C.s);
+  if (C.prm.flags & LEARNED) {
+    // learned stage: r' = v_j - A z_j, c = MLP(r'), t = A c; take z_j + c only
+    // when ||r' - t|| < tau ||r'|| (otherwise the plain preconditioner's z_j stands)
+    Learned& L = C.learned;
+    learned_residual(n, C.V.p, n, C.jdev.p, C.wfix.p, L.rp.p, L.part.p, C.s);
+    mlp_apply(learned_geom(L, C.off), L.w16.p, L.rp.p, L.c.p, C.s);
+    apply_operator(C, L.c.p, L.t.p);
+    learned_decide(n, L.rp.p, L.t.p, C.prm.learned_accept, L.part.p, L.counters.p, C.s);
+    learned_commit(n, L.counters.p, L.c.p, L.t.p, C.Z.p, n, C.jdev.p, C.wfix.p, C.s);
+  }
   mdot(n, C.V.p, n, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h1.p, m + 1, C.s);
   maxpy(n, C.V.p, n, C.jdev.p, 1, C.h1.p, 1.0, C.wfix.p, nullptr, C.s);
   mdot(n, C.V.p, n, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h2.p, m + 1, C.s);
@@ -483,7 +494,9 @@ void run_iteration(Context& C) {
     if (C.precision == 1) iteration_body<float>(C); else iteration_body<double>(C);
     return;
   }
-  if (!C.iter_graph || C.iter_graph_prec != C.precision) {
+  const bool learned = (C.prm.flags & LEARNED) != 0;
+  if (!C.iter_graph || C.iter_graph_prec != C.precision || C.iter_graph_learned != learned ||
+      C.iter_graph_harvest != C.harvest || C.iter_graph_harvest_n != C.harvest_n) {
     if (C.iter_graph) { cudaGraphExecDestroy(C.iter_graph); C.iter_graph = nullptr; }
     cudaGraph_t g;
     FSI_CUDA(cudaStreamBeginCapture(C.s, cudaStreamCaptureModeThreadLocal));
@@ -500,6 +513,9 @@ void run_iteration(Context& C) {
     FSI_CUDA(cudaGraphInstantiate(&C.iter_graph, g, 0));
     cudaGraphDestroy(g);
     C.iter_graph_prec = C.precision;
+    C.iter_graph_learned = learned;
+    C.iter_graph_harvest = C.harvest;
+    C.iter_graph_harvest_n = C.harvest_n;
   }
   FSI_CUDA(cudaGraphLaunch(C.iter_graph, C.s));
   g_kernel_launches += C.graph_kernels;
@@ -511,7 +527,12 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
   auto t0 = clk::now();
   const int64_t launches0 = g_kernel_launches;
   require(C.built, "fsi_solve before fsi_precond_build");
+  if (C.prm.flags & LEARNED)
+    require(C.learned.n_nodes > 0 && C.learned.has_weights,
+            "FSI_LEARNED needs fsi_learned_setup and weights (fsi_learned_load or fsi_precond_build's path)");
   ensure_krylov(C);
+  C.last_accepted = 0;
+  if (C.prm.flags & LEARNED) FSI_CUDA(cudaMemsetAsync(C.learned.counters.p, 0, 2 * sizeof(int), C.s));
   const int64_t n = C.n;
   const int m = C.prm.restart;
   C.hist.clear();
@@ -571,6 +592,8 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
     ++C.last_cycles;
   }
   FSI_CUDA(cudaStreamSynchronize(C.s));
+  if (C.prm.flags & LEARNED)
+    FSI_CUDA(cudaMemcpy(&C.last_accepted, C.learned.counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
   C.last_iters = total;
   C.last_true_relres = relres;
   if (nonfinite) status = ENONFINITE_;

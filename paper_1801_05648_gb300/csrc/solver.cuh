@@ -3,6 +3,7 @@
 // sub-solves) and the right-preconditioned FGMRES outer iteration.
 #pragma once
 #include "amg.cuh"
+#include "learned.cuh"
 #include "sparse_util.cuh"
 
 #include <string>
@@ -21,9 +22,10 @@ struct SolverParams {
   double mass_ratio = 8.0;
   double spmv_wave_fraction = 1.0;
   int spmv_unroll = 4;
+  double learned_accept = 0.1;   // accept the learned correction when ||r' - A c|| < this * ||r'||
 };
 
-enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8 };
+enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8, LEARNED = 16 };
 
 template <class T>
 struct PrecWork {
@@ -59,6 +61,13 @@ struct Context {
   PrecWork<double> pw64;
   PrecWork<float> pw32;
   DBuf<double> solid_B;       // near-nullspace of S_hat (rigid-body modes)
+  // learned correction stage, its training operator A^T, and the residual harvest
+  Learned learned;
+  Bsr AVVt, AVPt, APVt, APPt;
+  bool At_built = false;
+  double* harvest = nullptr;  // device, harvest_n x n: V_j - A z_j of the first iterations
+  int harvest_n = 0;
+  int last_accepted = 0;      // learned corrections taken in the last solve
   // FGMRES storage
   int m_alloc = 0;
   DBuf<double> V, Z, Hh, cs, sn, g, y, h1, h2, scal, partials, npart, zfix, wfix, rvec;
@@ -68,6 +77,9 @@ struct Context {
   int* pinned_j = nullptr;    // pinned host staging for the iteration index
   cudaGraphExec_t iter_graph = nullptr;
   int iter_graph_prec = -1;
+  bool iter_graph_learned = false;
+  const double* iter_graph_harvest = nullptr;
+  int iter_graph_harvest_n = 0;
   int64_t graph_kernels = 0;  // kernel launches inside one replay of iter_graph
   int64_t last_launches = 0;  // kernels launched by the last solve
   // stats
@@ -88,5 +100,16 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol);
 template <class T> void apply_block(Context& C, int which, const T* in, T* out);
 double precond_bytes(const Context& C, int vb);
 double operator_bytes(const Context& C);
+// y = A^T x (transposed blocks built on first use)
+void apply_operator_t(Context& C, const double* x, double* y);
+
+// Training of the learned stage (learned.cu)
+void trainer_init(Trainer& T, const TrainParams& p);
+void trainer_set_master(Trainer& T, const float* w);
+// one residual vector r' of context C: loss ||r' - A c||^2 / ||r'||^2, gradient
+// accumulated when grad is true
+double trainer_step(Trainer& T, Context& C, const double* rp, bool grad = true);
+// AdamW with the mean of the accumulated gradients at learning rate lr (<= 0: the parameters' rate)
+void trainer_update(Trainer& T, cudaStream_t s, double lr = 0.0);
 
 }  // namespace fsi

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libfsi.so")
 
 FSI_OK, FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA, FSI_ENOTCONV, FSI_EBREAKDOWN, FSI_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 FSI_FP64, FSI_FP32_AMG = 0, 1
-FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE = 1, 2, 4, 8
+FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_LEARNED = 1, 2, 4, 8, 16
+FSI_MLP_PARAMS, FSI_MLP_INPUTS = 7941, 53
 STATUS_NAMES = {0: "FSI_OK", -1: "FSI_EINVAL", -2: "FSI_ENOMEM", -3: "FSI_ECUDA", -4: "FSI_ENOTCONV",
                 -5: "FSI_EBREAKDOWN", -6: "FSI_ENONFINITE"}
 BLOCKS = {"mesh": 0, "solid_schur": 1, "fluid_velocity": 2, "pressure_schur": 3, "solid_mass": 4,
@@ -26,7 +27,11 @@ BLOCKS = {"mesh": 0, "solid_schur": 1, "fluid_velocity": 2, "pressure_schur": 3,
 # Every symbol include/fsi.h declares.
 EXPORTED = ["fsi_default_params", "fsi_setup", "fsi_precond_build", "fsi_solve", "fsi_free", "fsi_last_error",
             "fsi_apply_operator", "fsi_apply_block", "fsi_smoother_step", "fsi_amg_info", "fsi_amg_export",
-            "fsi_mass_solve_noalloc"]
+            "fsi_mass_solve_noalloc", "fsi_learned_setup", "fsi_learned_load", "fsi_learned_set_weights",
+            "fsi_learned_apply", "fsi_learned_features", "fsi_set_harvest", "fsi_default_train_params",
+            "fsi_trainer_create", "fsi_trainer_step", "fsi_trainer_loss", "fsi_trainer_update",
+            "fsi_trainer_set_master", "fsi_trainer_get", "fsi_trainer_save", "fsi_trainer_free", "fsi_set_flags",
+            "fsi_set_learned_accept"]
 
 
 class FSIError(RuntimeError):
@@ -43,7 +48,8 @@ class Params(ctypes.Structure):
                 ("presmooth", ctypes.c_int), ("postsmooth", ctypes.c_int), ("vcycles_mesh", ctypes.c_int),
                 ("vcycles_solid", ctypes.c_int), ("vcycles_fluid", ctypes.c_int),
                 ("vcycles_pressure", ctypes.c_int), ("mass_degree", ctypes.c_int), ("mass_ratio", ctypes.c_double),
-                ("spmv_wave_fraction", ctypes.c_double), ("spmv_unroll", ctypes.c_int)]
+                ("spmv_wave_fraction", ctypes.c_double), ("spmv_unroll", ctypes.c_int),
+                ("learned_accept", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -52,7 +58,14 @@ class Stats(ctypes.Structure):
                 ("precond_build_s", ctypes.c_double), ("solve_s", ctypes.c_double),
                 ("operator_bytes", ctypes.c_double), ("precond_bytes", ctypes.c_double),
                 ("relres_hist", ctypes.POINTER(ctypes.c_double)), ("hist_len", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("learned_accepted", ctypes.c_int)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("init_out_scale", ctypes.c_double), ("sigma_in", ctypes.c_float * 5),
+                ("sigma_out", ctypes.c_float * 5)]
 
 
 @dataclass
@@ -68,6 +81,7 @@ class SolveStats:
     precond_bytes: float
     history: list
     kernel_launches: int
+    learned_accepted: int = 0
 
 
 _lib = None
@@ -108,6 +122,31 @@ def load_library(path: str = LIB_PATH):
     lib.fsi_amg_export.restype = ctypes.c_int
     lib.fsi_mass_solve_noalloc.argtypes = [vp, vp, vp]
     lib.fsi_mass_solve_noalloc.restype = ctypes.c_int
+    f32p, u16p = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint16)
+    lib.fsi_learned_setup.argtypes = [vp, ctypes.c_int64, i32p, i32p]
+    lib.fsi_learned_load.argtypes = [vp, ctypes.c_char_p]
+    lib.fsi_learned_set_weights.argtypes = [vp, f32p, f32p, u16p]
+    lib.fsi_learned_apply.argtypes = [vp, vp, vp]
+    lib.fsi_learned_features.argtypes = [vp, vp, vp, vp]
+    lib.fsi_set_harvest.argtypes = [vp, vp, ctypes.c_int]
+    lib.fsi_default_train_params.argtypes = [ctypes.POINTER(TrainParams)]
+    lib.fsi_default_train_params.restype = None
+    lib.fsi_trainer_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(TrainParams)]
+    lib.fsi_trainer_step.argtypes = [vp, vp, vp, f64p]
+    lib.fsi_trainer_loss.argtypes = [vp, vp, vp, f64p]
+    lib.fsi_trainer_update.argtypes = [vp, vp, ctypes.c_double]
+    lib.fsi_set_flags.argtypes = [vp, ctypes.c_int]
+    lib.fsi_set_learned_accept.argtypes = [vp, ctypes.c_double]
+    lib.fsi_trainer_set_master.argtypes = [vp, f32p]
+    lib.fsi_trainer_get.argtypes = [vp, f32p, u16p, f32p]
+    lib.fsi_trainer_save.argtypes = [vp, ctypes.c_char_p]
+    lib.fsi_trainer_free.argtypes = [vp]
+    lib.fsi_trainer_free.restype = None
+    for name in ("fsi_learned_setup", "fsi_learned_load", "fsi_learned_set_weights", "fsi_learned_apply",
+                 "fsi_learned_features", "fsi_set_harvest", "fsi_trainer_create", "fsi_trainer_step",
+                 "fsi_trainer_loss", "fsi_trainer_update", "fsi_trainer_set_master", "fsi_trainer_get",
+                 "fsi_trainer_save", "fsi_set_flags", "fsi_set_learned_accept"):
+        getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -126,10 +165,11 @@ def _np_ptr(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
-def _dev_ptr(t):
+def _dev_ptr(t, dtype=None):
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise TypeError("expected a contiguous float64 CUDA tensor")
+    dtype = torch.float64 if dtype is None else dtype
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous {dtype} CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -147,6 +187,7 @@ class FSISolver:
         offsets = np.ascontiguousarray(offsets, np.int64)
         self.n = int(offsets[5])
         self.dim = dim
+        self.flags = int(params.flags) if params is not None else 0
         self.offsets = offsets.copy()
         coords = None if node_coords is None else np.ascontiguousarray(node_coords, np.float64)
         import torch
@@ -177,9 +218,10 @@ class FSISolver:
         import torch
         self.stream.wait_stream(torch.cuda.current_stream())
 
-    def precond_build(self, precision: str | int = "fp64"):
+    def precond_build(self, precision: str | int = "fp64", learned_weights: str | None = None):
         prec = {"fp64": FSI_FP64, "fp32": FSI_FP32_AMG}.get(precision, precision)
-        self._check(self._lib.fsi_precond_build(self._h, int(prec), None))
+        path = None if learned_weights is None else os.fsencode(learned_weights)
+        self._check(self._lib.fsi_precond_build(self._h, int(prec), path))
 
     def solve(self, rhs, x, rtol=1e-8, raise_on_error=True) -> SolveStats:
         self._order()
@@ -187,7 +229,8 @@ class FSISolver:
         rc = self._lib.fsi_solve(self._h, _dev_ptr(rhs), _dev_ptr(x), rtol, ctypes.byref(st))
         hist = [st.relres_hist[i] for i in range(st.hist_len)] if st.hist_len else []
         out = SolveStats(st.iters, st.cycles, st.status, st.true_relres, st.setup_s, st.precond_build_s,
-                         st.solve_s, st.operator_bytes, st.precond_bytes, hist, st.kernel_launches)
+                         st.solve_s, st.operator_bytes, st.precond_bytes, hist, st.kernel_launches,
+                         st.learned_accepted)
         if rc != FSI_OK and raise_on_error:
             raise FSIError(rc, self._lib.fsi_last_error(self._h).decode())
         return out
@@ -259,6 +302,69 @@ class FSISolver:
             return rp, ci, va
         raise ValueError(what)
 
+    def set_flags(self, flags: int):
+        """Run-time flags (FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_LEARNED)."""
+        self._check(self._lib.fsi_set_flags(self._h, int(flags)))
+        self.flags = int(flags)
+
+    def set_learned_accept(self, tau: float):
+        """Accept the learned correction only when ||r' - A c|| < tau ||r'||."""
+        self._check(self._lib.fsi_set_learned_accept(self._h, float(tau)))
+
+    # ------------------------------------------------------------ learned stage
+    def learned_setup(self, node_dof, patch):
+        """Node map (host int32 arrays [n_nodes, 4] and [n_nodes, 9]) for the learned stage."""
+        nd = np.ascontiguousarray(node_dof, np.int32)
+        pt = np.ascontiguousarray(patch, np.int32)
+        if nd.ndim != 2 or nd.shape[1] != 4 or pt.shape != (nd.shape[0], 9):
+            raise ValueError("node_dof must be [n_nodes, 4] and patch [n_nodes, 9]")
+        self._check(self._lib.fsi_learned_setup(self._h, nd.shape[0], _np_ptr(nd, ctypes.c_int32),
+                                                _np_ptr(pt, ctypes.c_int32)))
+        self.n_nodes = int(nd.shape[0])
+
+    def learned_load(self, path):
+        self._check(self._lib.fsi_learned_load(self._h, os.fsencode(path)))
+
+    def learned_set_weights(self, sigma_in, sigma_out, params_bf16):
+        si = np.ascontiguousarray(sigma_in, np.float32)
+        so = np.ascontiguousarray(sigma_out, np.float32)
+        pb = np.ascontiguousarray(params_bf16, np.uint16)
+        if si.shape != (5,) or so.shape != (5,) or pb.shape != (FSI_MLP_PARAMS,):
+            raise ValueError("sigma_in/sigma_out need 5 values and params FSI_MLP_PARAMS bfloat16 words")
+        self._check(self._lib.fsi_learned_set_weights(self._h, _np_ptr(si, ctypes.c_float),
+                                                      _np_ptr(so, ctypes.c_float), _np_ptr(pb, ctypes.c_uint16)))
+
+    def learned_apply(self, r, c, sync=True):
+        """c = MLP(r') (float64 device vectors of length n)."""
+        if r.numel() != self.n or c.numel() != self.n:
+            raise ValueError("r and c must have n entries")
+        self._order()
+        self._check(self._lib.fsi_learned_apply(self._h, _dev_ptr(r), _dev_ptr(c)))
+        if sync:
+            self._sync()
+
+    def learned_features(self, r, feat, rho, sync=True):
+        """Features [n_nodes, 53] and rho [n_nodes] (float32 device tensors) of r'."""
+        import torch
+        nn = getattr(self, "n_nodes", None)
+        if nn is None:
+            raise RuntimeError("learned_setup first")
+        if r.numel() != self.n or feat.numel() < nn * FSI_MLP_INPUTS or rho.numel() < nn:
+            raise ValueError("r needs n entries, feat n_nodes x 53 and rho n_nodes")
+        self._order()
+        self._check(self._lib.fsi_learned_features(self._h, _dev_ptr(r), _dev_ptr(feat, torch.float32),
+                                                   _dev_ptr(rho, torch.float32)))
+        if sync:
+            self._sync()
+
+    def set_harvest(self, buf=None, nvec=0):
+        """Store r'_j = v_j - A P^-1 v_j of the first nvec iterations of later solves into buf [nvec, n]."""
+        ptr = None if buf is None else _dev_ptr(buf)
+        if buf is not None and (buf.dim() != 2 or buf.shape[0] < nvec or buf.shape[1] != self.n):
+            raise ValueError("buf must be [>= nvec, n]")
+        self._keep_harvest = buf
+        self._check(self._lib.fsi_set_harvest(self._h, ptr, int(nvec if buf is not None else 0)))
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self._lib.fsi_free(self._h)
@@ -275,3 +381,87 @@ class FSISolver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def default_train_params(**overrides) -> TrainParams:
+    p = TrainParams()
+    load_library().fsi_default_train_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k in ("sigma_in", "sigma_out"):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = float(x)
+        elif hasattr(p, k):
+            setattr(p, k, v)
+        else:
+            raise KeyError(f"unknown fsi_train_params field {k!r}")
+    return p
+
+
+class Trainer:
+    """fsi_trainer: AdamW training of the learned stage on residuals of FSISolver contexts."""
+
+    def __init__(self, params: TrainParams | None = None, **overrides):
+        lib = load_library()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        p = params if params is not None else default_train_params(**overrides)
+        rc = lib.fsi_trainer_create(ctypes.byref(self._h), ctypes.byref(p))
+        if rc != FSI_OK:
+            raise FSIError(rc, lib.fsi_last_error(None).decode())
+
+    def _check_global(self, rc):
+        if rc != FSI_OK:
+            raise FSIError(rc, self._lib.fsi_last_error(None).decode())
+
+    def step(self, solver: FSISolver, rprime) -> float:
+        """Accumulate the gradient of ||r' - A c||^2 / ||r'||^2 for r' of `solver`; returns the loss."""
+        if rprime.numel() != solver.n:
+            raise ValueError("r' must have n entries")
+        loss = ctypes.c_double()
+        solver._order()
+        rc = self._lib.fsi_trainer_step(self._h, solver._h, _dev_ptr(rprime), ctypes.byref(loss))
+        solver._check(rc)
+        return loss.value
+
+    def loss(self, solver: FSISolver, rprime) -> float:
+        """Loss of r' with the current weights (no gradient)."""
+        if rprime.numel() != solver.n:
+            raise ValueError("r' must have n entries")
+        loss = ctypes.c_double()
+        solver._order()
+        solver._check(self._lib.fsi_trainer_loss(self._h, solver._h, _dev_ptr(rprime), ctypes.byref(loss)))
+        return loss.value
+
+    def update(self, solver: FSISolver, lr: float = 0.0):
+        """AdamW step with the mean accumulated gradient (lr <= 0: the creation-time rate)."""
+        solver._check(self._lib.fsi_trainer_update(self._h, solver._h, float(lr)))
+
+    def set_master(self, params):
+        w = np.ascontiguousarray(params, np.float32)
+        if w.shape != (FSI_MLP_PARAMS,):
+            raise ValueError("params must hold FSI_MLP_PARAMS floats")
+        self._check_global(self._lib.fsi_trainer_set_master(self._h, _np_ptr(w, ctypes.c_float)))
+
+    def get(self):
+        """(master float32, bfloat16 words, accumulated gradient float32)."""
+        m = np.empty(FSI_MLP_PARAMS, np.float32)
+        b = np.empty(FSI_MLP_PARAMS, np.uint16)
+        g = np.empty(FSI_MLP_PARAMS, np.float32)
+        self._check_global(self._lib.fsi_trainer_get(self._h, _np_ptr(m, ctypes.c_float),
+                                                     _np_ptr(b, ctypes.c_uint16), _np_ptr(g, ctypes.c_float)))
+        return m, b, g
+
+    def save(self, path):
+        self._check_global(self._lib.fsi_trainer_save(self._h, os.fsencode(path)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.fsi_trainer_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

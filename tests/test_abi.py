@@ -100,3 +100,49 @@ def test_null_context_calls(lib):
     assert lib.fsi_precond_build(None, 0, None) == -1
     assert lib.fsi_solve(None, None, None, 1e-8, None) == -1
     lib.fsi_free(None)
+
+
+def test_learned_defaults_and_validation(lib):
+    import paper_1801_05648_gb300 as P
+    assert P.default_params(2).learned_accept == pytest.approx(0.1)
+    tp = P.default_train_params()
+    assert (tp.lr, tp.beta1, tp.beta2, tp.eps, tp.weight_decay, tp.init_out_scale) == \
+        (1e-3, 0.9, 0.999, 1e-8, 0.0, 0.01)
+    assert list(tp.sigma_in) == [1.0] * 5 and list(tp.sigma_out) == [1.0] * 5
+    rp, ci, va, off = _tiny_csr()
+    for bad in (0.0, 1.5, float("nan")):
+        rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, learned_accept=bad))
+        assert rc == -1 and "learned_accept" in msg
+    # trainer parameters are checked before any device memory is touched
+    h = ctypes.c_void_p()
+    rc = lib.fsi_trainer_create(ctypes.byref(h), ctypes.byref(P.default_train_params(sigma_in=[1, 0, 1, 1, 1])))
+    assert rc == -1 and not h.value and "scales" in lib.fsi_last_error(None).decode()
+    rc = lib.fsi_trainer_create(ctypes.byref(h), ctypes.byref(P.default_train_params(beta1=1.0)))
+    assert rc == -1 and "AdamW" in lib.fsi_last_error(None).decode()
+
+
+def test_learned_null_calls(lib):
+    assert lib.fsi_learned_setup(None, 1, None, None) == -1
+    assert lib.fsi_learned_load(None, b"x") == -1
+    assert lib.fsi_learned_set_weights(None, None, None, None) == -1
+    assert lib.fsi_learned_apply(None, None, None) == -1
+    assert lib.fsi_learned_features(None, None, None, None) == -1
+    assert lib.fsi_set_harvest(None, None, 0) == -1
+    assert lib.fsi_set_flags(None, 0) == -1
+    assert lib.fsi_set_learned_accept(None, 0.5) == -1
+    assert lib.fsi_trainer_create(None, None) == -1
+    assert lib.fsi_trainer_step(None, None, None, None) == -1
+    assert lib.fsi_trainer_loss(None, None, None, None) == -1
+    assert lib.fsi_trainer_update(None, None, 0.0) == -1
+    assert lib.fsi_trainer_set_master(None, None) == -1
+    assert lib.fsi_trainer_get(None, None, None, None) == -1
+    assert lib.fsi_trainer_save(None, b"x") == -1
+    lib.fsi_trainer_free(None)
+
+
+def test_committed_weights_file_is_well_formed():
+    from oracle import learned as L
+    path = os.path.join(ROOT, "paper_1801_05648_gb300", "weights", "mlp_fsi2d_256x128.bin")
+    bits, si, so = L.read_weights(path)
+    assert bits.shape == (L.N_PARAMS,) and np.all(np.isfinite(L.bf16_value(bits)))
+    assert np.all(si > 0) and np.all(so > 0)
