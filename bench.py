@@ -27,6 +27,7 @@ import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1801_05648_gb300", "weights", "mlp_fsi2d_256x128.bin")
 sys.path.insert(0, ROOT)
 
 METRIC = "Newton-step solve seconds to 1e-8 rel. residual (FP32-AMG/learned vs FP64); GB/s"
@@ -48,6 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="2d_mid")
     ap.add_argument("--states", type=int, default=5)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-form timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--kernel-only", choices=["spmv", "solve"], default=None,
@@ -340,6 +342,48 @@ def bench_ours(args):
         rr = np.linalg.norm(systems[i].rhs - A @ xc) / np.linalg.norm(systems[i].rhs)
         assert rr <= 1.001e-8, f"end-to-end result fails the residual check ({rr})"
 
+    # ---- learned form: the headline form plus the learned correction stage (2D only;
+    # weights trained on the method's own Newton-step solves, default accept ratio)
+    learned = None
+    if systems[0].dim == 2 and not args.no_learned:
+        pb = fsigen.get_problem(systems[0].cfg)
+        nd, pt = pb.node_map()
+        for g in solvers:
+            g.learned_setup(nd, pt)
+            g.learned_load(LEARNED_WEIGHTS)
+            g.set_flags(flags | P.FSI_LEARNED)
+        ms_l, wall_l, st_l = timed(args.precision, max(3, min(args.steps, 10)), args.warmup)
+        for g in solvers:
+            g.set_flags(flags)
+        assert all(x.status == 0 for x in st_l), "a learned-form solve did not converge"
+        # the MLP kernel alone (one launch per resident Jacobian in turn)
+        reps = 30
+        cs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in systems]
+        for k in range(S):
+            solvers[k].learned_apply(rhs[k], cs[k], sync=False)
+        bs.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bs)
+        for k in range(reps):
+            solvers[k % S].learned_apply(rhs[k % S], cs[k % S], sync=False)
+        e1.record(bs)
+        bs.synchronize()
+        mlp_s = e0.elapsed_time(e1) / reps / 1e3
+        mlp_flops = nd.shape[0] * 2.0 * (53 * 64 + 64 * 64 + 64 * 5)
+        fp32_peak = 152 * 128 * 2 * (clocks.get("sm_max_mhz") or 2070) * 1e6 / 1e12
+        learned = {"form": "FP32-AMG + learned stage" if args.precision == "fp32" else "FP64 + learned stage",
+                   "solve_s": ms_l / 1e3, "iters_median": statistics.median([x.iters for x in st_l]),
+                   "accepted_total": sum(x.learned_accepted for x in st_l),
+                   "accept_ratio": float(P.default_params(2).learned_accept),
+                   "err_vs_exact_max": err_vs_exact(),
+                   "weights": os.path.relpath(LEARNED_WEIGHTS, ROOT),
+                   "roofline_mlp": {"kernel": "k_mlp<MODE_APPLY>: patch gather + 53-64-64-5 MLP (bfloat16 weights, "
+                                              "FP32 FMA) + scatter", "bound": "alu",
+                                    "achieved": mlp_flops / mlp_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                                    "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock",
+                                    "frac": mlp_flops / mlp_s / 1e12 / fp32_peak, "launch_us": mlp_s * 1e6,
+                                    "flops_per_launch": mlp_flops}}
+
     # ---- roofline of the dominant kernel: the fused FP32 2x2 Chebyshev SpMV step of the
     # V-cycles, on level 0 of the mesh and fluid-velocity hierarchies of every resident
     # Jacobian in turn (10 matrices, ~0.3 GB together: each launch finds the L2 holding
@@ -422,6 +466,7 @@ def bench_ours(args):
         "err_vs_exact_max": err_main,
         "other_form": {"form": other.upper() if other == "fp64" else "FP32-AMG", "solve_s": ms_o / 1e3,
                        "iters_median": statistics.median([x.iters for x in st_o]), "err_vs_exact_max": err_other},
+        "learned_form": learned,
         "setup_s": statistics.mean(x.setup_s for x in st[:S]) if st else None,
         "precond_build_s_fp64": statistics.mean(build_s),
         "solve_algorithmic_gbs": bytes_per_solve / (ms / 1e3) / 1e9,

@@ -65,15 +65,30 @@ enum { MODE_APPLY = 0, MODE_FEATURES = 1, MODE_TRAIN = 2 };
 // One thread per node: gather the patch, normalise, run the MLP (MODE_APPLY,
 // MODE_TRAIN) and scatter the correction; MODE_TRAIN also stores the features
 // and pre-activations column-major (row k of node a at [k * ld + a]).
+//
+// Dynamic shared memory: the weights as FP32 (kParamsPadded floats), then one
+// column of 64 floats per thread (act[k * kNodeThreads + t]) holding first the
+// features, then the hidden activations.  The layers loop over their inputs
+// (read from the thread's column) with the 64 accumulators in registers, so
+// the kernel body stays small enough for the instruction cache.
+constexpr size_t kMlpSmem = sizeof(float) * ((size_t)kParamsPadded + (size_t)kMlpHidden * kNodeThreads);
+
 template <int MODE>
 __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t* __restrict__ w16,
                                                       const double* __restrict__ rp, double* __restrict__ c,
                                                       float* __restrict__ F, float* __restrict__ rho_out,
                                                       float* __restrict__ H1, float* __restrict__ H2, int64_t ld) {
-  __shared__ __align__(16) float W[kParamsPadded];
+  extern __shared__ __align__(16) float smem[];
+  float* W = smem;
+  float* act = smem + kParamsPadded;
+  const int t = threadIdx.x;
   if (MODE != MODE_FEATURES) load_weights(W, w16);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < g.n_nodes; a += stride) {
+  // the block loops in lockstep so that the weights stay loaded; idle threads skip the work
+  const int64_t nb = (g.n_nodes + blockDim.x - 1) / blockDim.x * blockDim.x;
+  for (int64_t a0 = blockIdx.x * (int64_t)blockDim.x; a0 < nb; a0 += stride) {
+    const int64_t a = a0 + t;
+    if (a >= g.n_nodes) continue;
     const int4 me = g.node_dof[a];
     const int fl = me.w;
     float x[kMlpPatch];
@@ -98,15 +113,13 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t*
     const float rho = sqrtf(ss * (1.0f / kMlpPatch));
     const bool live = rho > 0.f;
     const float inv_rho = live ? 1.0f / rho : 0.f;
-#pragma unroll
-    for (int k = 0; k < kMlpPatch; ++k) x[k] *= inv_rho;
     const int par = ((fl >> 4) & 1) | (((fl >> 5) & 1) << 1);
     const float fbit[4] = {(fl & NF_SOLID) ? 1.f : 0.f, (fl & NF_VFIX) ? 1.f : 0.f, (fl & NF_UFIX) ? 1.f : 0.f,
                            (fl & NF_IFACE) ? 1.f : 0.f};
     if (MODE == MODE_FEATURES) {
       float* row = F + a * kMlpIn;
 #pragma unroll
-      for (int k = 0; k < kMlpPatch; ++k) row[k] = x[k];
+      for (int k = 0; k < kMlpPatch; ++k) row[k] = x[k] * inv_rho;
 #pragma unroll
       for (int k = 0; k < 4; ++k) row[kMlpPatch + k] = (k == par) ? 1.f : 0.f;
 #pragma unroll
@@ -114,22 +127,40 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t*
       rho_out[a] = rho;
       continue;
     }
-    if (MODE == MODE_TRAIN) {
 #pragma unroll
-      for (int k = 0; k < kMlpPatch; ++k) F[k * ld + a] = x[k];
+    for (int k = 0; k < kMlpPatch; ++k) {
+      const float f = x[k] * inv_rho;
+      act[k * kNodeThreads + t] = f;
+      if (MODE == MODE_TRAIN) F[k * ld + a] = f;
+    }
+    if (MODE == MODE_TRAIN) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) F[(kMlpPatch + k) * ld + a] = (k == par) ? 1.f : 0.f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) F[(kMlpPatch + 4 + k) * ld + a] = fbit[k];
       rho_out[a] = rho;
     }
-    // layer 1: h = W1^T f + b1
+    // layer 1: h = W1^T f + b1 (the one-hot and flag inputs add their weight rows)
     float h[kMlpHidden];
+    {
+      const float* wp = W + kW1 + (kMlpPatch + par) * kMlpHidden;
 #pragma unroll
-    for (int j = 0; j < kMlpHidden; ++j) h[j] = W[kB1 + j];
+      for (int j = 0; j < kMlpHidden; ++j) h[j] = W[kB1 + j] + wp[j];
+    }
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      if ((fl >> k) & 1) {   // flag inputs: NF_SOLID, NF_VFIX, NF_UFIX, NF_IFACE are bits 0..3
+        const float4* w4 = reinterpret_cast<const float4*>(W + kW1 + (kMlpPatch + 4 + k) * kMlpHidden);
 #pragma unroll
+        for (int q = 0; q < kMlpHidden / 4; ++q) {
+          const float4 w = w4[q];
+          h[4 * q + 0] += w.x; h[4 * q + 1] += w.y; h[4 * q + 2] += w.z; h[4 * q + 3] += w.w;
+        }
+      }
+    }
+#pragma unroll 1
     for (int i = 0; i < kMlpPatch; ++i) {
-      const float xi = x[i];
+      const float xi = act[i * kNodeThreads + t];
       const float4* w4 = reinterpret_cast<const float4*>(W + kW1 + i * kMlpHidden);
 #pragma unroll
       for (int q = 0; q < kMlpHidden / 4; ++q) {
@@ -137,50 +168,41 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t*
         h[4 * q + 0] += xi * w.x; h[4 * q + 1] += xi * w.y; h[4 * q + 2] += xi * w.z; h[4 * q + 3] += xi * w.w;
       }
     }
-    {
-      const float* wp = W + kW1 + (kMlpPatch + par) * kMlpHidden;
 #pragma unroll
-      for (int j = 0; j < kMlpHidden; ++j) h[j] += wp[j];
+    for (int j = 0; j < kMlpHidden; ++j) {
+      act[j * kNodeThreads + t] = h[j];
+      if (MODE == MODE_TRAIN) H1[j * ld + a] = h[j];
+    }
+#pragma unroll 1
+    for (int j = 0; j < kMlpHidden; ++j) act[j * kNodeThreads + t] = gelu(act[j * kNodeThreads + t]);
+    // layer 2: h = W2^T gelu(h1) + b2
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (fbit[k] != 0.f) {
-          const float* wf = W + kW1 + (kMlpPatch + 4 + k) * kMlpHidden;
+    for (int j = 0; j < kMlpHidden; ++j) h[j] = W[kB2 + j];
+#pragma unroll 1
+    for (int i = 0; i < kMlpHidden; ++i) {
+      const float hv = act[i * kNodeThreads + t];
+      const float4* w4 = reinterpret_cast<const float4*>(W + kW2 + i * kMlpHidden);
 #pragma unroll
-          for (int j = 0; j < kMlpHidden; ++j) h[j] += wf[j];
-        }
+      for (int q = 0; q < kMlpHidden / 4; ++q) {
+        const float4 w = w4[q];
+        h[4 * q + 0] += hv * w.x; h[4 * q + 1] += hv * w.y; h[4 * q + 2] += hv * w.z; h[4 * q + 3] += hv * w.w;
       }
     }
 #pragma unroll
     for (int j = 0; j < kMlpHidden; ++j) {
-      if (MODE == MODE_TRAIN) H1[j * ld + a] = h[j];
-      h[j] = gelu(h[j]);
+      act[j * kNodeThreads + t] = h[j];
+      if (MODE == MODE_TRAIN) H2[j * ld + a] = h[j];
     }
-    // layers 2 and 3, 16 hidden units at a time
+    // layer 3: y = W3^T gelu(h2) + b3
     float y[kMlpOut];
 #pragma unroll
     for (int o = 0; o < kMlpOut; ++o) y[o] = W[kB3 + o];
+#pragma unroll 1
+    for (int j = 0; j < kMlpHidden; ++j) {
+      const float a2 = gelu(act[j * kNodeThreads + t]);
+      const float* w3 = W + kW3 + j * kMlpOut;
 #pragma unroll
-    for (int j0 = 0; j0 < kMlpHidden; j0 += 16) {
-      float acc[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) acc[k] = W[kB2 + j0 + k];
-#pragma unroll
-      for (int i = 0; i < kMlpHidden; ++i) {
-        const float hv = h[i];
-        const float4* w4 = reinterpret_cast<const float4*>(W + kW2 + i * kMlpHidden + j0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 w = w4[q];
-          acc[4 * q + 0] += hv * w.x; acc[4 * q + 1] += hv * w.y; acc[4 * q + 2] += hv * w.z; acc[4 * q + 3] += hv * w.w;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        if (MODE == MODE_TRAIN) H2[(j0 + k) * ld + a] = acc[k];
-        const float a2 = gelu(acc[k]);
-#pragma unroll
-        for (int o = 0; o < kMlpOut; ++o) y[o] += a2 * W[kW3 + (j0 + k) * kMlpOut + o];
-      }
+      for (int o = 0; o < kMlpOut; ++o) y[o] += a2 * w3[o];
     }
     // scatter c = y rho sigma_out on the node's free DOFs
     const double rr = (double)rho;
@@ -195,6 +217,20 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t*
       c[me.z] = sp != 0.0 ? (double)y[4] * sp : 0.0;
     }
   }
+}
+
+template <int MODE>
+void launch_mlp(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, float* F, float* rho,
+                float* H1, float* H2, int64_t ld, cudaStream_t s) {
+  static bool attr = false;   // the opt-in above 48 KB, set once per instantiation
+  if (!attr) {
+    FSI_CUDA(cudaFuncSetAttribute(k_mlp<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem));
+    attr = true;
+  }
+  int64_t b = (g.n_nodes + kNodeThreads - 1) / kNodeThreads;
+  if (b > 152 * 3) b = 152 * 3;   // three 64 KB blocks fit one SM: one wave, weights loaded once per block
+  k_mlp<MODE><<<(int)(b < 1 ? 1 : b), kNodeThreads, kMlpSmem, s>>>(g, w16, rp, c, F, rho, H1, H2, ld);
+  FSI_CHECK_LAUNCH();
 }
 
 // Backward through the MLP for one node: dY from dL/dc, then dH2 and dH1.
@@ -236,7 +272,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp_bwd(MlpGeom g, const uint1
       d2[j] = s * gelu_grad(H2[j * ld + a]);
       dH2[j * ld + a] = d2[j];
     }
-#pragma unroll 4
+#pragma unroll 1
     for (int i = 0; i < kMlpHidden; ++i) {
       const float4* w4 = reinterpret_cast<const float4*>(W + kW2 + i * kMlpHidden);
       float s = 0.f;
@@ -583,15 +619,11 @@ MlpGeom learned_geom(const Learned& L, const int64_t off[6]) {
 
 
 void mlp_apply(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, cudaStream_t s) {
-  k_mlp<MODE_APPLY><<<grid_nodes(g.n_nodes), kNodeThreads, 0, s>>>(g, w16, rp, c, nullptr, nullptr, nullptr, nullptr,
-                                                                   0);
-  FSI_CHECK_LAUNCH();
+  launch_mlp<MODE_APPLY>(g, w16, rp, c, nullptr, nullptr, nullptr, nullptr, 0, s);
 }
 
 void mlp_features(const MlpGeom& g, const double* rp, float* F, float* rho, cudaStream_t s) {
-  k_mlp<MODE_FEATURES><<<grid_nodes(g.n_nodes), kNodeThreads, 0, s>>>(g, nullptr, rp, nullptr, F, rho, nullptr,
-                                                                      nullptr, 0);
-  FSI_CHECK_LAUNCH();
+  launch_mlp<MODE_FEATURES>(g, nullptr, rp, nullptr, F, rho, nullptr, nullptr, 0, s);
 }
 
 void learned_residual(int64_t n, const double* V, int64_t ldv, const int* jdev, const double* w, double* rp,
@@ -716,9 +748,7 @@ double trainer_step(Trainer& T, Context& C, const double* rp, bool grad) {
     g.sig_out[k] = T.prm.sig_out[k];
   }
   const int64_t ld = T.cap_nodes;
-  k_mlp<MODE_TRAIN><<<grid_nodes(nn), kNodeThreads, 0, s>>>(g, T.w16.p, rp, T.c.p, T.F.p, T.rho.p, T.H1.p, T.H2.p,
-                                                            ld);
-  FSI_CHECK_LAUNCH();
+  launch_mlp<MODE_TRAIN>(g, T.w16.p, rp, T.c.p, T.F.p, T.rho.p, T.H1.p, T.H2.p, ld, s);
   apply_operator(C, T.c.p, T.t.p);
   k_square_partial<<<kRedBlocks, kRT, 0, s>>>(n, rp, T.part.p);
   FSI_CHECK_LAUNCH();

@@ -25,7 +25,8 @@ constexpr int kW1 = 0, kB1 = kW1 + kMlpIn * kMlpHidden, kW2 = kB1 + kMlpHidden,
               kB2 = kW2 + kMlpHidden * kMlpHidden, kW3 = kB2 + kMlpHidden,
               kB3 = kW3 + kMlpHidden * kMlpOut, kMlpParams = kB3 + kMlpOut;
 
-// Node flags (fourth entry of a node's int4 record).
+// Node flags (fourth entry of a node's int4 record); the four flag inputs of the
+// MLP are bits 0..3 in this order.
 enum NodeFlags { NF_SOLID = 1, NF_VFIX = 2, NF_UFIX = 4, NF_IFACE = 8, NF_IODD = 16, NF_JODD = 32, NF_PFIX = 64 };
 
 // Everything the per-node kernels read besides the vectors (passed by value).
