@@ -52,7 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--kernel-only", choices=["spmv", "solve"], default=None,
+    ap.add_argument("--kernel-only", choices=["spmv", "solve", "mlp"], default=None,
                     help="small programs for ncu captures: 'spmv' runs the outer SpMV 6 times; 'solve' runs "
                          "one solve of the bench workload inside cudaProfilerStart/Stop")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -371,6 +371,8 @@ def bench_ours(args):
         mlp_s = e0.elapsed_time(e1) / reps / 1e3
         mlp_flops = nd.shape[0] * 2.0 * (53 * 64 + 64 * 64 + 64 * 5)
         fp32_peak = 152 * 128 * 2 * (clocks.get("sm_max_mhz") or 2070) * 1e6 / 1e12
+        mlp_traffic = kernel_traffic("mlp_apply_2d_mid.md", ["paper_1801_05648_gb300/csrc/learned.cu",
+                                                             "paper_1801_05648_gb300/csrc/learned.cuh"])
         learned = {"form": "FP32-AMG + learned stage" if args.precision == "fp32" else "FP64 + learned stage",
                    "solve_s": ms_l / 1e3, "iters_median": statistics.median([x.iters for x in st_l]),
                    "accepted_total": sum(x.learned_accepted for x in st_l),
@@ -382,7 +384,7 @@ def bench_ours(args):
                                     "achieved": mlp_flops / mlp_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                                     "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock",
                                     "frac": mlp_flops / mlp_s / 1e12 / fp32_peak, "launch_us": mlp_s * 1e6,
-                                    "flops_per_launch": mlp_flops}}
+                                    "flops_per_launch": mlp_flops, "traffic": mlp_traffic}}
 
     # ---- roofline of the dominant kernel: the fused FP32 2x2 Chebyshev SpMV step of the
     # V-cycles, on level 0 of the mesh and fluid-velocity hierarchies of every resident
@@ -546,6 +548,23 @@ def kernel_only(args):
         torch.cuda.cudart().cudaProfilerStop()
         print(json.dumps({"kernel_only": "solve", "workload": args.workload, "form": args.precision,
                           "iters": st.iters, "kernel_launches": st.kernel_launches, "solve_s": st.solve_s}))
+        g.close()
+        return
+    if args.kernel_only == "mlp":
+        # the learned stage's MLP on one resident Jacobian: 6 applications to the rhs
+        pb = fsigen.get_problem(s.cfg)
+        nd, pt = pb.node_map()
+        g = P.FSISolver.from_system(s)
+        g.learned_setup(nd, pt)
+        g.learned_load(LEARNED_WEIGHTS)
+        b = torch.tensor(s.rhs, device="cuda")
+        c = torch.empty_like(b)
+        for _ in range(6):
+            g.learned_apply(b, c, sync=False)
+        g.stream.synchronize()
+        assert bool(torch.isfinite(c).all())
+        print(json.dumps({"kernel_only": "mlp", "workload": args.workload, "nodes": int(nd.shape[0]),
+                          "c_norm": float(torch.linalg.vector_norm(c))}))
         g.close()
         return
     g = P.FSISolver.from_system(s)
