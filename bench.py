@@ -50,6 +50,7 @@ def parse_args(argv=None):
     ap.add_argument("--states", type=int, default=5)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form timing")
+    ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--kernel-only", choices=["spmv", "solve", "mlp"], default=None,
@@ -243,7 +244,7 @@ def bench_ours(args):
     libbuild.build()
     dev = torch.device("cuda", local)
     bs = torch.cuda.Stream(device=dev)       # every solver runs on this stream
-    flags = 0 if args.no_graphs else P.FSI_USE_GRAPHS
+    flags = (0 if args.no_graphs else P.FSI_USE_GRAPHS) | (P.FSI_NO_PDL if args.no_pdl else 0)
 
     systems, solvers = [], []
     setup_s, build_s = [], []
@@ -460,7 +461,8 @@ def bench_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOAD_DESC.get(args.workload, args.workload),
                    "form": "FP32-AMG" if args.precision == "fp32" else "FP64", "rtol": 1e-8, "restart": 100,
-                   "states": S, "graphs": not args.no_graphs, "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "states": S, "graphs": not args.no_graphs, "pdl": not args.no_pdl,
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2: each step solves another resident Jacobian (~0.6 GB of "
                          "matrices each)"},
         "iters": {"median": statistics.median(iters), "min": min(iters), "max": max(iters)},

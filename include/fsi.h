@@ -57,14 +57,18 @@ enum {
   FSI_CLUSTER_COARSE = 8,  /* run the coarse AMG levels (matrices <= 6 MB) of each V-cycle in one
                               16-CTA thread-block-cluster launch instead of one launch per step
                               (fewer launches, but slower on the 256x128 case: 26.7 vs 15.7 ms) */
-  FSI_LEARNED = 16         /* apply the learned correction stage after P^-1 in every FGMRES
+  FSI_LEARNED = 16,        /* apply the learned correction stage after P^-1 in every FGMRES
                               iteration (needs fsi_learned_setup and weights; see below) */
+  FSI_NO_PDL = 32          /* launch the solve's kernels without programmatic dependent launch
+                              (each kernel then waits for the previous one to finish before it
+                              is scheduled).  Process-wide: the last fsi_setup's choice applies */
 };
 
 typedef struct fsi_params {
   int restart;              /* FGMRES restart length m (default 100) */
   int maxit;                /* maximum FGMRES iterations (default 1000) */
-  int flags;                /* FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE */
+  int flags;                /* FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE |
+                               FSI_LEARNED | FSI_NO_PDL */
   double dt_theta;          /* c = dt*theta of the solid Schur complement S_hat = A_vv + c A_vu (0.01) */
   /* smoothed-aggregation AMG */
   double strength_theta;    /* strength threshold on node-block Frobenius norms (0.08) */
@@ -90,6 +94,17 @@ typedef struct fsi_params {
   /* learned stage: take the correction only when ||r' - A c|| < learned_accept * ||r'||
      (0.1; at 0.3 and above the trained stage's accepted corrections stall FGMRES) */
   double learned_accept;
+  /* SpMV L2 prefetch: 0 none, 1 each CTA bulk-prefetches its slice of the matrix arrays
+     into L2 before waiting for the previous kernel, 2 the same with at most 5 persistent
+     CTAs per SM walking longer slices (1; measured on the 256x128 case: FP64 solve
+     52.2 -> 49.2 ms, FP32 unchanged, 2 slower).  Process-wide, like the other SpMV knobs. */
+  int spmv_prefetch;
+  /* FSI_CLUSTER_COARSE: levels whose matrix values take at most this many bytes run in
+     the cluster launch (6e6).  Process-wide. */
+  double cluster_max_bytes;
+  /* Chebyshev degree on the coarser AMG levels (>= 1); 0 = cheb_degree on every level (2:
+     256x128 solve 14.3 -> 13.0 ms at 11-12 iterations; 1024x512 +3%, 35 vs 33 iterations) */
+  int cheb_degree_coarse;
 } fsi_params;
 
 typedef struct fsi_stats {
@@ -292,7 +307,8 @@ int fsi_learned_features(fsi_ctx* ctx, const double* r_dev, float* feat_dev, flo
 /* Change fsi_params.learned_accept (in (0, 1]) of a context. */
 int fsi_set_learned_accept(fsi_ctx* ctx, double tau);
 /* Change the run-time flags of a context (FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_LEARNED);
- * FSI_NO_RIGID_MODES and FSI_CLUSTER_COARSE are fixed at fsi_setup (FSI_EINVAL if they differ). */
+ * FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE and FSI_NO_PDL are fixed at fsi_setup (FSI_EINVAL if
+ * they differ). */
 int fsi_set_flags(fsi_ctx* ctx, int flags);
 /*
  * fsi_set_harvest - during later fsi_solve calls, store the preconditioned

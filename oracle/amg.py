@@ -51,6 +51,10 @@ class AMGParams:
     drop_tol: float = 1e-10
     presmooth: int = 1
     postsmooth: int = 1
+    cheb_degree_coarse: int = 2  # Chebyshev degree on levels >= 1 (0: cheb_degree everywhere)
+
+    def degree(self, level: int) -> int:
+        return self.cheb_degree_coarse if level > 0 and self.cheb_degree_coarse > 0 else self.cheb_degree
 
 
 # ------------------------------------------------------------------ set-up
@@ -287,12 +291,12 @@ def vcycle(H: Hierarchy, b: np.ndarray, lvl: int = 0) -> np.ndarray:
         return H.coarse_inv @ b
     x = None
     for s in range(p.presmooth):
-        x = chebyshev(L.A, L.dinv, b, x, L.lam, p.cheb_degree, p.cheb_ratio, p.cheb_upper, x_is_zero=(s == 0))
+        x = chebyshev(L.A, L.dinv, b, x, L.lam, p.degree(lvl), p.cheb_ratio, p.cheb_upper, x_is_zero=(s == 0))
     r = b - L.A @ x
     xc = vcycle(H, L.R @ r, lvl + 1)
     x = x + L.P @ xc
     for _ in range(p.postsmooth):
-        x = chebyshev(L.A, L.dinv, b, x, L.lam, p.cheb_degree, p.cheb_ratio, p.cheb_upper)
+        x = chebyshev(L.A, L.dinv, b, x, L.lam, p.degree(lvl), p.cheb_ratio, p.cheb_upper)
     return x
 
 

@@ -244,6 +244,7 @@ __global__ void k_power_init(int64_t n, int stream_id, double* __restrict__ x) {
 template <class T>
 __global__ void k_cheb_first(int64_t n, const T* __restrict__ b, const T* __restrict__ dinv, T inv_theta,
                              T* __restrict__ d, T* __restrict__ x) {
+  dep_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const T v = dinv[i] * b[i] * inv_theta;
@@ -254,6 +255,7 @@ __global__ void k_cheb_first(int64_t n, const T* __restrict__ b, const T* __rest
 // x = M b, M dense row-major n x n; one warp per row
 template <class T>
 __global__ void k_dense_gemv(int n, const T* __restrict__ M, const T* __restrict__ b, T* __restrict__ x) {
+  dep_wait();
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -315,8 +317,7 @@ void cheb_sweep(const Bsr& A, const T* dinv, double lam, int deg, double ratio, 
     oth = (first == x) ? xb : x;
     step0 = 1;
   } else if (zero_start) {
-    k_cheb_first<T><<<div_up(n, 256), 256, 0, s>>>(n, b, dinv, (T)(1.0 / theta), d, x);
-    FSI_CHECK_LAUNCH();
+    launch_k(k_cheb_first<T>, div_up(n, 256), 256, 0, s, n, b, dinv, (T)(1.0 / theta), d, x);
     cur = x;
     oth = xb;
   } else {
@@ -344,8 +345,7 @@ void vcycle_level(Hierarchy& H, int l, const T* b, T* x, cudaStream_t s) {
   if (l == last) {
     const int n = H.ncoarse;
     if (n == 0) return;
-    k_dense_gemv<T><<<div_up((int64_t)n * 32, 256), 256, 0, s>>>(n, cinv_of<T>(H), b, x);
-    FSI_CHECK_LAUNCH();
+    launch_k(k_dense_gemv<T>, div_up((int64_t)n * 32, 256), 256, 0, s, n, cinv_of<T>(H), b, x);
     return;
   }
   {
@@ -361,7 +361,7 @@ void vcycle_level(Hierarchy& H, int l, const T* b, T* x, cudaStream_t s) {
   LevelWork<T>& W = work<T>(L);
   const AmgParams& p = H.prm;
   for (int sw = 0; sw < p.presmooth; ++sw)
-    cheb_sweep<T>(L.A, dinv_of<T>(L), L.lam, p.cheb_degree, p.cheb_ratio, p.cheb_upper, b, x, W.xb.p, W.d.p, sw == 0, s);
+    cheb_sweep<T>(L.A, dinv_of<T>(L), L.lam, p.degree(l), p.cheb_ratio, p.cheb_upper, b, x, W.xb.p, W.d.p, sw == 0, s);
   spmv2_resid<T>(L.A, x, nullptr, nullptr, b, W.r.p, s);
   AmgLevel& C = H.levels[l + 1];
   LevelWork<T>& WC = work<T>(C);
@@ -369,7 +369,7 @@ void vcycle_level(Hierarchy& H, int l, const T* b, T* x, cudaStream_t s) {
   vcycle_level<T>(H, l + 1, WC.b.p, WC.x.p, s);
   spmv_axpby<T>(L.P, WC.x.p, T(1), T(1), x, s);
   for (int sw = 0; sw < p.postsmooth; ++sw)
-    cheb_sweep<T>(L.A, dinv_of<T>(L), L.lam, p.cheb_degree, p.cheb_ratio, p.cheb_upper, b, x, W.xb.p, W.d.p, false, s);
+    cheb_sweep<T>(L.A, dinv_of<T>(L), L.lam, p.degree(l), p.cheb_ratio, p.cheb_upper, b, x, W.xb.p, W.d.p, false, s);
 }
 
 int sync_read_int(const int* dev, cudaStream_t s) {
@@ -411,7 +411,7 @@ double Hierarchy::vcycle_bytes(int vb) const {
   const int nl = (int)levels.size();
   for (int l = 0; l + 1 < nl; ++l) {
     const AmgLevel& L = levels[l];
-    const int sweeps = prm.presmooth * prm.cheb_degree - 1 + prm.postsmooth * prm.cheb_degree + 1;  // smoother + residual
+    const int sweeps = prm.presmooth * prm.degree(l) - 1 + prm.postsmooth * prm.degree(l) + 1;  // smoother + residual
     tot += sweeps * L.A.spmv_bytes(vb) + L.R.spmv_bytes(vb) + L.P.spmv_bytes(vb);
   }
   tot += (double)ncoarse * ncoarse * vb;
@@ -562,7 +562,7 @@ int coarse_first_level(const Hierarchy& H, int value_bytes) {
   while (first - 1 >= 0) {
     const Bsr& A = H.levels[first - 1].A;
     const double bytes = (double)A.nnzb * A.br * A.bc * value_bytes;
-    if (bytes > kCoarseMaxBytes) break;
+    if (bytes > coarse_max_bytes()) break;
     --first;
   }
   if (first >= L - 1) return -1;                  // only the coarsest: nothing to merge

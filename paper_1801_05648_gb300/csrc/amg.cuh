@@ -36,6 +36,8 @@ struct AmgParams {
   double drop_tol = 1e-10;
   int presmooth = 1;
   int postsmooth = 1;
+  int cheb_degree_coarse = 2;   // Chebyshev degree on levels >= 1 (0: cheb_degree)
+  int degree(int level) const { return level > 0 && cheb_degree_coarse > 0 ? cheb_degree_coarse : cheb_degree; }
 };
 
 template <class T>
@@ -61,7 +63,11 @@ struct AmgLevel {
 constexpr int kCoarseThreads = 512;       // threads per CTA of the cluster kernel
 constexpr int kCoarseMaxLevels = 8;
 constexpr int kCoarseMaxDeg = 16;
-constexpr double kCoarseMaxBytes = 6.0e6; // levels at most this large (matrix bytes) run in the cluster
+// levels whose matrix has at most this many value bytes run in the cluster (fsi_params.cluster_max_bytes)
+inline double& coarse_max_bytes() {
+  static double b = 6.0e6;
+  return b;
+}
 
 struct CoarseMat {
   int nbr = 0, br = 1, bc = 1, tpr = 1;

@@ -293,7 +293,7 @@ void coarse_plan_build(Hierarchy& H, int first, CoarseRun<T>& run, cudaStream_t 
   const int threads = run.cluster * kCoarseThreads;
   CoarsePlan p = {};
   p.nlev = L - first;
-  p.deg = H.prm.cheb_degree;
+  p.deg = H.prm.degree(first);
   p.presmooth = H.prm.presmooth;
   p.postsmooth = H.prm.postsmooth;
   require(p.deg - 1 <= kCoarseMaxDeg, "coarse plan: Chebyshev degree too high");

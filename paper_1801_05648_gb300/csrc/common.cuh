@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 #include <stdexcept>
+#include <utility>
 
 namespace fsi {
 
@@ -37,6 +38,27 @@ inline int64_t g_kernel_launches = 0;
     ++::fsi::g_kernel_launches;   \
     FSI_CUDA(cudaGetLastError()); \
   } while (0)
+
+// Programmatic dependent launch (sm_90 and later).  A kernel started with
+// launch_k() may be scheduled while the previous kernel of its stream drains
+// (its blocks become resident during that kernel's tail); it executes
+// dep_wait() before its first global-memory access, which returns once the
+// previous kernel has completed and its writes are visible.  Every kernel
+// launched through launch_k() therefore starts with dep_wait().  Off for the
+// whole process when a context was set up with FSI_NO_PDL.
+__device__ __forceinline__ void dep_wait() {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+inline bool& pdl_enabled() {
+  static bool on = true;
+  return on;
+}
+
+template <class... KArgs, class... Args>
+void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args);
 
 inline void require(bool ok, const std::string& msg) {
   if (!ok) throw Error(EINVAL_, msg);
@@ -109,7 +131,9 @@ inline int lanes_for(int64_t nnzb, int nbr, double min_per_lane, double target_t
 // SpMV launch shape knobs (fsi_params: spmv_wave_fraction, spmv_unroll).
 struct SpmvTuning {
   double target_threads = kWaveThreads;
-  int unroll = 4;   // blocks each lane loads before multiplying: 4 or 8 (8 only for small blocks)
+  int unroll = 4;      // blocks each lane loads before multiplying: 4 or 8 (8 only for small blocks)
+  int prefetch = 1;    // 0 none, 1 L2 bulk prefetch of each CTA's matrix slice, 2 also persistent CTAs
+  int ctas_per_sm = 5; // persistent grid size per SM (prefetch 2)
 };
 inline SpmvTuning& spmv_tuning() {
   static SpmvTuning t;
@@ -122,6 +146,22 @@ inline void set_tpr(Bsr& A) {
 }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+template <class... KArgs, class... Args>
+void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  FSI_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+  ++g_kernel_launches;
+}
 
 // Streams and scratch shared by one context.
 struct Exec {

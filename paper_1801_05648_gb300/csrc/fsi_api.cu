@@ -50,6 +50,7 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.amg.coarse_max = p.coarse_max;
   s.amg.max_levels = p.max_levels;
   s.amg.cheb_degree = p.cheb_degree;
+  s.amg.cheb_degree_coarse = p.cheb_degree_coarse;
   s.amg.cheb_ratio = p.cheb_ratio;
   s.amg.cheb_upper = p.cheb_upper;
   s.amg.power_iters = p.power_iters;
@@ -65,6 +66,8 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.spmv_wave_fraction = p.spmv_wave_fraction;
   s.spmv_unroll = p.spmv_unroll;
   s.learned_accept = p.learned_accept;
+  s.spmv_prefetch = p.spmv_prefetch;
+  s.cluster_max_bytes = p.cluster_max_bytes;
 }
 
 void validate_params(const fsi::SolverParams& s) {
@@ -72,6 +75,7 @@ void validate_params(const fsi::SolverParams& s) {
   require(s.restart >= 1 && s.restart <= 1000, "restart must be in [1, 1000]");
   require(s.maxit >= 1, "maxit must be >= 1");
   require(s.amg.cheb_degree >= 1 && s.amg.presmooth >= 1 && s.amg.postsmooth >= 0, "smoother settings");
+  require(s.amg.cheb_degree_coarse >= 0 && s.amg.cheb_degree_coarse <= 16, "cheb_degree_coarse must be in [0, 16]");
   require(s.amg.cheb_ratio > 1.0 && s.amg.cheb_upper >= 1.0, "Chebyshev interval settings");
   require(s.amg.coarse_max >= 1 && s.amg.max_levels >= 1 && s.amg.power_iters >= 1, "AMG level settings");
   require(s.vc_mesh >= 1 && s.vc_solid >= 1 && s.vc_fluid >= 1 && s.vc_pressure >= 1, "V-cycle counts");
@@ -80,6 +84,8 @@ void validate_params(const fsi::SolverParams& s) {
   require(s.spmv_wave_fraction > 0.0 && s.spmv_wave_fraction <= 64.0, "spmv_wave_fraction must be in (0, 64]");
   require(s.spmv_unroll == 4 || s.spmv_unroll == 8, "spmv_unroll must be 4 or 8");
   require(s.learned_accept > 0.0 && s.learned_accept <= 1.0, "learned_accept must be in (0, 1]");
+  require(s.spmv_prefetch >= 0 && s.spmv_prefetch <= 2, "spmv_prefetch must be 0, 1 or 2");
+  require(s.cluster_max_bytes >= 0.0 && std::isfinite(s.cluster_max_bytes), "cluster_max_bytes must be >= 0");
 }
 
 void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -142,6 +148,9 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->spmv_wave_fraction = 1.0;
   p->spmv_unroll = 4;
   p->learned_accept = 0.1;
+  p->spmv_prefetch = 1;
+  p->cluster_max_bytes = 6.0e6;
+  p->cheb_degree_coarse = 2;
 }
 
 int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -171,6 +180,9 @@ int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const in
     }
     fsi::spmv_tuning().target_threads = fsi::kWaveThreads * ctx->C.prm.spmv_wave_fraction;
     fsi::spmv_tuning().unroll = ctx->C.prm.spmv_unroll;
+    fsi::spmv_tuning().prefetch = ctx->C.prm.spmv_prefetch;
+    fsi::coarse_max_bytes() = ctx->C.prm.cluster_max_bytes;
+    fsi::pdl_enabled() = (ctx->C.prm.flags & FSI_NO_PDL) == 0;
     fsi::context_setup(ctx->C, rowptr, colind, vals, node_coords);
   });
   if (rc != FSI_OK) {
@@ -384,11 +396,12 @@ int fsi_set_learned_accept(fsi_ctx* ctx, double tau) {
 int fsi_set_flags(fsi_ctx* ctx, int flags) {
   if (!ctx) return FSI_EINVAL;
   return guarded(ctx, [&] {
-    constexpr int fixed = FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE;
-    constexpr int known = FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED;
+    constexpr int fixed = FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_NO_PDL;
+    constexpr int known = FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED |
+                          FSI_NO_PDL;
     fsi::require((flags & ~known) == 0, "unknown flag bits");
     fsi::require((flags & fixed) == (ctx->C.prm.flags & fixed),
-                 "FSI_NO_RIGID_MODES and FSI_CLUSTER_COARSE are fixed at fsi_setup");
+                 "FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE and FSI_NO_PDL are fixed at fsi_setup");
     ctx->C.prm.flags = flags;
   });
 }

@@ -82,7 +82,9 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t*
   float* W = smem;
   float* act = smem + kParamsPadded;
   const int t = threadIdx.x;
+  // the weights do not depend on earlier kernels: load them before waiting for the previous one
   if (MODE != MODE_FEATURES) load_weights(W, w16);
+  dep_wait();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // the block loops in lockstep so that the weights stay loaded; idle threads skip the work
   const int64_t nb = (g.n_nodes + blockDim.x - 1) / blockDim.x * blockDim.x;
@@ -229,8 +231,7 @@ void launch_mlp(const MlpGeom& g, const uint16_t* w16, const double* rp, double*
   }
   int64_t b = (g.n_nodes + kNodeThreads - 1) / kNodeThreads;
   if (b > 152 * 3) b = 152 * 3;   // three 64 KB blocks fit one SM: one wave, weights loaded once per block
-  k_mlp<MODE><<<(int)(b < 1 ? 1 : b), kNodeThreads, kMlpSmem, s>>>(g, w16, rp, c, F, rho, H1, H2, ld);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_mlp<MODE>, (int)(b < 1 ? 1 : b), kNodeThreads, kMlpSmem, s, g, w16, rp, c, F, rho, H1, H2, ld);
 }
 
 // Backward through the MLP for one node: dY from dL/dc, then dH2 and dH1.
@@ -393,6 +394,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 __global__ void __launch_bounds__(kRT) k_learned_residual(int64_t n, const double* __restrict__ V, int64_t ldv,
                                                           const int* __restrict__ jdev, const double* __restrict__ w,
                                                           double* __restrict__ rp, double* __restrict__ part) {
+  dep_wait();
   __shared__ double sh[32];
   const double* v = V + (int64_t)(*jdev) * ldv;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -412,6 +414,7 @@ __global__ void __launch_bounds__(kRT) k_learned_residual(int64_t n, const doubl
 __global__ void __launch_bounds__(kRT) k_diff_sq(int64_t n, const double* __restrict__ rp,
                                                  const double* __restrict__ t, double* __restrict__ res,
                                                  double* __restrict__ part) {
+  dep_wait();
   __shared__ double sh[32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
@@ -429,6 +432,7 @@ __global__ void __launch_bounds__(kRT) k_diff_sq(int64_t n, const double* __rest
 // sums of both partial arrays (fixed order); accept iff ||rp - t||^2 < tau^2 ||rp||^2
 __global__ void __launch_bounds__(kRT) k_learned_decide(const double* __restrict__ part, int np, double tau2,
                                                         int* counters) {
+  dep_wait();
   __shared__ double sh[32];
   double a = 0.0, b = 0.0;
   for (int k = threadIdx.x; k < np; k += blockDim.x) {
@@ -447,6 +451,7 @@ __global__ void __launch_bounds__(kRT) k_learned_decide(const double* __restrict
 __global__ void k_learned_commit(int64_t n, const int* __restrict__ counters, const double* __restrict__ c,
                                  const double* __restrict__ t, double* __restrict__ Z, int64_t ldz,
                                  const int* __restrict__ jdev, double* __restrict__ w) {
+  dep_wait();
   if (counters[0] == 0) return;
   double* z = Z + (int64_t)(*jdev) * ldz;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -457,6 +462,7 @@ __global__ void k_learned_commit(int64_t n, const int* __restrict__ counters, co
 
 __global__ void k_harvest(int64_t n, const double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev,
                           const double* __restrict__ w, double* __restrict__ buf, int nvec) {
+  dep_wait();
   const int j = *jdev;
   if (j >= nvec) return;
   const double* v = V + (int64_t)j * ldv;
@@ -628,28 +634,23 @@ void mlp_features(const MlpGeom& g, const double* rp, float* F, float* rho, cuda
 
 void learned_residual(int64_t n, const double* V, int64_t ldv, const int* jdev, const double* w, double* rp,
                       double* part, cudaStream_t s) {
-  k_learned_residual<<<kRedBlocks, kRT, 0, s>>>(n, V, ldv, jdev, w, rp, part);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_learned_residual, kRedBlocks, kRT, 0, s, n, V, ldv, jdev, w, rp, part);
 }
 
 void learned_decide(int64_t n, const double* rp, const double* t, double tau, double* part, int* counters,
                     cudaStream_t s) {
-  k_diff_sq<<<kRedBlocks, kRT, 0, s>>>(n, rp, t, nullptr, part + kRedBlocks);
-  FSI_CHECK_LAUNCH();
-  k_learned_decide<<<1, kRT, 0, s>>>(part, kRedBlocks, tau * tau, counters);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_diff_sq, kRedBlocks, kRT, 0, s, n, rp, t, (double*)nullptr, part + kRedBlocks);
+  launch_k(k_learned_decide, 1, kRT, 0, s, part, kRedBlocks, tau * tau, counters);
 }
 
 void learned_commit(int64_t n, const int* counters, const double* c, const double* t, double* Z, int64_t ldz,
                     const int* jdev, double* w, cudaStream_t s) {
-  k_learned_commit<<<grid_elem(n), 256, 0, s>>>(n, counters, c, t, Z, ldz, jdev, w);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_learned_commit, grid_elem(n), 256, 0, s, n, counters, c, t, Z, ldz, jdev, w);
 }
 
 void harvest_residual(int64_t n, const double* V, int64_t ldv, const int* jdev, const double* w, double* buf,
                       int nvec, cudaStream_t s) {
-  k_harvest<<<grid_elem(n), 256, 0, s>>>(n, V, ldv, jdev, w, buf, nvec);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_harvest, grid_elem(n), 256, 0, s, n, V, ldv, jdev, w, buf, nvec);
 }
 
 // ---------------------------------------------------------------- training

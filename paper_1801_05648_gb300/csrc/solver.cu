@@ -57,6 +57,7 @@ void bsr_clone(const Bsr& A, Bsr& B, cudaStream_t s) {
 template <class Ti, class To>
 __global__ void k_col_in(int64_t n, const Ti* __restrict__ V, int64_t ldv, const int* __restrict__ jdev, int joff,
                          To* __restrict__ out) {
+  dep_wait();
   const int j = *jdev + joff;
   const Ti* src = V + (size_t)j * ldv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -66,6 +67,7 @@ __global__ void k_col_in(int64_t n, const Ti* __restrict__ V, int64_t ldv, const
 template <class T>
 __global__ void k_col_out(int64_t n, const T* __restrict__ in, double* __restrict__ zfix, double* __restrict__ Z,
                           int64_t ldz, const int* __restrict__ jdev) {
+  dep_wait();
   double* dst = Z + (size_t)(*jdev) * ldz;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = (double)in[i];
@@ -76,6 +78,7 @@ __global__ void k_col_out(int64_t n, const T* __restrict__ in, double* __restric
 // V_{j+1} = w / h  (left zero when h == 0)
 __global__ void k_scale_col(int64_t n, const double* __restrict__ w, const double* __restrict__ h,
                             double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev) {
+  dep_wait();
   const double hv = *h;
   double* dst = V + (size_t)(*jdev + 1) * ldv;
   const double inv = hv > 0.0 ? 1.0 / hv : 0.0;
@@ -90,6 +93,7 @@ __global__ void k_givens(int ldh, const int* __restrict__ jdev, const double* __
                          const double* __restrict__ h2, const double* __restrict__ hnorm, double* __restrict__ H,
                          double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
                          const double* __restrict__ inv_bnorm_p, double* __restrict__ out) {
+  dep_wait();
   const double inv_bnorm = *inv_bnorm_p;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int j = *jdev;
@@ -124,6 +128,7 @@ __global__ void k_givens(int ldh, const int* __restrict__ jdev, const double* __
 // H y = g, k x k upper triangular (column-major, leading dimension ldh); one thread
 __global__ void k_backsolve(int ldh, const int* __restrict__ kdev, const double* __restrict__ H,
                             const double* __restrict__ g, double* __restrict__ y) {
+  dep_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int k = *kdev;
   for (int i = k - 1; i >= 0; --i) {
@@ -134,6 +139,7 @@ __global__ void k_backsolve(int ldh, const int* __restrict__ kdev, const double*
 }
 
 __global__ void k_set_first(double* __restrict__ g, int len, double beta) {
+  dep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < len) g[i] = (i == 0) ? beta : 0.0;
 }
@@ -459,11 +465,9 @@ void iteration_body(Context& C) {
   const int64_t n = C.n;
   const int m = C.prm.restart;
   PrecWork<T>& W = pwork<T>(C);
-  k_col_in<double, T><<<grid_n(n), 256, 0, C.s>>>(n, C.V.p, n, C.jdev.p, 0, W.in.p);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_col_in<double, T>, grid_n(n), 256, 0, C.s, n, (const double*)C.V.p, n, (const int*)C.jdev.p, 0, W.in.p);
   precond_apply<T>(C, W.in.p, W.out.p);
-  k_col_out<T><<<grid_n(n), 256, 0, C.s>>>(n, W.out.p, C.zfix.p, C.Z.p, n, C.jdev.p);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_col_out<T>, grid_n(n), 256, 0, C.s, n, (const T*)W.out.p, C.zfix.p, C.Z.p, n, (const int*)C.jdev.p);
   apply_operator(C, C.zfix.p, C.wfix.p);
   if (C.harvest) harvest_residual(n, C.V.p, n, C.jdev.p, C.wfix.p, C.harvest, C.harvest_n, C.s);
   if (C.prm.flags & LEARNED) {
@@ -481,11 +485,9 @@ void iteration_body(Context& C) {
   mdot(n, C.V.p, n, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h2.p, m + 1, C.s);
   maxpy(n, C.V.p, n, C.jdev.p, 1, C.h2.p, 1.0, C.wfix.p, C.npart.p, C.s);
   finish_norm(C.npart.p, C.scal.p, C.s);
-  k_givens<<<1, 32, 0, C.s>>>(m + 1, C.jdev.p, C.h1.p, C.h2.p, C.scal.p, C.Hh.p, C.cs.p, C.sn.p, C.g.p,
-                              C.scal.p + 5, C.pinned_dev);
-  FSI_CHECK_LAUNCH();
-  k_scale_col<<<grid_n(n), 256, 0, C.s>>>(n, C.wfix.p, C.scal.p, C.V.p, n, C.jdev.p);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_givens, 1, 32, 0, C.s, m + 1, C.jdev.p, C.h1.p, C.h2.p, C.scal.p, C.Hh.p, C.cs.p, C.sn.p, C.g.p,
+           C.scal.p + 5, C.pinned_dev);
+  launch_k(k_scale_col, grid_n(n), 256, 0, C.s, n, C.wfix.p, C.scal.p, C.V.p, n, C.jdev.p);
 }
 
 void run_iteration(Context& C) {
@@ -564,8 +566,7 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
     if (relres <= tol) { status = OK; break; }
     if (total >= C.prm.maxit || breakdown) break;
     axpby<double>(n, 1.0 / beta, C.rvec.p, 0.0, C.V.p, C.s);
-    k_set_first<<<div_up(m + 2, 128), 128, 0, C.s>>>(C.g.p, m + 2, beta);
-    FSI_CHECK_LAUNCH();
+    launch_k(k_set_first, div_up(m + 2, 128), 128, 0, C.s, C.g.p, m + 2, beta);
     int k = 0;
     for (int j = 0; j < m; ++j) {
       C.pinned_j[0] = j;
@@ -586,8 +587,7 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
     if (nonfinite) break;
     C.pinned_j[1] = k;
     FSI_CUDA(cudaMemcpyAsync(C.kdev.p, C.pinned_j + 1, sizeof(int), cudaMemcpyHostToDevice, C.s));
-    k_backsolve<<<1, 32, 0, C.s>>>(m + 1, C.kdev.p, C.Hh.p, C.g.p, C.y.p);
-    FSI_CHECK_LAUNCH();
+    launch_k(k_backsolve, 1, 32, 0, C.s, m + 1, C.kdev.p, C.Hh.p, C.g.p, C.y.p);
     maxpy(n, C.Z.p, n, C.kdev.p, 0, C.y.p, -1.0, x, nullptr, C.s);
     ++C.last_cycles;
   }

@@ -23,9 +23,11 @@ struct SolverParams {
   double spmv_wave_fraction = 1.0;
   int spmv_unroll = 4;
   double learned_accept = 0.1;   // accept the learned correction when ||r' - A c|| < this * ||r'||
+  int spmv_prefetch = 1;
+  double cluster_max_bytes = 6.0e6;
 };
 
-enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8, LEARNED = 16 };
+enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8, LEARNED = 16, NO_PDL = 32 };
 
 template <class T>
 struct PrecWork {

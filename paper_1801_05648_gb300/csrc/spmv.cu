@@ -13,16 +13,25 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
   if (A1.nbr == 0) return;
   const int tpr = sizeof(T) == 8 ? A1.tpr64 : A1.tpr;
   const int threads = 256;
-  const int blocks = div_up((int64_t)A1.nbr * tpr, threads);
+  const int per_pass = threads / tpr;
+  const SpmvTuning& tu = spmv_tuning();
+  int rows_per_cta = per_pass;
+  int blocks = div_up(A1.nbr, per_pass);
+  if (tu.prefetch >= 2 && blocks > 152 * tu.ctas_per_sm) {
+    // persistent: at most ctas_per_sm CTAs per SM, each over a longer contiguous slice
+    const int passes = div_up(blocks, 152 * tu.ctas_per_sm);
+    rows_per_cta = passes * per_pass;
+    blocks = div_up(A1.nbr, rows_per_cta);
+  }
   const T* v2 = nullptr; const int* rp2 = nullptr; const int* ci2 = nullptr;
   if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; }
-  if (spmv_tuning().unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
-    k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8><<<blocks, threads, 0, s>>>(A1.nbr, tpr, A1.rowptr.p, A1.colind.p,
-                                                                       A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
+  const int pf = tu.prefetch > 0 ? 1 : 0;
+  if (tu.unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
+    launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf,
+             A1.rowptr.p, A1.colind.p, A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
   else
-    k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4><<<blocks, threads, 0, s>>>(A1.nbr, tpr, A1.rowptr.p, A1.colind.p,
-                                                                       A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
-  FSI_CHECK_LAUNCH();
+    launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf,
+             A1.rowptr.p, A1.colind.p, A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
 }
 
 template <class T, int BR, int BC1, int BC2, class Epi>

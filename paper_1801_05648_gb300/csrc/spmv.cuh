@@ -249,29 +249,62 @@ __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const
   }
 }
 
+// L2 prefetch of the 16-byte-aligned interior of [p, p + bytes) (one bulk
+// prefetch per 64 KB; the unaligned edges are left to the ordinary loads).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
+  const uintptr_t a0 = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  for (uintptr_t a = a0; a < e; a += 65536) {
+    const uint32_t n = (uint32_t)(e - a < 65536 ? e - a : 65536);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+  }
+#endif
+}
+
+// One CTA handles the contiguous block rows [blockIdx.x * rows_per_cta, + rows_per_cta),
+// blockDim.x / tpr rows per pass, tpr lanes per row.  With prefetch, thread 0 first
+// asks L2 for the CTA's slice of the (constant) matrix arrays, before waiting for the
+// previous kernel (programmatic dependent launch), so the slice streams in while
+// that kernel drains and while the CTA works through its first rows.
 template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4>
-__global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr,
+__global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per_cta, int prefetch,
     const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, G1 g1,
     const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, const T* __restrict__ x2,
     Epi epi) {
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row = gtid / tpr;
-  const int lane = threadIdx.x & (tpr - 1);
-  const bool valid = row < nbr;
-  T acc[BR];
-#pragma unroll
-  for (int i = 0; i < BR; ++i) acc[i] = T(0);
-  typename Epi::Pre pre;
-  if (valid && lane == 0) pre = epi.load(row);
-  if (valid) {
-    row_accumulate<T, BR, BC1, UREQ>(ci1, v1, g1, rp1[row], rp1[row + 1], lane, tpr, acc);
-    if constexpr (BC2 > 0)
-      row_accumulate<T, BR, BC2, UREQ>(ci2, v2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr, acc);
+  const int r0 = blockIdx.x * rows_per_cta;
+  const int r1 = r0 + rows_per_cta < nbr ? r0 + rows_per_cta : nbr;
+  if (prefetch && threadIdx.x == 0 && r0 < r1) {
+    const int a = rp1[r0], b = rp1[r1];
+    prefetch_l2(v1 + (size_t)a * BR * BC1, sizeof(T) * (size_t)(b - a) * BR * BC1);
+    prefetch_l2(ci1 + a, sizeof(int) * (size_t)(b - a));
+    if constexpr (BC2 > 0) {
+      const int a2 = rp2[r0], b2 = rp2[r1];
+      prefetch_l2(v2 + (size_t)a2 * BR * BC2, sizeof(T) * (size_t)(b2 - a2) * BR * BC2);
+      prefetch_l2(ci2 + a2, sizeof(int) * (size_t)(b2 - a2));
+    }
   }
-  for (int off = tpr >> 1; off > 0; off >>= 1)
+  dep_wait();
+  const int per_pass = blockDim.x / tpr;
+  const int lane = threadIdx.x & (tpr - 1);
+  for (int base = r0; base < r1; base += per_pass) {
+    const int row = base + threadIdx.x / tpr;
+    const bool valid = row < r1;
+    T acc[BR];
 #pragma unroll
-    for (int i = 0; i < BR; ++i) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off, tpr);
-  if (valid && lane == 0) epi.store(row, acc, pre);
+    for (int i = 0; i < BR; ++i) acc[i] = T(0);
+    typename Epi::Pre pre;
+    if (valid && lane == 0) pre = epi.load(row);
+    if (valid) {
+      row_accumulate<T, BR, BC1, UREQ>(ci1, v1, g1, rp1[row], rp1[row + 1], lane, tpr, acc);
+      if constexpr (BC2 > 0)
+        row_accumulate<T, BR, BC2, UREQ>(ci2, v2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr, acc);
+    }
+    for (int off = tpr >> 1; off > 0; off >>= 1)
+#pragma unroll
+      for (int i = 0; i < BR; ++i) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off, tpr);
+    if (valid && lane == 0) epi.store(row, acc, pre);
+  }
 }
 
 // ------------------------------------------------------------------ host API

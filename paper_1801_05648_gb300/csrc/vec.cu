@@ -14,6 +14,7 @@ inline int grid_for(int64_t n) {
 
 template <class T>
 __global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  dep_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T v = a * x[i];
     if (b != T(0)) v += b * y[i];
@@ -23,18 +24,21 @@ __global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restr
 
 template <class T>
 __global__ void k_axpbyz(int64_t n, T a, const T* __restrict__ x, T b, const T* __restrict__ y, T* __restrict__ z) {
+  dep_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     z[i] = a * x[i] + b * y[i];
 }
 
 template <class T>
 __global__ void k_vmul(int64_t n, const T* __restrict__ x, const T* __restrict__ w, T* __restrict__ y) {
+  dep_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = x[i] * w[i];
 }
 
 template <class Ti, class To>
 __global__ void k_cast(int64_t n, const Ti* __restrict__ x, To* __restrict__ y) {
+  dep_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (To)x[i];
 }
@@ -57,6 +61,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 template <class T>
 __global__ void __launch_bounds__(kRedThreads) k_dot_partial(int64_t n, const T* __restrict__ x,
                                                               const T* __restrict__ y, double* __restrict__ partials) {
+  dep_wait();
   __shared__ double sh[32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
@@ -70,6 +75,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_partial(int64_t n, const T*
 // out[c] = (sqrt?) sum_k partials[c * np + k], one block per column c
 __global__ void __launch_bounds__(kRedThreads) k_reduce_cols(const double* __restrict__ partials, int np,
                                                              const int* jcount, int joff, double* out, int take_sqrt) {
+  dep_wait();
   __shared__ double sh[32];
   const int c = blockIdx.x;
   const int J = jcount ? (*jcount + joff) : joff;
@@ -86,6 +92,7 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot_partial(int64_t n, const d
                                                               const int* __restrict__ jcount, int joff,
                                                               const double* __restrict__ w,
                                                               double* __restrict__ partials) {
+  dep_wait();
   __shared__ double sh[32];
   const int J = *jcount + joff;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -115,6 +122,7 @@ __global__ void __launch_bounds__(kRedThreads) k_maxpy(int64_t n, const double* 
                                                        const int* __restrict__ jcount, int joff,
                                                        const double* __restrict__ h, double sign,
                                                        double* __restrict__ w, double* __restrict__ nrm_partials) {
+  dep_wait();
   __shared__ double hs[256];
   __shared__ double sh[32];
   const int J = *jcount + joff;
@@ -148,33 +156,27 @@ __global__ void __launch_bounds__(kRedThreads) k_maxpy(int64_t n, const double* 
 template <class T>
 void axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s) {
   if (n <= 0) return;
-  k_axpby<T><<<grid_for(n), kThreads, 0, s>>>(n, a, x, b, y);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_axpby<T>, grid_for(n), kThreads, 0, s, n, a, x, b, y);
 }
 template <class T>
 void axpbyz(int64_t n, T a, const T* x, T b, const T* y, T* z, cudaStream_t s) {
   if (n <= 0) return;
-  k_axpbyz<T><<<grid_for(n), kThreads, 0, s>>>(n, a, x, b, y, z);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_axpbyz<T>, grid_for(n), kThreads, 0, s, n, a, x, b, y, z);
 }
 template <class T>
 void vmul(int64_t n, const T* x, const T* w, T* y, cudaStream_t s) {
   if (n <= 0) return;
-  k_vmul<T><<<grid_for(n), kThreads, 0, s>>>(n, x, w, y);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_vmul<T>, grid_for(n), kThreads, 0, s, n, x, w, y);
 }
 template <class Ti, class To>
 void cast(int64_t n, const Ti* x, To* y, cudaStream_t s) {
   if (n <= 0) return;
-  k_cast<Ti, To><<<grid_for(n), kThreads, 0, s>>>(n, x, y);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_cast<Ti, To>, grid_for(n), kThreads, 0, s, n, x, y);
 }
 template <class T>
 void dot_dev(int64_t n, const T* x, const T* y, double* partials, double* out, cudaStream_t s) {
-  k_dot_partial<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, x, y, partials);
-  FSI_CHECK_LAUNCH();
-  k_reduce_cols<<<1, kRedThreads, 0, s>>>(partials, kRedBlocks, nullptr, 1, out, 0);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_dot_partial<T>, kRedBlocks, kRedThreads, 0, s, n, x, y, partials);
+  launch_k(k_reduce_cols, 1, kRedThreads, 0, s, partials, kRedBlocks, (const int*)nullptr, 1, out, 0);
 }
 template <class T>
 double dot_host(int64_t n, const T* x, const T* y, double* partials, double* out, cudaStream_t s) {
@@ -187,21 +189,17 @@ double dot_host(int64_t n, const T* x, const T* y, double* partials, double* out
 
 void mdot(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* w, double* partials,
           double* h, int maxcols, cudaStream_t s) {
-  k_mdot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, V, ldv, jcount, joff, w, partials);
-  FSI_CHECK_LAUNCH();
-  k_reduce_cols<<<maxcols, kRedThreads, 0, s>>>(partials, kRedBlocks, jcount, joff, h, 0);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_mdot_partial, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, w, partials);
+  launch_k(k_reduce_cols, maxcols, kRedThreads, 0, s, partials, kRedBlocks, jcount, joff, h, 0);
 }
 
 void maxpy(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* h, double sign,
            double* w, double* nrm_partials, cudaStream_t s) {
-  k_maxpy<<<kRedBlocks, kRedThreads, 0, s>>>(n, V, ldv, jcount, joff, h, sign, w, nrm_partials);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_maxpy, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, h, sign, w, nrm_partials);
 }
 
 void finish_norm(const double* partials, double* out, cudaStream_t s) {
-  k_reduce_cols<<<1, kRedThreads, 0, s>>>(partials, kRedBlocks, nullptr, 1, out, 1);
-  FSI_CHECK_LAUNCH();
+  launch_k(k_reduce_cols, 1, kRedThreads, 0, s, partials, kRedBlocks, (const int*)nullptr, 1, out, 1);
 }
 
 template void axpby<double>(int64_t, double, const double*, double, double*, cudaStream_t);

@@ -40,6 +40,7 @@ def test_default_params(lib):
     assert (p2.restart, p2.maxit, p2.cheb_degree, p2.vcycles_solid, p2.mass_degree) == (100, 1000, 4, 2, 12)
     assert p2.mass_ratio == 8.0 and p3.mass_ratio == 20.0
     assert p2.strength_theta == 0.08 and p2.dt_theta == 0.01
+    assert (p2.cheb_degree_coarse, p2.spmv_prefetch, p2.cluster_max_bytes) == (2, 1, 6.0e6)
 
 
 def _setup(lib, dim, n, rowptr, colind, vals, off, params=None):
