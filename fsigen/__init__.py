@@ -127,6 +127,8 @@ CONFIGS = {
     "2d_tiny": FSIConfig("2d_tiny", 2, (16, 16)),
     # 256x128 cells: n = 560,517
     "2d_mid": FSIConfig("2d_mid", 2, (256, 128)),
+    # 512x256 cells: n = 2,235,141 (kernel profiles above L2 size, a few GB on the device)
+    "2d_512x256": FSIConfig("2d_512x256", 2, (512, 256)),
     # 32x16x16 hex cells on [0,2]x[0,1]^2, solid slab z < 0.25: n = 434,247
     "3d": FSIConfig("3d", 3, (32, 16, 16)),
     # 1024x512 cells: n = 8,926,725.  Run at amplitude 1e-2: at 5e-2 the seed-0

@@ -85,11 +85,10 @@ typedef struct fsi_params {
   /* solid mass solve: Chebyshev polynomial on D^-1 A_uu */
   int mass_degree;          /* (12) */
   double mass_ratio;        /* interval [lambda/ratio, upper*lambda] (8 in 2D, 20 in 3D) */
-  /* SpMV launch shape: lanes per block row are chosen so a launch holds about
-     spmv_wave_fraction x (152 SMs x 2048 threads) threads (1.0); each lane loads
-     spmv_unroll blocks (4 or 8; 8 applies to blocks of at most 24 bytes) before
-     multiplying (4).  Process-wide: the last fsi_setup's values apply. */
-  double spmv_wave_fraction;
+  /* SpMV launch shape: lanes per block row follow the mean row length (each lane
+     takes at least 2 blocks in FP32, 8 in FP64); each lane loads spmv_unroll blocks
+     (4 or 8; 8 applies to blocks of at most 24 bytes) before multiplying (4).
+     Process-wide: the last fsi_setup's values apply. */
   int spmv_unroll;
   /* learned stage: take the correction only when ||r' - A c|| < learned_accept * ||r'||
      (0.1; at 0.3 and above the trained stage's accepted corrections stall FGMRES) */

@@ -114,23 +114,22 @@ struct Bsr {
 template <> inline const double* Bsr::vals<double>() const { return v64.p; }
 template <> inline const float* Bsr::vals<float>() const { return v32.p; }
 
-// Lanes per block row.  Enough lanes that a launch fills about `target_threads`
-// threads (default one wave: 152 SMs x 2048) when the rows are long enough,
-// while each lane keeps at least `min_per_lane` blocks.  FP32 rows stop at two
-// blocks per lane.  FP64 rows keep at least eight: the FP64 pipe of this GPU
-// retires a small fraction of the FP32 rate, and the shuffle reduction across a
-// wide lane group would cost more FP64 instructions than the products themselves.
-constexpr double kWaveThreads = 152.0 * 2048.0;
-inline int lanes_for(int64_t nnzb, int nbr, double min_per_lane, double target_threads) {
+// Lanes per block row: the most lanes (a power of two, at most 32) that leave
+// each lane at least `min_per_lane` blocks of an average row, so a row's blocks
+// are read by neighbouring lanes (coalesced) in about one pass per lane,
+// whatever the number of rows.  FP32 rows keep two blocks per lane.  FP64 rows
+// keep at least eight: the FP64 pipe of this GPU retires a small fraction of the
+// FP32 rate, and the shuffle reduction across a wide lane group would cost more
+// FP64 instructions than the products themselves.
+inline int lanes_for(int64_t nnzb, int nbr, double min_per_lane) {
   const double mean = nbr ? (double)nnzb / nbr : 0.0;
   int t = 1;
-  while (t < 32 && (double)nbr * t < target_threads && mean / (2 * t) >= min_per_lane) t *= 2;
+  while (t < 32 && mean / (2 * t) >= min_per_lane) t *= 2;
   return t;
 }
 
-// SpMV launch shape knobs (fsi_params: spmv_wave_fraction, spmv_unroll).
+// SpMV launch shape knobs (fsi_params: spmv_unroll, spmv_prefetch).
 struct SpmvTuning {
-  double target_threads = kWaveThreads;
   int unroll = 4;      // blocks each lane loads before multiplying: 4 or 8 (8 only for small blocks)
   int prefetch = 1;    // 0 none, 1 L2 bulk prefetch of each CTA's matrix slice, 2 also persistent CTAs
   int ctas_per_sm = 5; // persistent grid size per SM (prefetch 2)
@@ -141,8 +140,8 @@ inline SpmvTuning& spmv_tuning() {
 }
 
 inline void set_tpr(Bsr& A) {
-  A.tpr = lanes_for(A.nnzb, A.nbr, 2.0, spmv_tuning().target_threads);
-  A.tpr64 = lanes_for(A.nnzb, A.nbr, 8.0, spmv_tuning().target_threads);
+  A.tpr = lanes_for(A.nnzb, A.nbr, 2.0);
+  A.tpr64 = lanes_for(A.nnzb, A.nbr, 8.0);
 }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

@@ -63,7 +63,6 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.vc_pressure = p.vcycles_pressure;
   s.mass_degree = p.mass_degree;
   s.mass_ratio = p.mass_ratio;
-  s.spmv_wave_fraction = p.spmv_wave_fraction;
   s.spmv_unroll = p.spmv_unroll;
   s.learned_accept = p.learned_accept;
   s.spmv_prefetch = p.spmv_prefetch;
@@ -81,7 +80,6 @@ void validate_params(const fsi::SolverParams& s) {
   require(s.vc_mesh >= 1 && s.vc_solid >= 1 && s.vc_fluid >= 1 && s.vc_pressure >= 1, "V-cycle counts");
   require(s.mass_degree >= 1 && s.mass_ratio > 1.0, "mass solve settings");
   require(std::isfinite(s.dt_theta), "dt_theta");
-  require(s.spmv_wave_fraction > 0.0 && s.spmv_wave_fraction <= 64.0, "spmv_wave_fraction must be in (0, 64]");
   require(s.spmv_unroll == 4 || s.spmv_unroll == 8, "spmv_unroll must be 4 or 8");
   require(s.learned_accept > 0.0 && s.learned_accept <= 1.0, "learned_accept must be in (0, 1]");
   require(s.spmv_prefetch >= 0 && s.spmv_prefetch <= 2, "spmv_prefetch must be 0, 1 or 2");
@@ -145,7 +143,6 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->vcycles_pressure = 1;
   p->mass_degree = 12;
   p->mass_ratio = dim == 3 ? 20.0 : 8.0;
-  p->spmv_wave_fraction = 1.0;
   p->spmv_unroll = 4;
   p->learned_accept = 0.1;
   p->spmv_prefetch = 1;
@@ -178,7 +175,6 @@ int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const in
       FSI_CUDA(cudaStreamCreateWithFlags(&ctx->C.s, cudaStreamNonBlocking));
       ctx->C.own_stream = true;
     }
-    fsi::spmv_tuning().target_threads = fsi::kWaveThreads * ctx->C.prm.spmv_wave_fraction;
     fsi::spmv_tuning().unroll = ctx->C.prm.spmv_unroll;
     fsi::spmv_tuning().prefetch = ctx->C.prm.spmv_prefetch;
     fsi::coarse_max_bytes() = ctx->C.prm.cluster_max_bytes;

@@ -20,7 +20,6 @@ struct SolverParams {
   int vc_mesh = 1, vc_solid = 2, vc_fluid = 1, vc_pressure = 1;
   int mass_degree = 12;
   double mass_ratio = 8.0;
-  double spmv_wave_fraction = 1.0;
   int spmv_unroll = 4;
   double learned_accept = 0.1;   // accept the learned correction when ||r' - A c|| < this * ||r'||
   int spmv_prefetch = 1;

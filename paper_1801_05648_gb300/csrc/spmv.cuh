@@ -214,28 +214,33 @@ __host__ __device__ constexpr int unroll_for() {
 }
 
 // acc += sum over the lane's share of row entries [kb, ke) of block * x[col].
-// The U column indices are loaded first, then the U blocks and x segments, so a
-// lane keeps U independent requests in flight before it multiplies.
+// The U column indices and the U blocks are requested together (which entries
+// exist follows from the position alone), then the x segments, which need the
+// indices: one dependent memory round trip for the matrix data, one for x.
 template <class T, int BR, int BC, int UREQ, class G>
 __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const T* __restrict__ v, const G& gx,
                                                int kb, int ke, int lane, int tpr, T* acc) {
   constexpr int U = unroll_for<T, BR, BC, UREQ>();
   for (int k0 = kb + lane; k0 < ke; k0 += tpr * U) {
     int col[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + u * tpr;
-      col[u] = k < ke ? __ldcs(ci + k) : -1;
-    }
     T blk[U][BR * BC], xv[U][BC];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (col[u] >= 0) {
-        load_stream<T, BR * BC>(v + (size_t)(k0 + u * tpr) * (BR * BC), blk[u]);
-        gx(col[u], xv[u]);
+      const int k = k0 + u * tpr;
+      if (k < ke) {
+        col[u] = __ldcs(ci + k);
+        load_stream<T, BR * BC>(v + (size_t)k * (BR * BC), blk[u]);
       } else {
+        col[u] = -1;
 #pragma unroll
         for (int t = 0; t < BR * BC; ++t) blk[u][t] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u * tpr < ke) {
+        gx(col[u], xv[u]);
+      } else {
 #pragma unroll
         for (int t = 0; t < BC; ++t) xv[u][t] = T(0);
       }

@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
                 ("presmooth", ctypes.c_int), ("postsmooth", ctypes.c_int), ("vcycles_mesh", ctypes.c_int),
                 ("vcycles_solid", ctypes.c_int), ("vcycles_fluid", ctypes.c_int),
                 ("vcycles_pressure", ctypes.c_int), ("mass_degree", ctypes.c_int), ("mass_ratio", ctypes.c_double),
-                ("spmv_wave_fraction", ctypes.c_double), ("spmv_unroll", ctypes.c_int),
+                ("spmv_unroll", ctypes.c_int),
                 ("learned_accept", ctypes.c_double), ("spmv_prefetch", ctypes.c_int),
                 ("cluster_max_bytes", ctypes.c_double), ("cheb_degree_coarse", ctypes.c_int)]
 

@@ -173,6 +173,52 @@ def test_graph_replay_is_bit_identical(torch_cuda):
     assert np.array_equal(xs[0], xs[2]) and np.array_equal(xs[1], xs[3])
 
 
+def test_launch_modes_are_bit_identical(torch_cuda):
+    """Programmatic dependent launch on/off and the SpMV prefetch modes change only
+    launch attributes and the assignment of rows to CTAs: every solve is bit-identical.
+    (Both knobs are process-wide; each fsi_setup sets them from its parameters.)"""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    s, o, ref, _, mr = case("2d_64x32", torch)
+    b = torch.tensor(s.rhs, device="cuda")
+    G = P.FSI_USE_GRAPHS
+    modes = [dict(flags=G), dict(flags=G | P.FSI_NO_PDL), dict(flags=G, spmv_prefetch=0),
+             dict(flags=G, spmv_prefetch=2), dict(flags=0, spmv_prefetch=0)]
+    for prec in ("fp64", "fp32"):
+        first = None
+        for kw in modes:
+            g = P.FSISolver.from_system(s, params=P.default_params(2, **kw))
+            g.precond_build(prec)
+            x = torch.zeros_like(b)
+            st = g.solve(b, x, 1e-8)
+            g.close()
+            if first is None:
+                first = (x, st.iters)
+            else:
+                assert torch.equal(x, first[0]) and st.iters == first[1], (prec, kw)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 3])
+def test_coarse_chebyshev_degree_parity(deg, torch_cuda):
+    """The coarse-level Chebyshev degree (0: the level-0 degree everywhere) is the
+    same algorithm on both sides: FP64 solves agree like the default ones."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    cfg, mr = CASES["2d_64x32"]
+    s = fsigen.make_system(cfg)
+    o = oracle.OracleSolver.from_system(
+        s, params=oracle.PrecondParams(mass_ratio=mr, amg=oracle.AMGParams(cheb_degree_coarse=deg)))
+    ref = o.solve(s.rhs)
+    g = P.FSISolver.from_system(s, params=P.default_params(2, mass_ratio=mr, cheb_degree_coarse=deg))
+    g.precond_build("fp64")
+    b = torch.tensor(s.rhs, device="cuda")
+    x = torch.zeros_like(b)
+    st = g.solve(b, x, 1e-8)
+    g.close()
+    assert st.status == 0 and abs(st.iters - ref.iters) <= 1, (st.iters, ref.iters)
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-8
+
+
 def test_edge_cases(torch_cuda):
     torch = torch_cuda
     import paper_1801_05648_gb300 as P
