@@ -59,16 +59,20 @@ enum {
                               (fewer launches, but slower on the 256x128 case: 26.7 vs 15.7 ms) */
   FSI_LEARNED = 16,        /* apply the learned correction stage after P^-1 in every FGMRES
                               iteration (needs fsi_learned_setup and weights; see below) */
-  FSI_NO_PDL = 32          /* launch the solve's kernels without programmatic dependent launch
+  FSI_NO_PDL = 32,         /* launch the solve's kernels without programmatic dependent launch
                               (each kernel then waits for the previous one to finish before it
                               is scheduled).  Process-wide: the last fsi_setup's choice applies */
+  FSI_GRID_COARSE = 64     /* like FSI_CLUSTER_COARSE, but the coarse levels run as one cooperative
+                              launch over half the GPU with a software grid barrier (bounded
+                              waits: a barrier that times out makes fsi_solve return FSI_ECUDA).
+                              Not together with FSI_CLUSTER_COARSE */
 };
 
 typedef struct fsi_params {
   int restart;              /* FGMRES restart length m (default 100) */
   int maxit;                /* maximum FGMRES iterations (default 1000) */
   int flags;                /* FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE |
-                               FSI_LEARNED | FSI_NO_PDL */
+                               FSI_LEARNED | FSI_NO_PDL | FSI_GRID_COARSE */
   double dt_theta;          /* c = dt*theta of the solid Schur complement S_hat = A_vv + c A_vu (0.01) */
   /* smoothed-aggregation AMG */
   double strength_theta;    /* strength threshold on node-block Frobenius norms (0.08) */
@@ -98,8 +102,8 @@ typedef struct fsi_params {
      CTAs per SM walking longer slices (1; measured on the 256x128 case: FP64 solve
      52.2 -> 49.2 ms, FP32 unchanged, 2 slower).  Process-wide, like the other SpMV knobs. */
   int spmv_prefetch;
-  /* FSI_CLUSTER_COARSE: levels whose matrix values take at most this many bytes run in
-     the cluster launch (6e6).  Process-wide. */
+  /* FSI_CLUSTER_COARSE / FSI_GRID_COARSE: levels whose matrix values take at most this
+     many bytes run in the single coarse launch (6e6).  Process-wide. */
   double cluster_max_bytes;
   /* Chebyshev degree on the coarser AMG levels (>= 1); 0 = cheb_degree on every level (2:
      256x128 solve 14.3 -> 13.0 ms at 11-12 iterations; 1024x512 +3%, 35 vs 33 iterations) */
@@ -306,8 +310,8 @@ int fsi_learned_features(fsi_ctx* ctx, const double* r_dev, float* feat_dev, flo
 /* Change fsi_params.learned_accept (in (0, 1]) of a context. */
 int fsi_set_learned_accept(fsi_ctx* ctx, double tau);
 /* Change the run-time flags of a context (FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_LEARNED);
- * FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE and FSI_NO_PDL are fixed at fsi_setup (FSI_EINVAL if
- * they differ). */
+ * FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_GRID_COARSE and FSI_NO_PDL are fixed at fsi_setup
+ * (FSI_EINVAL if they differ). */
 int fsi_set_flags(fsi_ctx* ctx, int flags);
 /*
  * fsi_set_harvest - during later fsi_solve calls, store the preconditioned

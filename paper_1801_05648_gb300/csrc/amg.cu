@@ -352,7 +352,7 @@ void vcycle_level(Hierarchy& H, int l, const T* b, T* x, cudaStream_t s) {
     const CoarseRun<T>& run = [&]() -> const CoarseRun<T>& {
       if constexpr (sizeof(T) == 8) return H.crun64; else return H.crun32;
     }();
-    if (H.use_cluster && run.first == l && run.cluster > 0) {
+    if (H.coarse_mode != COARSE_PER_LEVEL && run.first == l && run.ctas > 0) {
       coarse_vcycle<T>(run, b, x, s);
       return;
     }
@@ -552,7 +552,7 @@ void amg_setup(Hierarchy& H, Bsr&& A0, const double* B0, int k0, const AmgParams
   require(dense_inverse((int)nc, dense.p, H.cinv64.p, s), "amg_setup: singular coarsest matrix");
   FSI_CUDA(cudaStreamSynchronize(s));
   const int first = coarse_first_level(H, 8);
-  if (first >= 0 && H.use_cluster) coarse_plan_build<double>(H, first, H.crun64, s);
+  if (first >= 0 && H.coarse_mode != COARSE_PER_LEVEL) coarse_plan_build<double>(H, first, H.crun64, s);
 }
 
 int coarse_first_level(const Hierarchy& H, int value_bytes) {
@@ -582,7 +582,7 @@ void amg_make_fp32(Hierarchy& H, cudaStream_t s) {
   H.has_fp32 = true;
   FSI_CUDA(cudaStreamSynchronize(s));
   const int first = coarse_first_level(H, 4);
-  if (first >= 0 && H.use_cluster) coarse_plan_build<float>(H, first, H.crun32, s);
+  if (first >= 0 && H.coarse_mode != COARSE_PER_LEVEL) coarse_plan_build<float>(H, first, H.crun32, s);
 }
 
 template <class T>

@@ -59,8 +59,9 @@ struct AmgLevel {
   int64_t n() const { return A.rows(); }
 };
 
-// ---- coarse end of a V-cycle in one cluster launch (coarse.cu)
-constexpr int kCoarseThreads = 512;       // threads per CTA of the cluster kernel
+// ---- coarse end of a V-cycle in one launch (coarse.cu): a thread-block cluster, or a
+// cooperative grid over half the GPU with a software grid barrier
+constexpr int kCoarseThreads = 512;       // threads per CTA of the coarse kernel
 constexpr int kCoarseMaxLevels = 8;
 constexpr int kCoarseMaxDeg = 16;
 // levels whose matrix has at most this many value bytes run in the cluster (fsi_params.cluster_max_bytes)
@@ -80,26 +81,32 @@ struct CoarseLevel {
   const void* dinv = nullptr;
   void* b = nullptr; void* x = nullptr; void* xb = nullptr; void* r = nullptr; void* d = nullptr;
   double inv_theta = 0.0;
+  int deg = 0;   // Chebyshev degree of this level
   double c1[kCoarseMaxDeg] = {}, c2[kCoarseMaxDeg] = {};
 };
 struct CoarsePlan {
-  int nlev = 0, deg = 0, presmooth = 1, postsmooth = 1;
+  int nlev = 0, presmooth = 1, postsmooth = 1;
   CoarseLevel lev[kCoarseMaxLevels];
   const void* cinv = nullptr;
   int ncoarse = 0;
 };
+enum CoarseMode { COARSE_PER_LEVEL = 0, COARSE_CLUSTER = 1, COARSE_GRID = 2 };
+
 template <class T>
 struct CoarseRun {
   DBuf<CoarsePlan> plan;
-  int cluster = 0;   // CTAs per cluster (0: not available)
-  int first = -1;    // first level handled by the cluster kernel (-1: none)
+  int mode = COARSE_PER_LEVEL;
+  int ctas = 0;      // CTAs of the launch (cluster size, or cooperative grid size); 0: not available
+  int first = -1;    // first level handled by the coarse kernel (-1: none)
+  DBuf<unsigned> bar;   // grid barrier: arrivals, generation
+  DBuf<int> err;        // set when a grid barrier wait gave up
 };
 
 struct Hierarchy {
   std::vector<AmgLevel> levels;
   CoarseRun<double> crun64;
   CoarseRun<float> crun32;
-  bool use_cluster = false;   // run the small coarse levels in one cluster launch (opt-in)
+  int coarse_mode = COARSE_PER_LEVEL;   // how the small coarse levels run (opt-in: one launch)
   int ncoarse = 0;
   DBuf<double> cinv64;
   DBuf<float> cinv32;
@@ -130,6 +137,9 @@ template <class T> void amg_vcycle(Hierarchy& H, const T* b, T* x, cudaStream_t 
 template <class T> void coarse_plan_build(Hierarchy& H, int first, CoarseRun<T>& run, cudaStream_t s);
 // V-cycle of levels [run.first, end) from x = 0 in one launch (b, x: level run.first sized).
 template <class T> void coarse_vcycle(const CoarseRun<T>& run, const T* b, T* x, cudaStream_t s);
+// True when a grid-barrier wait of the hierarchy's coarse kernel gave up since the
+// last check (the barrier state is then reset).  Waits for the stream.
+bool coarse_failed(Hierarchy& H, cudaStream_t s);
 // First level from which every level is small enough for the cluster kernel, or
 // -1 when that leaves only the dense coarsest level.
 int coarse_first_level(const Hierarchy& H, int value_bytes);

@@ -3,18 +3,21 @@
 // Levels whose matrices are small (a few MB) leave most of the GPU idle and
 // cost a kernel launch per smoothing step, residual, restriction and
 // prolongation.  Here every level from `first` down to the dense coarsest solve
-// and back up runs inside one thread-block cluster: the CTAs of the cluster
-// share the rows of each step and meet at a hardware cluster barrier between
-// dependent steps.  The arithmetic is that of the per-level path (Chebyshev
-// steps with the same coefficients, residual, R, coarsest dense solve, P
-// correction); only the launch granularity differs.
+// and back up runs inside one launch whose CTAs share the rows of each step and
+// meet at a barrier between dependent steps: either one thread-block cluster
+// (hardware cluster barrier), or a cooperative grid over half the GPU's
+// co-resident CTAs (software grid barrier; half, so that the two concurrent
+// sub-solve branches of Alg. 2 can both be resident).  The arithmetic is that of
+// the per-level path (Chebyshev steps with the same coefficients, residual, R,
+// coarsest dense solve, P correction); only the launch granularity differs.
 //
 // Memory ordering: vectors written in one step are read by other CTAs in the
-// next.  Those loads go through L2 (ld.global.cg) after the cluster barrier
-// (arrive.release / wait.acquire); read-only data (matrices, D^-1, the coarse
-// inverse) uses the read-only path.  Every barrier sits in control flow that is
-// uniform across the cluster (loop bounds come from the plan), and no thread
-// leaves the kernel before the last barrier.
+// next.  Those loads go through L2 (ld.global.cg) after the barrier; read-only
+// data (matrices, D^-1, the coarse inverse) uses the read-only path.  Every
+// barrier sits in control flow that is uniform across the CTAs (loop bounds come
+// from the plan).  The grid barrier's wait is bounded: a CTA that waits too long
+// sets the run's error flag and leaves the kernel (the solve then reports the
+// failure), so the kernel cannot hang.
 #include "amg.cuh"
 #include "spmv.cuh"
 
@@ -49,6 +52,46 @@ __device__ __forceinline__ void row_prod(const CoarseMat& M, const T* x, int row
 }
 
 enum StepKind { kCheb = 0, kResid = 1, kAxpy = 2 };
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Spins (with ~64 ns sleeps) a CTA waits at a grid barrier before it gives up.
+constexpr unsigned kBarrierSpins = 1u << 22;
+
+// Grid-wide barrier over `nblocks` co-resident CTAs: bar[0] counts arrivals,
+// bar[1] is the generation the last arrival advances.  Returns false (in every
+// thread of the CTA) when the wait gave up; err is then set.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = ld_acquire(bar + 1);
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned spins = 0;
+      while (ld_acquire(bar + 1) == g) {
+        if (++spins > kBarrierSpins) {
+          ok = 0;
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
 
 // One pass over the rows of M: acc = M x, then per row
 //   kCheb : r = dinv (b - acc); d = c1 d + c2 r; xo = xin + d   (xin = x, the gathered vector)
@@ -100,19 +143,33 @@ __device__ void pass_any(const CoarseMat& M, const T* x, int kind, const T* b, c
 #undef FSI_P
 }
 
-template <class T>
+template <class T, bool GRID>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_vcycle(const CoarsePlan* __restrict__ plan, const T* b0,
-                                                                  T* x0) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int nblk = (int)cluster.num_blocks();
-  const int rank = (int)cluster.block_rank();
+                                                                  T* x0, unsigned* bar, int* err) {
+  __shared__ int s_ok;
+  int nblk, rank;
+  if constexpr (GRID) {
+    nblk = (int)gridDim.x;
+    rank = (int)blockIdx.x;
+  } else {
+    cg::cluster_group cluster = cg::this_cluster();
+    nblk = (int)cluster.num_blocks();
+    rank = (int)cluster.block_rank();
+  }
+  auto sync = [&]() -> bool {
+    if constexpr (GRID) {
+      return grid_barrier(bar, (unsigned)nblk, err, &s_ok);
+    } else {
+      cg::this_cluster().sync();
+      return true;
+    }
+  };
   const int lane32 = threadIdx.x & 31;
   const int gwarp = rank * (kCoarseThreads / 32) + (threadIdx.x >> 5);
   const int nwarps = nblk * (kCoarseThreads / 32);
   const int gtid = rank * kCoarseThreads + threadIdx.x;
   const int nth = nblk * kCoarseThreads;
   const int L = plan->nlev;
-  const int deg = plan->deg;
   // ------------------------------------------------ descend
   for (int li = 0; li + 1 < L; ++li) {
     const CoarseLevel& lv = plan->lev[li];
@@ -122,6 +179,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_vcycle(const CoarsePl
     T* d = static_cast<T*>(lv.d);
     const T* dinv = static_cast<const T*>(lv.dinv);
     const int n = lv.A.nbr * lv.A.br;
+    const int deg = lv.deg;
     for (int sw = 0; sw < plan->presmooth; ++sw) {
       const bool zero = sw == 0;
       const int nsp = zero ? deg - 1 : deg;
@@ -136,7 +194,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_vcycle(const CoarsePl
         }
         cur = first;
         oth = (first == x) ? xb : x;
-        cluster.sync();
+        if (!sync()) return;
       }
       for (int st = 0; st < nsp; ++st) {
         T c1, c2;
@@ -144,19 +202,19 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_vcycle(const CoarsePl
         else { const int r = zero ? st : st - 1; c1 = (T)lv.c1[r]; c2 = (T)lv.c2[r]; }
         pass_any<T>(lv.A, cur, kCheb, b, dinv, d, oth, c1, c2, T(0), T(0), gwarp, nwarps, lane32);
         T* t = cur; cur = oth; oth = t;
-        cluster.sync();
+        if (!sync()) return;
       }
       if (cur != x) {
         for (int i = gtid; i < n; i += nth) x[i] = ldv(cur + i);
-        cluster.sync();
+        if (!sync()) return;
       }
     }
     pass_any<T>(lv.A, x, kResid, b, nullptr, nullptr, static_cast<T*>(lv.r), T(0), T(0), T(0), T(0), gwarp, nwarps,
                 lane32);
-    cluster.sync();
+    if (!sync()) return;
     pass_any<T>(lv.R, static_cast<const T*>(lv.r), kAxpy, nullptr, nullptr, nullptr,
                 static_cast<T*>(plan->lev[li + 1].b), T(0), T(0), T(1), T(0), gwarp, nwarps, lane32);
-    cluster.sync();
+    if (!sync()) return;
   }
   // ------------------------------------------------ coarsest: x = Cinv b
   {
@@ -171,7 +229,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_vcycle(const CoarsePl
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
       if (lane32 == 0) x[row] = acc;
     }
-    cluster.sync();
+    if (!sync()) return;
   }
   // ------------------------------------------------ ascend
   for (int li = L - 2; li >= 0; --li) {
@@ -182,9 +240,10 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_vcycle(const CoarsePl
     T* d = static_cast<T*>(lv.d);
     const T* dinv = static_cast<const T*>(lv.dinv);
     const int n = lv.A.nbr * lv.A.br;
+    const int deg = lv.deg;
     pass_any<T>(lv.P, static_cast<const T*>(plan->lev[li + 1].x), kAxpy, nullptr, nullptr, nullptr, x, T(0), T(0),
                 T(1), T(1), gwarp, nwarps, lane32);
-    cluster.sync();
+    if (!sync()) return;
     for (int sw = 0; sw < plan->postsmooth; ++sw) {
       T* cur = x;
       T* oth = xb;
@@ -194,11 +253,11 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_vcycle(const CoarsePl
         else { c1 = (T)lv.c1[st - 1]; c2 = (T)lv.c2[st - 1]; }
         pass_any<T>(lv.A, cur, kCheb, b, dinv, d, oth, c1, c2, T(0), T(0), gwarp, nwarps, lane32);
         T* t = cur; cur = oth; oth = t;
-        cluster.sync();
+        if (!sync()) return;
       }
       if (cur != x) {
         for (int i = gtid; i < n; i += nth) x[i] = ldv(cur + i);
-        cluster.sync();
+        if (!sync()) return;
       }
     }
   }
@@ -231,21 +290,44 @@ bool shape_ok(const Bsr& A) {
 }
 
 template <class T>
-void launch(const CoarsePlan* dplan, int cluster, const T* b0, T* x0, cudaStream_t s) {
+void launch(const CoarseRun<T>& run, const T* b0, T* x0, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cluster, 1, 1);
+  cfg.gridDim = dim3(run.ctas, 1, 1);
   cfg.blockDim = dim3(kCoarseThreads, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  if (run.mode == COARSE_GRID) {
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+  } else {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = run.ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+  }
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FSI_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_vcycle<T>, dplan, b0, x0));
+  if (run.mode == COARSE_GRID)
+    FSI_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_vcycle<T, true>, run.plan.p, b0, x0, run.bar.p, run.err.p));
+  else
+    FSI_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_vcycle<T, false>, run.plan.p, b0, x0, (unsigned*)nullptr,
+                                (int*)nullptr));
   ++g_kernel_launches;
+}
+
+// Cooperative grid: half of the CTAs the whole GPU holds at once (0 when none fit).
+template <class T>
+int choose_grid() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  FSI_CUDA(cudaGetDevice(&dev));
+  FSI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  FSI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  FSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_vcycle<T, true>, kCoarseThreads, 0));
+  cached = coop ? (per_sm * nsm) / 2 : 0;
+  return cached;
 }
 
 template <class T>
@@ -254,7 +336,7 @@ int choose_cluster() {
   if (cached >= 0) return cached;
   int best = 0;
   for (int c : {16, 8}) {
-    if (c == 16 && cudaFuncSetAttribute(k_coarse_vcycle<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+    if (c == 16 && cudaFuncSetAttribute(k_coarse_vcycle<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                        cudaSuccess) {
       cudaGetLastError();
       continue;
@@ -270,7 +352,7 @@ int choose_cluster() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_vcycle<T>, &cfg) == cudaSuccess && nclusters > 0) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_vcycle<T, false>, &cfg) == cudaSuccess && nclusters > 0) {
       best = c;
       break;
     }
@@ -288,15 +370,14 @@ void coarse_plan_build(Hierarchy& H, int first, CoarseRun<T>& run, cudaStream_t 
   const int L = (int)H.levels.size();
   require(first >= 0 && first < L, "coarse plan: bad first level");
   require(L - first <= kCoarseMaxLevels, "coarse plan: too many levels");
-  run.cluster = choose_cluster<T>();
-  if (run.cluster == 0) return;          // no cluster launch possible: caller keeps the per-level path
-  const int threads = run.cluster * kCoarseThreads;
+  run.mode = H.coarse_mode;
+  run.ctas = run.mode == COARSE_GRID ? choose_grid<T>() : choose_cluster<T>();
+  if (run.ctas == 0) return;             // no such launch possible: caller keeps the per-level path
+  const int threads = run.ctas * kCoarseThreads;
   CoarsePlan p = {};
   p.nlev = L - first;
-  p.deg = H.prm.degree(first);
   p.presmooth = H.prm.presmooth;
   p.postsmooth = H.prm.postsmooth;
-  require(p.deg - 1 <= kCoarseMaxDeg, "coarse plan: Chebyshev degree too high");
   for (int li = 0; li < p.nlev; ++li) {
     AmgLevel& Lv = H.levels[first + li];
     CoarseLevel& c = p.lev[li];
@@ -317,7 +398,9 @@ void coarse_plan_build(Hierarchy& H, int first, CoarseRun<T>& run, cudaStream_t 
     const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha), sigma = theta / delta;
     double rho = 1.0 / sigma;
     c.inv_theta = 1.0 / theta;
-    for (int k = 0; k + 1 < p.deg; ++k) {
+    c.deg = H.prm.degree(first + li);
+    require(c.deg >= 1 && c.deg - 1 <= kCoarseMaxDeg, "coarse plan: Chebyshev degree out of range");
+    for (int k = 0; k + 1 < c.deg; ++k) {
       const double rn = 1.0 / (2.0 * sigma - rho);
       c.c1[k] = rn * rho;
       c.c2[k] = 2.0 * rn / delta;
@@ -328,13 +411,40 @@ void coarse_plan_build(Hierarchy& H, int first, CoarseRun<T>& run, cudaStream_t 
   p.ncoarse = H.ncoarse;
   run.plan.alloc(1);
   FSI_CUDA(cudaMemcpyAsync(run.plan.p, &p, sizeof(CoarsePlan), cudaMemcpyHostToDevice, s));
+  if (run.mode == COARSE_GRID) {
+    run.bar.alloc(2);
+    run.err.alloc(1);
+    FSI_CUDA(cudaMemsetAsync(run.bar.p, 0, 2 * sizeof(unsigned), s));
+    FSI_CUDA(cudaMemsetAsync(run.err.p, 0, sizeof(int), s));
+  }
   FSI_CUDA(cudaStreamSynchronize(s));
   run.first = first;
 }
 
+namespace {
+template <class T>
+bool run_failed(CoarseRun<T>& run, cudaStream_t s) {
+  if (run.mode != COARSE_GRID || !run.err.p) return false;
+  int h = 0;
+  FSI_CUDA(cudaMemcpyAsync(&h, run.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  if (h == 0) return false;
+  FSI_CUDA(cudaMemsetAsync(run.bar.p, 0, 2 * sizeof(unsigned), s));
+  FSI_CUDA(cudaMemsetAsync(run.err.p, 0, sizeof(int), s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  return true;
+}
+}  // namespace
+
+bool coarse_failed(Hierarchy& H, cudaStream_t s) {
+  const bool a = run_failed(H.crun64, s);
+  const bool b = run_failed(H.crun32, s);
+  return a || b;
+}
+
 template <class T>
 void coarse_vcycle(const CoarseRun<T>& run, const T* b, T* x, cudaStream_t s) {
-  launch<T>(run.plan.p, run.cluster, b, x, s);
+  launch<T>(run, b, x, s);
 }
 
 template void coarse_plan_build<double>(Hierarchy&, int, CoarseRun<double>&, cudaStream_t);

@@ -84,6 +84,10 @@ void validate_params(const fsi::SolverParams& s) {
   require(s.learned_accept > 0.0 && s.learned_accept <= 1.0, "learned_accept must be in (0, 1]");
   require(s.spmv_prefetch >= 0 && s.spmv_prefetch <= 2, "spmv_prefetch must be 0, 1 or 2");
   require(s.cluster_max_bytes >= 0.0 && std::isfinite(s.cluster_max_bytes), "cluster_max_bytes must be >= 0");
+  require(!((s.flags & FSI_CLUSTER_COARSE) && (s.flags & FSI_GRID_COARSE)),
+          "FSI_CLUSTER_COARSE and FSI_GRID_COARSE exclude each other");
+  require((s.flags & ~(FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED |
+                       FSI_NO_PDL | FSI_GRID_COARSE)) == 0, "unknown flag bits");
 }
 
 void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -392,12 +396,12 @@ int fsi_set_learned_accept(fsi_ctx* ctx, double tau) {
 int fsi_set_flags(fsi_ctx* ctx, int flags) {
   if (!ctx) return FSI_EINVAL;
   return guarded(ctx, [&] {
-    constexpr int fixed = FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_NO_PDL;
+    constexpr int fixed = FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_NO_PDL | FSI_GRID_COARSE;
     constexpr int known = FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED |
-                          FSI_NO_PDL;
+                          FSI_NO_PDL | FSI_GRID_COARSE;
     fsi::require((flags & ~known) == 0, "unknown flag bits");
     fsi::require((flags & fixed) == (ctx->C.prm.flags & fixed),
-                 "FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE and FSI_NO_PDL are fixed at fsi_setup");
+                 "FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_GRID_COARSE and FSI_NO_PDL are fixed at fsi_setup");
     ctx->C.prm.flags = flags;
   });
 }

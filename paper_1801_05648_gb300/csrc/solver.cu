@@ -329,7 +329,10 @@ void precond_build(Context& C, int precision) {
     DBuf<double> Bst;
     if (!rigid) upload(Bst, translations(Shat.nbr, d), s);
     const int ks = rigid ? (d == 2 ? 3 : 6) : d;
-    for (auto& H : C.H) H.use_cluster = (C.prm.flags & CLUSTER_COARSE) != 0;
+    for (auto& H : C.H)
+      H.coarse_mode = (C.prm.flags & CLUSTER_COARSE) ? COARSE_CLUSTER
+                      : (C.prm.flags & GRID_COARSE)  ? COARSE_GRID
+                                                     : COARSE_PER_LEVEL;
     amg_setup(C.H[0], std::move(C.Mblk), Bm.p, d, C.prm.amg, s);
     amg_setup(C.H[1], std::move(Shat), rigid ? C.solid_B.p : Bst.p, ks, C.prm.amg, s);
     amg_setup(C.H[2], std::move(C.Aff), Bf.p, d, C.prm.amg, s);
@@ -594,6 +597,15 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
   FSI_CUDA(cudaStreamSynchronize(C.s));
   if (C.prm.flags & LEARNED)
     FSI_CUDA(cudaMemcpy(&C.last_accepted, C.learned.counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (C.prm.flags & GRID_COARSE) {
+    bool failed = false;
+    for (auto& H : C.H) failed = coarse_failed(H, C.s) || failed;
+    if (failed) {
+      C.last_status = ECUDA_;
+      C.solve_s = secs(t0, clk::now());
+      throw Error(ECUDA_, "a grid barrier of the coarse-level kernel timed out; the result is not valid");
+    }
+  }
   C.last_iters = total;
   C.last_true_relres = relres;
   if (nonfinite) status = ENONFINITE_;

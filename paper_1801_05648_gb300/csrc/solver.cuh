@@ -26,7 +26,8 @@ struct SolverParams {
   double cluster_max_bytes = 6.0e6;
 };
 
-enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8, LEARNED = 16, NO_PDL = 32 };
+enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8, LEARNED = 16, NO_PDL = 32,
+             GRID_COARSE = 64 };
 
 template <class T>
 struct PrecWork {

@@ -285,15 +285,18 @@ def test_full_size_solves(name, torch_cuda):
     assert e32 <= max(10.0 * e64, 1e-6), (e32, e64)
 
 
-@pytest.mark.parametrize("name", ["2d_16x16", "3d_8x4x4"])
-def test_cluster_coarse_vcycle_matches_per_level_path(name, torch_cuda):
-    """FSI_CLUSTER_COARSE runs the coarse levels of each V-cycle in one thread-block
-    cluster launch; the block inverses and the solve must match the per-level path."""
+@pytest.mark.parametrize("name", ["2d_16x16", "2d_64x32", "3d_8x4x4"])
+@pytest.mark.parametrize("mode", ["cluster", "grid"])
+def test_coarse_vcycle_in_one_launch_matches_per_level_path(name, mode, torch_cuda):
+    """FSI_CLUSTER_COARSE / FSI_GRID_COARSE run the coarse levels of each V-cycle in one
+    launch (a thread-block cluster, or a cooperative grid with a software barrier); the
+    block inverses and the solve must match the oracle like the per-level path."""
     torch = torch_cuda
     import paper_1801_05648_gb300 as P
     s, o, ref, g, mr = case(name, torch)
+    flag = P.FSI_CLUSTER_COARSE if mode == "cluster" else P.FSI_GRID_COARSE
     for prec, tol in (("fp64", 1e-11), ("fp32", 1e-4)):
-        gc = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr, flags=P.FSI_CLUSTER_COARSE))
+        gc = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr, flags=flag))
         gc.precond_build(prec)
         for blk, sl, f in _block_slices(s, o):
             r = np.random.default_rng(3).standard_normal(sl.stop - sl.start)
