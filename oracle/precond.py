@@ -9,9 +9,11 @@ Alg. 2 (C_sm dropped, Schur perturbation ignored, Sec. 4.1):
     x_m = M^-1 r_m;  x_s = S^-1 r_s;  x_f = F^-1 (r_f - C_fm x_m - C_fs x_s);
     x_s -= S^-1 C_sf x_f;  x_m -= M^-1 C_ms x_s.
 Alg. 3 (Sec. 4.3) with S = [[A_vv, A_vu], [A_uv, A_uu]], A_uu the solid mass
-matrix and A_uv = -dt*theta*A_uu on its free rows:
-    x_v = S_hat^-1 (r_v - A_vu A_uu^-1 r_u),  S_hat = A_vv + dt*theta*A_vu;
-    x_u = A_uu^-1 (r_u - A_uv x_v).
+matrix and A_uv = -dt*theta*A_uu on its free rows (no entries on fixed rows):
+    y = A_uu^-1 r_u;  x_v = S_hat^-1 (r_v - A_vu y),  S_hat = A_vv + dt*theta*A_vu;
+    x_u = A_uu^-1 (r_u - A_uv x_v) = y + dt*theta x_v on the free rows, y on fixed rows
+(the second solve of Alg. 3 written out with A_uu^-1 A_uu = I: one mass solve
+serves both steps).
 Fluid (Sec. 4.4, "the same Schur-complement approach as for the solid"; the
 reading taken here is the SIMPLE-type pressure Schur approximation):
     y_v = A_ff^-1 r_v;  x_p = S_p^-1 (r_p - B_pv y_v);  x_v = A_ff^-1 (r_v - B_vp x_p),
@@ -145,6 +147,8 @@ class BlockLDU:
             translations(self.S_hat.shape[0] // d, d)
         self.Shat_inv = _AMGInverse(self.S_hat, d, ns, ap, params.vcycles_solid)
         self.Ms_inv = _ChebInverse(B.A_uu, params.mass_degree, params.mass_ratio, ap.cheb_upper, ap.power_iters)
+        # dt*theta on the s_u rows A_uv couples (the free rows), 0 on the fixed ones
+        self.uv_weight = np.where(np.diff(sp.csr_matrix(B.A_uv).indptr) > 0, params.dt_theta, 0.0)
         self.Aff_inv = _AMGInverse(B.A_ff, d, translations(B.A_ff.shape[0] // d, d), ap, params.vcycles_fluid)
         self.Sp_inv = _AMGInverse(self.S_p, 1, np.ones((self.S_p.shape[0], 1)), ap, params.vcycles_pressure)
 
@@ -156,8 +160,9 @@ class BlockLDU:
         B = self.B
         nv = B.A_vv.shape[0]
         r_v, r_u = r_s[:nv], r_s[nv:]
-        x_v = self.Shat_inv(r_v - B.A_vu @ self.Ms_inv(r_u))
-        x_u = self.Ms_inv(r_u - B.A_uv @ x_v)
+        y = self.Ms_inv(r_u)
+        x_v = self.Shat_inv(r_v - B.A_vu @ y)
+        x_u = y + self.uv_weight * x_v
         return np.concatenate([x_v, x_u])
 
     def F_inv(self, r_f):

@@ -5,8 +5,9 @@
 // P^-1 r (Alg. 2, Sec. 4.1):
 //   x_m = M^-1 r_m;  x_s = S^-1 r_s;  x_f = F^-1 (r_f - C_fm x_m - C_fs x_s);
 //   x_s -= S^-1 C_sf x_f;  x_m -= M^-1 C_ms x_s.
-// S^-1 (Alg. 3, Sec. 4.3): x_v = S_hat^-1 (r_v - A_vu A_uu^-1 r_u), S_hat = A_vv + dt*theta*A_vu;
-//   x_u = A_uu^-1 (r_u - A_uv x_v).
+// S^-1 (Alg. 3, Sec. 4.3): y = A_uu^-1 r_u;  x_v = S_hat^-1 (r_v - A_vu y), S_hat = A_vv + dt*theta*A_vu;
+//   x_u = A_uu^-1 (r_u - A_uv x_v) = y + dt*theta x_v on the free s_u rows (A_uv = -dt*theta A_uu
+//   there; fixed rows keep y), so one mass solve serves both steps of Alg. 3.
 // F^-1 (Sec. 4.4, pressure Schur complement S_p = C_pp - B_pv diag(A_ff)^-1 B_vp):
 //   y = A_ff^-1 r_v;  x_p = S_p^-1 (r_p - B_pv y);  x_v = A_ff^-1 (r_v - B_vp x_p).
 // Inverses: smoothed-aggregation V-cycles (M, S_hat, A_ff, S_p) and a Chebyshev
@@ -210,6 +211,18 @@ template <class T>
 void mesh_solve(Context& C, const T* r, T* x, cudaStream_t st) { amg_solve<T>(C, 0, C.prm.vc_mesh, r, x, st); }
 
 // Alg. 3: solid sub-solve on (r_v, r_u) -> (x_v, x_u)
+template <class T> const T* uv_weight(const Context& C);
+template <> const double* uv_weight<double>(const Context& C) { return C.uv_w64.p; }
+template <> const float* uv_weight<float>(const Context& C) { return C.uv_w32.p; }
+
+// w[i] = c where scalar row i of A (block rows of br) has entries, else 0
+__global__ void k_row_weight(int nbr, int br, const int* __restrict__ rowptr, double c, double* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr * br) return;
+  const int r = i / br;
+  w[i] = rowptr[r + 1] > rowptr[r] ? c : 0.0;
+}
+
 template <class T>
 void solid_solve(Context& C, const T* r, T* x, cudaStream_t st) {
   PrecWork<T>& W = pwork<T>(C);
@@ -218,11 +231,11 @@ void solid_solve(Context& C, const T* r, T* x, cudaStream_t st) {
   const T* r_u = r + nsv;
   T* x_v = x;
   T* x_u = x + nsv;
-  cheb_apply<T>(C.mass, r_u, W.s3_y.p, st);                                   // y = A_uu^-1 r_u
-  spmv2_resid<T>(C.A_vu, W.s3_y.p, nullptr, nullptr, r_v, W.s3_t.p, st);      // t = r_v - A_vu y
+  const int64_t nsu = C.off[3] - C.off[2];
+  cheb_apply<T>(C.mass, r_u, x_u, st);                                        // y = A_uu^-1 r_u (in x_u)
+  spmv2_resid<T>(C.A_vu, x_u, nullptr, nullptr, r_v, W.s3_t.p, st);           // t = r_v - A_vu y
   amg_solve<T>(C, 1, C.prm.vc_solid, W.s3_t.p, x_v, st);                      // x_v = S_hat^-1 t
-  spmv2_resid<T>(C.A_uv, x_v, nullptr, nullptr, r_u, W.s3_t.p, st);           // t = r_u - A_uv x_v
-  cheb_apply<T>(C.mass, W.s3_t.p, x_u, st);                                   // x_u = A_uu^-1 t
+  vfma<T>(nsu, uv_weight<T>(C), x_v, x_u, st);                                // x_u = y + dt*theta x_v
 }
 
 // fluid sub-solve on (r_v, r_p) -> (x_v, x_p)
@@ -339,6 +352,15 @@ void precond_build(Context& C, int precision) {
     amg_setup(C.H[3], std::move(Sp), Bp.p, 1, C.prm.amg, s);
     cheb_setup(C.mass, std::move(C.Auu), C.prm.mass_degree, C.prm.mass_ratio, C.prm.amg.cheb_upper,
                C.prm.amg.power_iters, s);
+    {
+      const int64_t nsu = C.off[3] - C.off[2];
+      C.uv_w64.alloc(nsu > 0 ? nsu : 1);
+      if (nsu > 0) {
+        k_row_weight<<<div_up(nsu, 256), 256, 0, s>>>(C.A_uv.nbr, C.A_uv.br, C.A_uv.rowptr.p, C.prm.dt_theta,
+                                                       C.uv_w64.p);
+        FSI_CHECK_LAUNCH();
+      }
+    }
     C.Avv = Bsr();
     C.Cpp = Bsr();
     alloc_pw(C.pw64, C.n);
@@ -347,6 +369,11 @@ void precond_build(Context& C, int precision) {
   if (precision == 1 && !C.pw32.ready) {
     for (auto& H : C.H) amg_make_fp32(H, s);
     cheb_make_fp32(C.mass, s);
+    {
+      const int64_t nsu = C.off[3] - C.off[2];
+      C.uv_w32.alloc(nsu > 0 ? nsu : 1);
+      if (nsu > 0) cast<double, float>(nsu, C.uv_w64.p, C.uv_w32.p, s);
+    }
     for (Bsr* B : {&C.C_ms, &C.A_vu, &C.A_uv, &C.C_sv_f, &C.C_sv_p, &C.C_fv_ms, &C.C_p_ms, &C.B_vp, &C.B_pv})
       bsr_make_fp32(*B, s);
     alloc_pw(C.pw32, C.n);
@@ -425,14 +452,16 @@ double operator_bytes(const Context& C) {
 
 double precond_bytes(const Context& C, int vb) {
   const SolverParams& p = C.prm;
-  // Alg. 2: two mesh solves, two solid solves (each with two mass solves), one
-  // fluid solve (two A_ff solves and one S_p solve), and the coupling products
+  // Alg. 2: two mesh solves, two solid solves (each with one mass solve and the
+  // x_u update), one fluid solve (two A_ff solves and one S_p solve), and the
+  // coupling products
   double b = 0;
   b += 2.0 * p.vc_mesh * C.H[0].vcycle_bytes(vb) + 2.0 * p.vc_solid * C.H[1].vcycle_bytes(vb) +
        2.0 * p.vc_fluid * C.H[2].vcycle_bytes(vb) + 1.0 * p.vc_pressure * C.H[3].vcycle_bytes(vb);
-  b += 4.0 * C.mass.degree * C.mass.A.spmv_bytes(vb);
+  b += 2.0 * C.mass.degree * C.mass.A.spmv_bytes(vb);
+  b += 2.0 * 4.0 * vb * (double)(C.off[3] - C.off[2]);
   for (const Bsr* B : {&C.C_ms, &C.C_sv_f, &C.C_sv_p, &C.C_fv_ms, &C.C_p_ms}) b += B->spmv_bytes(vb);
-  b += 2.0 * (C.A_vu.spmv_bytes(vb) + C.A_uv.spmv_bytes(vb)) + C.B_vp.spmv_bytes(vb) + C.B_pv.spmv_bytes(vb);
+  b += 2.0 * C.A_vu.spmv_bytes(vb) + C.B_vp.spmv_bytes(vb) + C.B_pv.spmv_bytes(vb);
   return b;
 }
 

@@ -52,6 +52,8 @@ struct Context {
   // preconditioner blocks
   Bsr C_ms;                   // m rows x (s_v, s_u) cols
   Bsr A_vu, A_uv;             // solid couplings
+  DBuf<double> uv_w64;        // dt*theta on the free s_u rows (A_uv = -dt*theta A_uu there), 0 on fixed rows
+  DBuf<float> uv_w32;
   Bsr C_sv_f, C_sv_p;         // s rows x f_v cols, s rows x p cols
   Bsr C_fv_ms, C_p_ms;        // f_v rows x (m, s) cols, p rows x (m, s) cols
   Bsr B_vp, B_pv;             // fluid velocity-pressure couplings

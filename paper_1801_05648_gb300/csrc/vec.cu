@@ -36,6 +36,13 @@ __global__ void k_vmul(int64_t n, const T* __restrict__ x, const T* __restrict__
     y[i] = x[i] * w[i];
 }
 
+template <class T>
+__global__ void k_vfma(int64_t n, const T* __restrict__ w, const T* __restrict__ x, T* __restrict__ y) {
+  dep_wait();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += w[i] * x[i];
+}
+
 template <class Ti, class To>
 __global__ void k_cast(int64_t n, const Ti* __restrict__ x, To* __restrict__ y) {
   dep_wait();
@@ -168,6 +175,11 @@ void vmul(int64_t n, const T* x, const T* w, T* y, cudaStream_t s) {
   if (n <= 0) return;
   launch_k(k_vmul<T>, grid_for(n), kThreads, 0, s, n, x, w, y);
 }
+template <class T>
+void vfma(int64_t n, const T* w, const T* x, T* y, cudaStream_t s) {
+  if (n <= 0) return;
+  launch_k(k_vfma<T>, grid_for(n), kThreads, 0, s, n, w, x, y);
+}
 template <class Ti, class To>
 void cast(int64_t n, const Ti* x, To* y, cudaStream_t s) {
   if (n <= 0) return;
@@ -208,6 +220,8 @@ template void axpbyz<double>(int64_t, double, const double*, double, const doubl
 template void axpbyz<float>(int64_t, float, const float*, float, const float*, float*, cudaStream_t);
 template void vmul<double>(int64_t, const double*, const double*, double*, cudaStream_t);
 template void vmul<float>(int64_t, const float*, const float*, float*, cudaStream_t);
+template void vfma<double>(int64_t, const double*, const double*, double*, cudaStream_t);
+template void vfma<float>(int64_t, const float*, const float*, float*, cudaStream_t);
 template void cast<double, float>(int64_t, const double*, float*, cudaStream_t);
 template void cast<float, double>(int64_t, const float*, double*, cudaStream_t);
 template void dot_dev<double>(int64_t, const double*, const double*, double*, double*, cudaStream_t);

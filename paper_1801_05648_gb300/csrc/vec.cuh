@@ -16,6 +16,8 @@ template <class T> void axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_
 template <class T> void axpbyz(int64_t n, T a, const T* x, T b, const T* y, T* z, cudaStream_t s);
 // y = x * w (elementwise)
 template <class T> void vmul(int64_t n, const T* x, const T* w, T* y, cudaStream_t s);
+// y += w * x (elementwise)
+template <class T> void vfma(int64_t n, const T* w, const T* x, T* y, cudaStream_t s);
 // y = (To) x
 template <class Ti, class To> void cast(int64_t n, const Ti* x, To* y, cudaStream_t s);
 // out[0] = sum_i x_i y_i (FP64 accumulation), device result; partials has kRedBlocks doubles

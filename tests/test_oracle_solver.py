@@ -135,6 +135,23 @@ def test_solid_schur_alg3_with_exact_inverses_is_exact():
     assert np.linalg.norm(x - x_direct) <= 1e-6 * np.linalg.norm(x_direct)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_solid_velocity_coupling_is_minus_dt_theta_mass(dim):
+    """Alg. 3 applies one mass solve for both of its steps, which rests on
+    A_uv = -dt*theta*A_uu on every free s_u row (the displacement equation
+    (u - u_old) - dt*theta*v = 0 tested with the same Q2 basis) and on A_uv
+    having no entries on fixed rows."""
+    s = tiny(dim)
+    pre = oracle.BlockLDU(s.scipy(), s.offsets, dim)
+    B = pre.B
+    c = pre.params.dt_theta
+    fixed_u = s.fixed[B.su]
+    D = (B.A_uv + c * B.A_uu).tocsr()
+    assert abs(D[~fixed_u]).max() <= 1e-12 * abs(B.A_uu[~fixed_u]).max()
+    assert B.A_uv.tocsr()[fixed_u].nnz == 0
+    assert np.array_equal(pre.uv_weight, np.where(fixed_u, 0.0, c))
+
+
 def test_fluid_schur_elimination_with_exact_schur_is_exact():
     s = tiny(2)
     pre = oracle.BlockLDU(s.scipy(), s.offsets, 2)
