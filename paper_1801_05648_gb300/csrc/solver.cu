@@ -223,8 +223,10 @@ __global__ void k_row_weight(int nbr, int br, const int* __restrict__ rowptr, do
   w[i] = rowptr[r + 1] > rowptr[r] ? c : 0.0;
 }
 
+// r_u_zero: the caller's r_u is zero by structure; y = A_uu^-1 0 = 0 and t = r_v
+// exactly, so the mass solve and the A_vu product are skipped (same result).
 template <class T>
-void solid_solve(Context& C, const T* r, T* x, cudaStream_t st) {
+void solid_solve(Context& C, const T* r, T* x, cudaStream_t st, bool r_u_zero = false) {
   PrecWork<T>& W = pwork<T>(C);
   const int64_t nsv = C.off[2] - C.off[1];
   const T* r_v = r;
@@ -232,6 +234,11 @@ void solid_solve(Context& C, const T* r, T* x, cudaStream_t st) {
   T* x_v = x;
   T* x_u = x + nsv;
   const int64_t nsu = C.off[3] - C.off[2];
+  if (r_u_zero) {
+    amg_solve<T>(C, 1, C.prm.vc_solid, r_v, x_v, st);                          // x_v = S_hat^-1 r_v
+    vmul<T>(nsu, x_v, uv_weight<T>(C), x_u, st);                                // x_u = dt*theta x_v
+    return;
+  }
   cheb_apply<T>(C.mass, r_u, x_u, st);                                        // y = A_uu^-1 r_u (in x_u)
   spmv2_resid<T>(C.A_vu, x_u, nullptr, nullptr, r_v, W.s3_t.p, st);           // t = r_v - A_vu y
   amg_solve<T>(C, 1, C.prm.vc_solid, W.s3_t.p, x_v, st);                      // x_v = S_hat^-1 t
@@ -304,6 +311,21 @@ void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, con
   extract_bsr(A, o[2], nsu, d, o[2], nsu, d, C.Auu, s);
   extract_bsr(A, o[1], ns, d, o[3], nfv, d, C.C_sv_f, s);
   extract_bsr(A, o[1], ns, d, o[4], nP, 1, C.C_sv_p, s);
+  {
+    // do the s_u rows of C_sf hold entries?  (The displacement equation couples
+    // no fluid unknown, so normally not: then the S^-1 of step 4 of Alg. 2 sees
+    // r_u = 0 and skips its mass solve, see solid_solve.)
+    auto tail_empty = [&](const Bsr& B) {
+      int rp[2] = {0, 0};
+      const int b0 = nsv;   // first s_u block row
+      if (B.nbr == 0) return true;
+      FSI_CUDA(cudaMemcpyAsync(&rp[0], B.rowptr.p + b0, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FSI_CUDA(cudaMemcpyAsync(&rp[1], B.rowptr.p + B.nbr, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FSI_CUDA(cudaStreamSynchronize(s));
+      return rp[0] == rp[1];
+    };
+    C.csf_u_zero = tail_empty(C.C_sv_f) && tail_empty(C.C_sv_p);
+  }
   extract_bsr(A, o[3], nfv, d, o[0], nms, d, C.C_fv_ms, s);
   extract_bsr(A, o[4], nP, 1, o[0], nms, d, C.C_p_ms, s);
   extract_bsr(A, o[3], nfv, d, o[3], nfv, d, C.Aff, s);
@@ -409,7 +431,7 @@ void precond_apply(Context& C, const T* r, T* z) {
   fluid_solve<T>(C, W.a2_t.p, z_f, C.s);
   // 4: x_s -= S^-1 C_sf x_f
   spmv2_axpby<T>(C.C_sv_f, z_f, &C.C_sv_p, z_f + nfv, T(1), T(0), W.a2_t.p, C.s);
-  solid_solve<T>(C, W.a2_t.p, W.a2_u.p, C.s);
+  solid_solve<T>(C, W.a2_t.p, W.a2_u.p, C.s, C.csf_u_zero);
   axpby<T>(ns, T(-1), W.a2_u.p, T(1), z_s, C.s);
   // 5: x_m -= M^-1 C_ms x_s
   spmv_axpby<T>(C.C_ms, z_s, T(1), T(0), W.a2_t.p, C.s);
@@ -452,16 +474,17 @@ double operator_bytes(const Context& C) {
 
 double precond_bytes(const Context& C, int vb) {
   const SolverParams& p = C.prm;
-  // Alg. 2: two mesh solves, two solid solves (each with one mass solve and the
-  // x_u update), one fluid solve (two A_ff solves and one S_p solve), and the
-  // coupling products
+  // Alg. 2: two mesh solves, two solid solves (one mass solve each, none in the
+  // second when its r_u is structurally zero, and the x_u update), one fluid solve
+  // (two A_ff solves and one S_p solve), and the coupling products
   double b = 0;
   b += 2.0 * p.vc_mesh * C.H[0].vcycle_bytes(vb) + 2.0 * p.vc_solid * C.H[1].vcycle_bytes(vb) +
        2.0 * p.vc_fluid * C.H[2].vcycle_bytes(vb) + 1.0 * p.vc_pressure * C.H[3].vcycle_bytes(vb);
-  b += 2.0 * C.mass.degree * C.mass.A.spmv_bytes(vb);
+  const double mass_solves = C.csf_u_zero ? 1.0 : 2.0;   // step 4's S^-1 skips its mass solve when r_u = 0
+  b += mass_solves * C.mass.degree * C.mass.A.spmv_bytes(vb);
   b += 2.0 * 4.0 * vb * (double)(C.off[3] - C.off[2]);
   for (const Bsr* B : {&C.C_ms, &C.C_sv_f, &C.C_sv_p, &C.C_fv_ms, &C.C_p_ms}) b += B->spmv_bytes(vb);
-  b += 2.0 * C.A_vu.spmv_bytes(vb) + C.B_vp.spmv_bytes(vb) + C.B_pv.spmv_bytes(vb);
+  b += mass_solves * C.A_vu.spmv_bytes(vb) + C.B_vp.spmv_bytes(vb) + C.B_pv.spmv_bytes(vb);
   return b;
 }
 

@@ -55,6 +55,7 @@ struct Context {
   DBuf<double> uv_w64;        // dt*theta on the free s_u rows (A_uv = -dt*theta A_uu there), 0 on fixed rows
   DBuf<float> uv_w32;
   Bsr C_sv_f, C_sv_p;         // s rows x f_v cols, s rows x p cols
+  bool csf_u_zero = false;    // the s_u rows of C_sv_f and C_sv_p hold no entries
   Bsr C_fv_ms, C_p_ms;        // f_v rows x (m, s) cols, p rows x (m, s) cols
   Bsr B_vp, B_pv;             // fluid velocity-pressure couplings
   Bsr Mblk, Avv, Auu, Aff, Cpp;   // diagonal blocks, consumed by precond_build
