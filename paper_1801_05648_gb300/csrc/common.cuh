@@ -133,11 +133,22 @@ struct SpmvTuning {
   int unroll = 4;      // blocks each lane loads before multiplying: 4 or 8 (8 only for small blocks)
   int prefetch = 1;    // 0 none, 1 L2 bulk prefetch of each CTA's matrix slice, 2 also persistent CTAs
   int ctas_per_sm = 5; // persistent grid size per SM (prefetch 2)
+  int setup_depth = 0; // > 0 while matrices are being built: no reads before the dependency wait
 };
 inline SpmvTuning& spmv_tuning() {
   static SpmvTuning t;
   return t;
 }
+
+// Marks the set-up phase (context set-up, preconditioner build): an SpMV may then
+// be launched right after the kernel that writes its matrix, so it reads no matrix
+// memory before its dependency wait.
+struct SetupPhase {
+  SetupPhase() { ++spmv_tuning().setup_depth; }
+  ~SetupPhase() { --spmv_tuning().setup_depth; }
+  SetupPhase(const SetupPhase&) = delete;
+  SetupPhase& operator=(const SetupPhase&) = delete;
+};
 
 inline void set_tpr(Bsr& A) {
   A.tpr = lanes_for(A.nnzb, A.nbr, 2.0);

@@ -275,6 +275,7 @@ Context::~Context() {
 
 void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, const double* vals,
                    const double* solid_coords) {
+  SetupPhase setup_phase;
   auto t0 = clk::now();
   FSI_CUDA(cudaStreamCreateWithFlags(&C.s2, cudaStreamNonBlocking));
   FSI_CUDA(cudaEventCreateWithFlags(&C.ev_fork, cudaEventDisableTiming));
@@ -338,6 +339,7 @@ void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, con
 }
 
 void precond_build(Context& C, int precision) {
+  SetupPhase setup_phase;
   auto t0 = clk::now();
   auto& s = C.s;
   const int d = C.dim;

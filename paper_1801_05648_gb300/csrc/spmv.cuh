@@ -271,14 +271,17 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 // blockDim.x / tpr rows per pass, tpr lanes per row.  With prefetch, thread 0 first
 // asks L2 for the CTA's slice of the (constant) matrix arrays, before waiting for the
 // previous kernel (programmatic dependent launch), so the slice streams in while
-// that kernel drains and while the CTA works through its first rows.
+// that kernel drains and while the CTA works through its first rows.  Reading the
+// row pointers before the wait is only allowed once the matrices are built
+// (pre_wait != 0); during set-up the previous kernel may still be writing them.
 template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4>
-__global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per_cta, int prefetch,
+__global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per_cta, int prefetch, int pre_wait,
     const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, G1 g1,
     const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, const T* __restrict__ x2,
     Epi epi) {
   const int r0 = blockIdx.x * rows_per_cta;
   const int r1 = r0 + rows_per_cta < nbr ? r0 + rows_per_cta : nbr;
+  if (!pre_wait) dep_wait();
   if (prefetch && threadIdx.x == 0 && r0 < r1) {
     const int a = rp1[r0], b = rp1[r1];
     prefetch_l2(v1 + (size_t)a * BR * BC1, sizeof(T) * (size_t)(b - a) * BR * BC1);
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
       prefetch_l2(ci2 + a2, sizeof(int) * (size_t)(b2 - a2));
     }
   }
-  dep_wait();
+  if (pre_wait) dep_wait();
   const int per_pass = blockDim.x / tpr;
   const int lane = threadIdx.x & (tpr - 1);
   for (int base = r0; base < r1; base += per_pass) {
