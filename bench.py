@@ -53,6 +53,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--spmv-prefetch", type=int, default=None, choices=[0, 1, 2],
+                    help="SpMV L2 prefetch mode (fsi_params.spmv_prefetch; default: the library's)")
     ap.add_argument("--kernel-only", choices=["spmv", "solve", "mlp"], default=None,
                     help="small programs for ncu captures: 'spmv' runs the outer SpMV 6 times; 'solve' runs "
                          "one solve of the bench workload inside cudaProfilerStart/Stop")
@@ -251,8 +253,9 @@ def bench_ours(args):
     for seed in replica_seeds(rank, args.states):
         cfg = fsigen.CONFIGS[args.workload].with_(state_seed=seed)
         s = fsigen.make_system(cfg)
+        knobs = {} if args.spmv_prefetch is None else {"spmv_prefetch": args.spmv_prefetch}
         g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=8.0 if s.dim == 2 else 20.0,
-                                                               flags=flags), stream=bs)
+                                                               flags=flags, **knobs), stream=bs)
         t0 = time.perf_counter()
         g.precond_build("fp64")
         build_s.append(time.perf_counter() - t0)
@@ -465,6 +468,7 @@ def bench_ours(args):
         "config": {"workload": args.workload, "description": WORKLOAD_DESC.get(args.workload, args.workload),
                    "form": "FP32-AMG" if args.precision == "fp32" else "FP64", "rtol": 1e-8, "restart": 100,
                    "states": S, "graphs": not args.no_graphs, "pdl": not args.no_pdl,
+                   "spmv_prefetch": int(P.default_params(systems[0].dim, **knobs).spmv_prefetch),
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2: each step solves another resident Jacobian (~0.6 GB of "
                          "matrices each)"},

@@ -17,6 +17,17 @@
 
 namespace fsi {
 
+// Products and fused multiply-adds with their rounding fixed.  Where a formula has
+// two products feeding one sum, the compiler may fuse either of them into an FMA,
+// and may choose differently in two kernels that inline the same code; the row
+// sums and epilogues below spell out which operations round, so the results do
+// not depend on those choices (another kernel computing the same rows in the same
+// order, e.g. a variant staged through shared memory, is bit-identical).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class T, int N>
 __device__ __forceinline__ void load_stream(const T* __restrict__ p, T* out) {
   if constexpr (sizeof(T) == 8 && N % 2 == 0) {
@@ -79,7 +90,7 @@ struct GatherScaled {
     load_gather<T, BC>(b + (size_t)c * BC, bv);
     load_gather<T, BC>(dinv + (size_t)c * BC, dv);
 #pragma unroll
-    for (int j = 0; j < BC; ++j) out[j] = dv[j] * bv[j] * s;
+    for (int j = 0; j < BC; ++j) out[j] = mul_rn(mul_rn(dv[j], bv[j]), s);
   }
 };
 
@@ -101,8 +112,8 @@ struct EpiAxpby {
   __device__ __forceinline__ void store(int row, const T* acc, const Pre& p) const {
 #pragma unroll
     for (int i = 0; i < BR; ++i) {
-      T v = alpha * acc[i];
-      if (beta != T(0)) v += beta * p.y[i];
+      T v = mul_rn(alpha, acc[i]);
+      if (beta != T(0)) v = fma_rn(beta, p.y[i], v);
       y[(size_t)row * BR + i] = v;
     }
   }
@@ -149,9 +160,9 @@ struct EpiCheb {
 #pragma unroll
     for (int i = 0; i < BR; ++i) {
       const size_t k = (size_t)row * BR + i;
-      const T r = p.dinv[i] * (p.b[i] - acc[i]);
-      T dn = c2 * r;
-      if (c1 != T(0)) dn += c1 * p.d[i];
+      const T r = mul_rn(p.dinv[i], p.b[i] - acc[i]);
+      T dn = mul_rn(c2, r);
+      if (c1 != T(0)) dn = fma_rn(c1, p.d[i], dn);
       d[k] = dn;
       xo[k] = p.x[i] + dn;
     }
@@ -179,9 +190,9 @@ struct EpiChebFromZero {
 #pragma unroll
     for (int i = 0; i < BR; ++i) {
       const size_t k = (size_t)row * BR + i;
-      const T d1 = p.dinv[i] * p.b[i] * inv_theta;
-      const T r = p.dinv[i] * (p.b[i] - acc[i]);
-      const T dn = c1 * d1 + c2 * r;
+      const T d1 = mul_rn(mul_rn(p.dinv[i], p.b[i]), inv_theta);
+      const T r = mul_rn(p.dinv[i], p.b[i] - acc[i]);
+      const T dn = fma_rn(c1, d1, mul_rn(c2, r));
       d[k] = dn;
       xo[k] = d1 + dn;
     }
@@ -201,7 +212,7 @@ struct EpiDinv {
   }
   __device__ __forceinline__ void store(int row, const T* acc, const Pre& p) const {
 #pragma unroll
-    for (int i = 0; i < BR; ++i) y[(size_t)row * BR + i] = p.dinv[i] * acc[i];
+    for (int i = 0; i < BR; ++i) y[(size_t)row * BR + i] = mul_rn(p.dinv[i], acc[i]);
   }
 };
 
@@ -250,7 +261,7 @@ __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const
 #pragma unroll
       for (int i = 0; i < BR; ++i)
 #pragma unroll
-        for (int j = 0; j < BC; ++j) acc[i] += blk[u][i * BC + j] * xv[u][j];
+        for (int j = 0; j < BC; ++j) acc[i] = fma_rn(blk[u][i * BC + j], xv[u][j], acc[i]);
   }
 }
 
