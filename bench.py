@@ -375,7 +375,7 @@ def bench_ours(args):
         mlp_s = e0.elapsed_time(e1) / reps / 1e3
         mlp_flops = nd.shape[0] * 2.0 * (53 * 64 + 64 * 64 + 64 * 5)
         fp32_peak = 152 * 128 * 2 * (clocks.get("sm_max_mhz") or 2070) * 1e6 / 1e12
-        mlp_traffic = kernel_traffic("mlp_apply_2d_mid.md", ["paper_1801_05648_gb300/csrc/learned.cu",
+        mlp_traffic = kernel_traffic(f"mlp_apply_{args.workload}.md", ["paper_1801_05648_gb300/csrc/learned.cu",
                                                              "paper_1801_05648_gb300/csrc/learned.cuh"])
         learned = {"form": "FP32-AMG + learned stage" if args.precision == "fp32" else "FP64 + learned stage",
                    "solve_s": ms_l / 1e3, "iters_median": statistics.median([x.iters for x in st_l]),
@@ -430,8 +430,9 @@ def bench_ours(args):
     achieved = op_bytes / spmv_s / 1e9
     peak, peak_kind = measured_peak()
     srcs = ["paper_1801_05648_gb300/csrc/spmv.cuh", "paper_1801_05648_gb300/csrc/spmv.cu"]
-    traffic = kernel_traffic("spmv_outer_fp64_2d_mid.md", srcs)
-    cheb_traffic = kernel_traffic("spmv_cheb_fp32_2d_mid.md", srcs)
+    # DRAM bytes per launch from the ncu summary of this workload (null without one)
+    traffic = kernel_traffic(f"spmv_outer_fp64_{args.workload}.md", srcs)
+    cheb_traffic = kernel_traffic(f"spmv_cheb_fp32_{args.workload}.md", srcs)
 
     # ---- CPU baseline: the oracle on this host's cores (bounded sample)
     cpu = None

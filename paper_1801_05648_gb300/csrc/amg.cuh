@@ -72,6 +72,7 @@ inline double& coarse_max_bytes() {
 
 struct CoarseMat {
   int nbr = 0, br = 1, bc = 1, tpr = 1;
+  int64_t nnzb = 0;
   const int* rp = nullptr;
   const int* ci = nullptr;
   const void* v = nullptr;

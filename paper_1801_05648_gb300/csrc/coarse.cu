@@ -39,15 +39,26 @@ __device__ __forceinline__ void row_prod(const CoarseMat& M, const T* x, int row
   const int kb = __ldg(M.rp + row), ke = __ldg(M.rp + row + 1);
   for (int k = kb + lane; k < ke; k += tpr) {
     const int c = __ldg(M.ci + k);
-    const T* blk = v + (size_t)k * (BR * BC);
     const T* xc = x + (size_t)c * BC;
-    T xv[BC];
+    T xv[BC], blk[BR * BC];
 #pragma unroll
     for (int j = 0; j < BC; ++j) xv[j] = ldv(xc + j);
+    if constexpr (planar_blocks<T, BR, BC>()) {
+      // planar FP32 3 x 3 blocks (see load_block in spmv.cuh)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        blk[t] = __ldg(v + 4 * (int64_t)k + t);
+        blk[4 + t] = __ldg(v + 4 * M.nnzb + 4 * (int64_t)k + t);
+      }
+      blk[8] = __ldg(v + 8 * M.nnzb + k);
+    } else {
+#pragma unroll
+      for (int t = 0; t < BR * BC; ++t) blk[t] = __ldg(v + (size_t)k * (BR * BC) + t);
+    }
 #pragma unroll
     for (int i = 0; i < BR; ++i)
 #pragma unroll
-      for (int j = 0; j < BC; ++j) acc[i] += __ldg(blk + i * BC + j) * xv[j];
+      for (int j = 0; j < BC; ++j) acc[i] += blk[i * BC + j] * xv[j];
   }
 }
 
@@ -277,7 +288,7 @@ template <> const float* vals_of<float>(const Bsr& A) { return A.v32.p; }
 template <class T>
 CoarseMat mat_of(const Bsr& A, int threads) {
   CoarseMat m;
-  m.nbr = A.nbr; m.br = A.br; m.bc = A.bc;
+  m.nbr = A.nbr; m.br = A.br; m.bc = A.bc; m.nnzb = A.nnzb;
   m.rp = A.rowptr.p; m.ci = A.colind.p; m.v = vals_of<T>(A);
   m.tpr = lanes_for_rows(A, threads);
   return m;

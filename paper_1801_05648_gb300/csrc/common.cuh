@@ -111,6 +111,11 @@ struct Bsr {
     return (double)nnzb * (br * bc * value_bytes + 4) + 4.0 * (nbr + 1) + (double)value_bytes * (cols() + rows());
   }
 };
+// FP32 copies of blocks with 9 values (3 x 3) are stored planar (values 0-3 of
+// every block, then 4-7, then 8; see load_block in spmv.cuh); all other copies are
+// row-major blocks.
+__host__ __device__ constexpr bool planar_fp32_shape(int br, int bc) { return br * bc == 9; }
+
 template <> inline const double* Bsr::vals<double>() const { return v64.p; }
 template <> inline const float* Bsr::vals<float>() const { return v32.p; }
 

@@ -346,6 +346,16 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restr
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
 }
+// FP32 copy of 3 x 3 blocks in the planar layout: value t of block k goes to
+// 4k + t (t < 4), 4 nnzb + 4k + t - 4 (t < 8) or 8 nnzb + k (t = 8).
+__global__ void k_to_f32_planar9(int64_t nnzb, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 9 * nnzb) return;
+  const int64_t k = i / 9;
+  const int t = (int)(i - 9 * k);
+  const int64_t o = t < 4 ? 4 * k + t : (t < 8 ? 4 * nnzb + 4 * k + (t - 4) : 8 * nnzb + k);
+  b[o] = (float)a[i];
+}
 __global__ void k_to_dense(int nbr, int br, int bc, int ncols, const int* __restrict__ rp, const int* __restrict__ ci,
                            const double* __restrict__ va, double* __restrict__ D) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -580,7 +590,10 @@ void bsr_make_fp32(Bsr& A, cudaStream_t s) {
   const int64_t n = A.nnzb * A.br * A.bc;
   A.v32.alloc(n > 0 ? n : 1);
   if (n > 0) {
-    k_to_f32<<<div_up(n, 256), 256, 0, s>>>(n, A.v64.p, A.v32.p);
+    if (planar_fp32_shape(A.br, A.bc))
+      k_to_f32_planar9<<<div_up(n, 256), 256, 0, s>>>(A.nnzb, A.v64.p, A.v32.p);
+    else
+      k_to_f32<<<div_up(n, 256), 256, 0, s>>>(n, A.v64.p, A.v32.p);
     FSI_CHECK_LAUNCH();
   }
 }

@@ -24,15 +24,16 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
     blocks = div_up(A1.nbr, rows_per_cta);
   }
   const T* v2 = nullptr; const int* rp2 = nullptr; const int* ci2 = nullptr;
-  if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; }
+  int64_t nnzb2 = 0;
+  if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; nnzb2 = A2->nnzb; }
   const int pre_wait = tu.setup_depth == 0 ? 1 : 0;
   const int pf = tu.prefetch > 0 ? 1 : 0;
   if (tu.unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
     launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf, pre_wait,
-             A1.rowptr.p, A1.colind.p, A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
+             A1.rowptr.p, A1.colind.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2, epi);
   else
     launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf, pre_wait,
-             A1.rowptr.p, A1.colind.p, A1.vals<T>(), g1, rp2, ci2, v2, x2, epi);
+             A1.rowptr.p, A1.colind.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2, epi);
 }
 
 template <class T, int BR, int BC1, int BC2, class Epi>

@@ -74,6 +74,33 @@ __device__ __forceinline__ void load_gather(const T* __restrict__ p, T* out) {
   }
 }
 
+// FP32 copies of 3 x 3-block matrices are stored planar (bsr_make_fp32): values
+// 0-3 of every block, then values 4-7 of every block, then value 8 of every block,
+// so that the lanes of a row group, which read consecutive blocks, issue two
+// contiguous 16-byte loads and one contiguous 4-byte load per block.  (A 36-byte
+// block read row-major takes nine 4-byte loads whose lanes are 36 bytes apart:
+// each touches about nine cache lines, and the L1 tag stage, not DRAM, becomes the
+// limit.)  Every other block shape and every FP64 copy is stored row-major.
+template <class T, int BR, int BC>
+__host__ __device__ constexpr bool planar_blocks() {
+  return sizeof(T) == 4 && planar_fp32_shape(BR, BC);
+}
+
+// Block k of a matrix with nnzb blocks (row-major block values in `out`), loaded
+// with the evict-first policy of the matrix streams.
+template <class T, int BR, int BC>
+__device__ __forceinline__ void load_block(const T* __restrict__ v, int64_t nnzb, int64_t k, T* out) {
+  if constexpr (planar_blocks<T, BR, BC>()) {
+    const float4 p = __ldcs(reinterpret_cast<const float4*>(v) + k);
+    const float4 q = __ldcs(reinterpret_cast<const float4*>(v + 4 * nnzb) + k);
+    out[0] = p.x; out[1] = p.y; out[2] = p.z; out[3] = p.w;
+    out[4] = q.x; out[5] = q.y; out[6] = q.z; out[7] = q.w;
+    out[8] = __ldcs(v + 8 * nnzb + k);
+  } else {
+    load_stream<T, BR * BC>(v + k * (BR * BC), out);
+  }
+}
+
 // ------------------------------------------------------------------ gathers
 // x[c] segment of the vector the matrix multiplies.
 template <class T, int BC>
@@ -229,8 +256,8 @@ __host__ __device__ constexpr int unroll_for() {
 // exist follows from the position alone), then the x segments, which need the
 // indices: one dependent memory round trip for the matrix data, one for x.
 template <class T, int BR, int BC, int UREQ, class G>
-__device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const T* __restrict__ v, const G& gx,
-                                               int kb, int ke, int lane, int tpr, T* acc) {
+__device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const T* __restrict__ v, int64_t nnzb,
+                                               const G& gx, int kb, int ke, int lane, int tpr, T* acc) {
   constexpr int U = unroll_for<T, BR, BC, UREQ>();
   for (int k0 = kb + lane; k0 < ke; k0 += tpr * U) {
     int col[U];
@@ -240,7 +267,7 @@ __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const
       const int k = k0 + u * tpr;
       if (k < ke) {
         col[u] = __ldcs(ci + k);
-        load_stream<T, BR * BC>(v + (size_t)k * (BR * BC), blk[u]);
+        load_block<T, BR, BC>(v, nnzb, k, blk[u]);
       } else {
         col[u] = -1;
 #pragma unroll
@@ -278,6 +305,18 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 #endif
 }
 
+// L2 prefetch of the values of blocks [a, b) (three ranges in the planar layout).
+template <class T, int BR, int BC>
+__device__ __forceinline__ void prefetch_blocks(const T* v, int64_t nnzb, int a, int b) {
+  if constexpr (planar_blocks<T, BR, BC>()) {
+    prefetch_l2(v + 4 * (int64_t)a, sizeof(T) * 4 * (size_t)(b - a));
+    prefetch_l2(v + 4 * nnzb + 4 * (int64_t)a, sizeof(T) * 4 * (size_t)(b - a));
+    prefetch_l2(v + 8 * nnzb + a, sizeof(T) * (size_t)(b - a));
+  } else {
+    prefetch_l2(v + (size_t)a * BR * BC, sizeof(T) * (size_t)(b - a) * BR * BC);
+  }
+}
+
 // One CTA handles the contiguous block rows [blockIdx.x * rows_per_cta, + rows_per_cta),
 // blockDim.x / tpr rows per pass, tpr lanes per row.  With prefetch, thread 0 first
 // asks L2 for the CTA's slice of the (constant) matrix arrays, before waiting for the
@@ -287,19 +326,20 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 // (pre_wait != 0); during set-up the previous kernel may still be writing them.
 template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per_cta, int prefetch, int pre_wait,
-    const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, G1 g1,
-    const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, const T* __restrict__ x2,
+    const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, int64_t nnzb1, G1 g1,
+    const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, int64_t nnzb2,
+    const T* __restrict__ x2,
     Epi epi) {
   const int r0 = blockIdx.x * rows_per_cta;
   const int r1 = r0 + rows_per_cta < nbr ? r0 + rows_per_cta : nbr;
   if (!pre_wait) dep_wait();
   if (prefetch && threadIdx.x == 0 && r0 < r1) {
     const int a = rp1[r0], b = rp1[r1];
-    prefetch_l2(v1 + (size_t)a * BR * BC1, sizeof(T) * (size_t)(b - a) * BR * BC1);
+    prefetch_blocks<T, BR, BC1>(v1, nnzb1, a, b);
     prefetch_l2(ci1 + a, sizeof(int) * (size_t)(b - a));
     if constexpr (BC2 > 0) {
       const int a2 = rp2[r0], b2 = rp2[r1];
-      prefetch_l2(v2 + (size_t)a2 * BR * BC2, sizeof(T) * (size_t)(b2 - a2) * BR * BC2);
+      prefetch_blocks<T, BR, BC2>(v2, nnzb2, a2, b2);
       prefetch_l2(ci2 + a2, sizeof(int) * (size_t)(b2 - a2));
     }
   }
@@ -315,9 +355,10 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
     typename Epi::Pre pre;
     if (valid && lane == 0) pre = epi.load(row);
     if (valid) {
-      row_accumulate<T, BR, BC1, UREQ>(ci1, v1, g1, rp1[row], rp1[row + 1], lane, tpr, acc);
+      row_accumulate<T, BR, BC1, UREQ>(ci1, v1, nnzb1, g1, rp1[row], rp1[row + 1], lane, tpr, acc);
       if constexpr (BC2 > 0)
-        row_accumulate<T, BR, BC2, UREQ>(ci2, v2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr, acc);
+        row_accumulate<T, BR, BC2, UREQ>(ci2, v2, nnzb2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr,
+                                         acc);
     }
     for (int off = tpr >> 1; off > 0; off >>= 1)
 #pragma unroll
