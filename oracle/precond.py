@@ -18,6 +18,11 @@ Fluid (Sec. 4.4, "the same Schur-complement approach as for the solid"; the
 reading taken here is the SIMPLE-type pressure Schur approximation):
     y_v = A_ff^-1 r_v;  x_p = S_p^-1 (r_p - B_pv y_v);  x_v = A_ff^-1 (r_v - B_vp x_p),
     S_p = C_pp - B_pv diag(A_ff)^-1 B_vp.
+With fluid_gmres_iters = k > 0 each A_ff^-1 above is k steps of GMRES on A_ff,
+right-preconditioned by the A_ff V-cycle(s), from a zero start (Sec. 4.4: an
+AMG-preconditioned GMRES approximates the fluid inverses); k is fixed (no
+stopping test), and the map r -> x is then nonlinear in r, which the outer
+flexible GMRES allows.
 Every inverse is a fixed number of smoothed-aggregation V-cycles (``amg.py``,
 x <- x + V(r - A x) after the first); A_uu^-1 is a Chebyshev-Jacobi polynomial
 (Chebyshev semi-iteration for mass matrices, Wathen & Rees, ETNA 34, 2009).  ``exact=True`` replaces all of them by sparse LU
@@ -33,6 +38,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .amg import AMGParams, chebyshev, point_dinv, power_lambda, rigid_body_modes, sa_setup, translations, vcycle
+from .fgmres import fgmres
 
 
 @dataclass
@@ -45,6 +51,7 @@ class PrecondParams:
     vcycles_solid: int = 2         # ... of S_hat^-1
     vcycles_fluid: int = 1         # ... of A_ff^-1
     vcycles_pressure: int = 1      # ... of S_p^-1
+    fluid_gmres_iters: int = 0     # > 0: each A_ff^-1 of the fluid solve is that many V-cycle-preconditioned GMRES steps
 
 
 class Blocks:
@@ -117,6 +124,17 @@ class _ChebInverse:
         return chebyshev(self.A, self.dinv, r, None, self.lam, self.degree, self.ratio, self.upper, x_is_zero=True)
 
 
+class _GMRESInverse:
+    """x_k of k steps of GMRES on A x = r from x = 0, right-preconditioned by M
+    (x_k minimises ||r - A x|| over x in M K_k(A M, r)); no stopping test."""
+
+    def __init__(self, A, M, k: int):
+        self.A, self.M, self.k = A, M, k
+
+    def __call__(self, r):
+        return fgmres(lambda v: self.A @ v, self.M, r, tol=0.0, restart=self.k, maxit=self.k).x
+
+
 class _ExactInverse:
     def __init__(self, A):
         self.lu = spla.splu(sp.csc_matrix(A))
@@ -150,6 +168,8 @@ class BlockLDU:
         # dt*theta on the s_u rows A_uv couples (the free rows), 0 on the fixed ones
         self.uv_weight = np.where(np.diff(sp.csr_matrix(B.A_uv).indptr) > 0, params.dt_theta, 0.0)
         self.Aff_inv = _AMGInverse(B.A_ff, d, translations(B.A_ff.shape[0] // d, d), ap, params.vcycles_fluid)
+        if params.fluid_gmres_iters > 0:
+            self.Aff_inv = _GMRESInverse(B.A_ff, self.Aff_inv, params.fluid_gmres_iters)
         self.Sp_inv = _AMGInverse(self.S_p, 1, np.ones((self.S_p.shape[0], 1)), ap, params.vcycles_pressure)
 
     # -------------------------------------------------------- sub-solves

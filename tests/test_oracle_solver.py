@@ -200,3 +200,52 @@ def test_large_amplitude_state_makes_the_solid_block_indefinite():
         lo[amp] = float(np.min(ev.real))
     assert lo[1e-2] > 0.0
     assert lo[5e-2] < -0.5
+
+
+def test_inner_gmres_returns_the_krylov_minimiser():
+    """The fluid solve's inner GMRES (Sec. 4.4) against what k GMRES steps must
+    return: with k = n the exact solution; after one step the minimal-residual
+    multiple alpha M r; after k steps the minimiser of ||r - A x|| over
+    x in M K_k(A M, r), computed here by least squares on an explicit basis."""
+    from oracle.precond import _GMRESInverse
+    rng = np.random.default_rng(11)
+    n = 12
+    A = 4.0 * np.eye(n) + rng.standard_normal((n, n))
+    Mm = np.diag(1.0 / np.diag(A)) + 0.01 * rng.standard_normal((n, n))
+    M = lambda v: Mm @ v
+    r = rng.standard_normal(n)
+    x = _GMRESInverse(A, M, n)(r)
+    assert np.linalg.norm(A @ x - r) <= 1e-10 * np.linalg.norm(r)
+    q = A @ (Mm @ r)
+    alpha = (q @ r) / (q @ q)
+    np.testing.assert_allclose(_GMRESInverse(A, M, 1)(r), alpha * (Mm @ r), rtol=1e-12, atol=1e-14)
+    K = [r]
+    for _ in range(3):
+        K.append(A @ (Mm @ K[-1]))
+    Q, _ = np.linalg.qr(np.column_stack(K))
+    P = Mm @ Q
+    c, *_ = np.linalg.lstsq(A @ P, r, rcond=None)
+    x4 = _GMRESInverse(A, M, 4)(r)
+    assert np.linalg.norm(x4 - P @ c) <= 1e-10 * np.linalg.norm(P @ c)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fluid_inner_gmres_improves_the_velocity_solve(dim):
+    """k inner GMRES steps never leave a larger A_ff residual than the plain
+    V-cycle (x = M r lies in the space they minimise over), and the outer solve
+    still reaches the tolerance."""
+    # 16x16 in 2D: A_ff needs more than one AMG level, so the V-cycle is not exact
+    s = fsigen.make_system(fsigen.CONFIGS["2d_tiny"]) if dim == 2 else tiny(3)
+    mr = 8.0 if dim == 2 else 20.0
+    base = oracle.BlockLDU(s.scipy(), s.offsets, dim, params=oracle.PrecondParams(mass_ratio=mr))
+    g4 = oracle.BlockLDU(s.scipy(), s.offsets, dim, params=oracle.PrecondParams(mass_ratio=mr, fluid_gmres_iters=4))
+    A_ff = base.B.A_ff
+    r = np.random.default_rng(6).standard_normal(A_ff.shape[0])
+    res = lambda x: np.linalg.norm(r - A_ff @ x)
+    assert len(base.Aff_inv.H.levels) > 1
+    r0 = res(base.Aff_inv(r))
+    assert r0 > 1e-6 * np.linalg.norm(r)
+    assert res(g4.Aff_inv(r)) <= r0 * (1 + 1e-12)
+    o = oracle.OracleSolver.from_system(s, oracle.PrecondParams(mass_ratio=mr, fluid_gmres_iters=4))
+    rr = o.solve(s.rhs, tol=1e-8)
+    assert rr.converged and rr.true_relres <= 1e-8
