@@ -62,17 +62,23 @@ enum {
   FSI_NO_PDL = 32,         /* launch the solve's kernels without programmatic dependent launch
                               (each kernel then waits for the previous one to finish before it
                               is scheduled).  Process-wide: the last fsi_setup's choice applies */
-  FSI_GRID_COARSE = 64     /* like FSI_CLUSTER_COARSE, but the coarse levels run as one cooperative
+  FSI_GRID_COARSE = 64,    /* like FSI_CLUSTER_COARSE, but the coarse levels run as one cooperative
                               launch over half the GPU with a software grid barrier (bounded
                               waits: a barrier that times out makes fsi_solve return FSI_ECUDA).
                               Not together with FSI_CLUSTER_COARSE */
+  FSI_FLUID_GMRES = 128    /* Sec. 4.4: every A_ff^-1 of the fluid Schur solve (and fsi_apply_block 2)
+                              is fluid_gmres_iters steps of GMRES on A_ff from a zero start,
+                              right-preconditioned by the A_ff V-cycle(s), Arnoldi in FP64 (classical
+                              Gram-Schmidt twice), least squares by Givens rotations on the device; a
+                              fixed step count, no stopping test.  The preconditioner then depends
+                              nonlinearly on its input, which FGMRES allows */
 };
 
 typedef struct fsi_params {
   int restart;              /* FGMRES restart length m (default 100) */
   int maxit;                /* maximum FGMRES iterations (default 1000) */
   int flags;                /* FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE |
-                               FSI_LEARNED | FSI_NO_PDL | FSI_GRID_COARSE */
+                               FSI_LEARNED | FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES */
   double dt_theta;          /* c = dt*theta of the solid Schur complement S_hat = A_vv + c A_vu (0.01) */
   /* smoothed-aggregation AMG */
   double strength_theta;    /* strength threshold on node-block Frobenius norms (0.08) */
@@ -108,6 +114,8 @@ typedef struct fsi_params {
   /* Chebyshev degree on the coarser AMG levels (>= 1); 0 = cheb_degree on every level (2:
      256x128 solve 14.3 -> 13.0 ms at 11-12 iterations; 1024x512 +3%, 35 vs 33 iterations) */
   int cheb_degree_coarse;
+  /* FSI_FLUID_GMRES: inner GMRES steps k per A_ff^-1, 1..32 (4) */
+  int fluid_gmres_iters;
 } fsi_params;
 
 typedef struct fsi_stats {

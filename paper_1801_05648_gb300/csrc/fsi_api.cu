@@ -67,6 +67,7 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.learned_accept = p.learned_accept;
   s.spmv_prefetch = p.spmv_prefetch;
   s.cluster_max_bytes = p.cluster_max_bytes;
+  s.fluid_gmres_iters = p.fluid_gmres_iters;
 }
 
 void validate_params(const fsi::SolverParams& s) {
@@ -87,7 +88,8 @@ void validate_params(const fsi::SolverParams& s) {
   require(!((s.flags & FSI_CLUSTER_COARSE) && (s.flags & FSI_GRID_COARSE)),
           "FSI_CLUSTER_COARSE and FSI_GRID_COARSE exclude each other");
   require((s.flags & ~(FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED |
-                       FSI_NO_PDL | FSI_GRID_COARSE)) == 0, "unknown flag bits");
+                       FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES)) == 0, "unknown flag bits");
+  require(s.fluid_gmres_iters >= 1 && s.fluid_gmres_iters <= fsi::kFluidGmresMax, "fluid_gmres_iters must be in [1, 32]");
 }
 
 void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -152,6 +154,7 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->spmv_prefetch = 1;
   p->cluster_max_bytes = 6.0e6;
   p->cheb_degree_coarse = 2;
+  p->fluid_gmres_iters = 4;
 }
 
 int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -398,7 +401,7 @@ int fsi_set_flags(fsi_ctx* ctx, int flags) {
   return guarded(ctx, [&] {
     constexpr int fixed = FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_NO_PDL | FSI_GRID_COARSE;
     constexpr int known = FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED |
-                          FSI_NO_PDL | FSI_GRID_COARSE;
+                          FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES;
     fsi::require((flags & ~known) == 0, "unknown flag bits");
     fsi::require((flags & fixed) == (ctx->C.prm.flags & fixed),
                  "FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_GRID_COARSE and FSI_NO_PDL are fixed at fsi_setup");

@@ -245,6 +245,145 @@ void solid_solve(Context& C, const T* r, T* x, cudaStream_t st, bool r_u_zero = 
   vfma<T>(nsu, uv_weight<T>(C), x_v, x_u, st);                                // x_u = y + dt*theta x_v
 }
 
+// ---- Sec. 4.4 inner solver for A_ff^-1: k steps of GMRES on A_ff from x = 0,
+// right-preconditioned by the A_ff V-cycle(s).  Arnoldi in FP64 with classical
+// Gram-Schmidt applied twice; the (k+1) x k least-squares problem by Givens
+// rotations in one device thread; x = Z y.  k is fixed (no stopping test), so the
+// whole sequence is enqueued once and can be captured into the iteration graph.
+
+// out = w / a with a = nrm[0] (sqrt(nrm[0]) when squared); out = 0 when a == 0
+__global__ void k_unit_scale(int64_t n, const double* __restrict__ w, const double* __restrict__ nrm, int squared,
+                             double* __restrict__ out) {
+  dep_wait();
+  const double a = squared ? sqrt(nrm[0]) : nrm[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a > 0.0 ? w[i] / a : 0.0;
+}
+
+// y = argmin || beta e_1 - H y ||, H the (k+1) x k Hessenberg matrix of the Arnoldi
+// step: H(i, j) = h1[j ld + i] + h2[j ld + i] for i <= j (the two Gram-Schmidt
+// passes), H(j+1, j) = nrm[j]; beta = sqrt(beta2[0]).  A zero pivot (exact
+// breakdown) gives y_i = 0 for that column.
+__global__ void k_inner_ls(int k, const double* __restrict__ h1, const double* __restrict__ h2, int ld,
+                           const double* __restrict__ nrm, const double* __restrict__ beta2, double* __restrict__ y) {
+  __shared__ double R[kFluidGmresMax + 1][kFluidGmresMax];   // shared, not local: no stack frame
+  __shared__ double g[kFluidGmresMax + 1], cs[kFluidGmresMax], sn[kFluidGmresMax];
+  dep_wait();
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i <= k; ++i) R[i][j] = 0.0;
+    for (int i = 0; i <= j; ++i) R[i][j] = h1[(size_t)j * ld + i] + h2[(size_t)j * ld + i];
+    R[j + 1][j] = nrm[j];
+  }
+  for (int i = 0; i <= k; ++i) g[i] = 0.0;
+  g[0] = sqrt(beta2[0]);
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * R[i][j] + sn[i] * R[i + 1][j];
+      R[i + 1][j] = -sn[i] * R[i][j] + cs[i] * R[i + 1][j];
+      R[i][j] = t;
+    }
+    const double den = hypot(R[j][j], R[j + 1][j]);
+    cs[j] = den > 0.0 ? R[j][j] / den : 1.0;
+    sn[j] = den > 0.0 ? R[j + 1][j] / den : 0.0;
+    R[j][j] = den;
+    R[j + 1][j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int l = i + 1; l < k; ++l) acc -= R[i][l] * y[l];
+    y[i] = R[i][i] != 0.0 ? acc / R[i][i] : 0.0;
+  }
+}
+
+template <class Ti, class To>
+void copy_as(int64_t n, const Ti* x, To* y, cudaStream_t st) {
+  if constexpr (sizeof(Ti) == sizeof(To)) axpby<To>(n, To(1), x, To(0), y, st);
+  else cast<Ti, To>(n, x, y, st);
+}
+
+template <class T>
+void aff_gmres(Context& C, const T* r, T* x, cudaStream_t st) {
+  FluidGmres& F = C.fg;
+  const int k = F.k;
+  const int64_t n = F.n;
+  const int ld = k + 1;
+  const Bsr& A = C.H[2].levels[0].A;
+  double* V = F.V.p;
+  double* Z = F.Z.p;
+  copy_as<T, double>(n, r, F.w.p, st);                                          // v_0 = r / ||r||
+  dot_dev<double>(n, F.w.p, F.w.p, F.part.p, F.beta.p, st);
+  launch_k(k_unit_scale, grid_n(n), 256, 0, st, n, (const double*)F.w.p, (const double*)F.beta.p, 1, V);
+  for (int j = 0; j < k; ++j) {
+    double* vj = V + (size_t)j * n;
+    double* zj = Z + (size_t)j * n;
+    if constexpr (sizeof(T) == 4) {                                             // z_j = V-cycle(v_j)
+      cast<double, float>(n, vj, F.t32a.p, st);
+      amg_solve<float>(C, 2, C.prm.vc_fluid, F.t32a.p, F.t32b.p, st);
+      cast<float, double>(n, F.t32b.p, zj, st);
+    } else {
+      amg_solve<double>(C, 2, C.prm.vc_fluid, vj, zj, st);
+    }
+    spmv_axpby<double>(A, zj, 1.0, 0.0, F.w.p, st);                             // w = A_ff z_j
+    double* hj1 = F.h1.p + (size_t)j * ld;
+    double* hj2 = F.h2.p + (size_t)j * ld;
+    mdot(n, V, n, F.zero.p, j + 1, F.w.p, F.part.p, hj1, ld, st);              // CGS, twice
+    maxpy(n, V, n, F.zero.p, j + 1, hj1, 1.0, F.w.p, nullptr, st);
+    mdot(n, V, n, F.zero.p, j + 1, F.w.p, F.part.p, hj2, ld, st);
+    maxpy(n, V, n, F.zero.p, j + 1, hj2, 1.0, F.w.p, F.npart.p, st);
+    finish_norm(F.npart.p, F.nrm.p + j, st);                                    // h_{j+1,j} = ||w||
+    if (j + 1 < k)
+      launch_k(k_unit_scale, grid_n(n), 256, 0, st, n, (const double*)F.w.p, (const double*)(F.nrm.p + j), 0,
+               V + (size_t)(j + 1) * n);
+  }
+  launch_k(k_inner_ls, 1, 32, 0, st, k, (const double*)F.h1.p, (const double*)F.h2.p, ld, (const double*)F.nrm.p,
+           (const double*)F.beta.p, F.y.p);
+  FSI_CUDA(cudaMemsetAsync(F.w.p, 0, sizeof(double) * n, st));
+  maxpy(n, Z, n, F.zero.p, k, F.y.p, -1.0, F.w.p, nullptr, st);                 // x = Z y
+  copy_as<double, T>(n, F.w.p, x, st);
+}
+
+// Workspace of the inner GMRES for the current flags and k (allocated outside any
+// stream capture: at preconditioner build, before a solve, before a block apply).
+void ensure_fluid_gmres(Context& C) {
+  if (!(C.prm.flags & FLUID_GMRES)) return;
+  FluidGmres& F = C.fg;
+  const int k = C.prm.fluid_gmres_iters;
+  const int64_t n = C.off[4] - C.off[3];
+  if (F.k == k && F.n == n) return;
+  F.k = k;
+  F.n = n;
+  if (n == 0) return;
+  F.V.alloc((size_t)(k + 1) * n);
+  F.Z.alloc((size_t)k * n);
+  F.w.alloc(n);
+  F.t32a.alloc(n);
+  F.t32b.alloc(n);
+  F.h1.alloc((size_t)(k + 1) * k);
+  F.h2.alloc((size_t)(k + 1) * k);
+  F.nrm.alloc(k);
+  F.beta.alloc(1);
+  F.y.alloc(k);
+  F.part.alloc((size_t)(k + 1) * kRedBlocks);
+  F.npart.alloc(kRedBlocks);
+  F.zero.alloc(1);
+  FSI_CUDA(cudaMemsetAsync(F.zero.p, 0, sizeof(int), C.s));
+  if (C.iter_graph) { cudaGraphExecDestroy(C.iter_graph); C.iter_graph = nullptr; }
+}
+
+// A_ff^-1 of the fluid solve: V-cycle(s), or the inner GMRES with FLUID_GMRES
+template <class T>
+void aff_inverse(Context& C, const T* r, T* x, cudaStream_t st) {
+  if (!(C.prm.flags & FLUID_GMRES)) {
+    amg_solve<T>(C, 2, C.prm.vc_fluid, r, x, st);
+    return;
+  }
+  require(C.fg.k == C.prm.fluid_gmres_iters && C.fg.n == C.off[4] - C.off[3], "inner fluid GMRES not prepared");
+  if (C.fg.n > 0) aff_gmres<T>(C, r, x, st);
+}
+
 // fluid sub-solve on (r_v, r_p) -> (x_v, x_p)
 template <class T>
 void fluid_solve(Context& C, const T* r, T* x, cudaStream_t st) {
@@ -254,11 +393,11 @@ void fluid_solve(Context& C, const T* r, T* x, cudaStream_t st) {
   const T* r_p = r + nfv;
   T* x_v = x;
   T* x_p = x + nfv;
-  amg_solve<T>(C, 2, C.prm.vc_fluid, r_v, W.s3_y.p, st);                      // y = A_ff^-1 r_v
+  aff_inverse<T>(C, r_v, W.s3_y.p, st);                                       // y = A_ff^-1 r_v
   spmv2_resid<T>(C.B_pv, W.s3_y.p, nullptr, nullptr, r_p, W.s3_t.p, st);      // t = r_p - B_pv y
   amg_solve<T>(C, 3, C.prm.vc_pressure, W.s3_t.p, x_p, st);                   // x_p = S_p^-1 t
   spmv2_resid<T>(C.B_vp, x_p, nullptr, nullptr, r_v, W.s3_t.p, st);           // t = r_v - B_vp x_p
-  amg_solve<T>(C, 2, C.prm.vc_fluid, W.s3_t.p, x_v, st);                      // x_v = A_ff^-1 t
+  aff_inverse<T>(C, W.s3_t.p, x_v, st);                                       // x_v = A_ff^-1 t
 }
 
 }  // namespace
@@ -443,10 +582,11 @@ void precond_apply(Context& C, const T* r, T* z) {
 
 template <class T>
 void apply_block(Context& C, int which, const T* in, T* out) {
+  ensure_fluid_gmres(C);
   switch (which) {
     case 0: amg_solve<T>(C, 0, C.prm.vc_mesh, in, out, C.s); break;
     case 1: amg_solve<T>(C, 1, C.prm.vc_solid, in, out, C.s); break;
-    case 2: amg_solve<T>(C, 2, C.prm.vc_fluid, in, out, C.s); break;
+    case 2: aff_inverse<T>(C, in, out, C.s); break;
     case 3: amg_solve<T>(C, 3, C.prm.vc_pressure, in, out, C.s); break;
     case 4: cheb_apply<T>(C.mass, in, out, C.s); break;
     case 5: solid_solve<T>(C, in, out, C.s); break;
@@ -481,7 +621,20 @@ double precond_bytes(const Context& C, int vb) {
   // (two A_ff solves and one S_p solve), and the coupling products
   double b = 0;
   b += 2.0 * p.vc_mesh * C.H[0].vcycle_bytes(vb) + 2.0 * p.vc_solid * C.H[1].vcycle_bytes(vb) +
-       2.0 * p.vc_fluid * C.H[2].vcycle_bytes(vb) + 1.0 * p.vc_pressure * C.H[3].vcycle_bytes(vb);
+       1.0 * p.vc_pressure * C.H[3].vcycle_bytes(vb);
+  if (p.flags & FLUID_GMRES) {
+    // per A_ff^-1: k steps of (V-cycle, FP64 A_ff product, two Gram-Schmidt passes
+    // over V_0..V_j: read V twice and w, write w), the start and x = Z y
+    const double nf = (double)(C.off[4] - C.off[3]);
+    const int k = p.fluid_gmres_iters;
+    double g = 3.0 * 8.0 * nf + 8.0 * nf * (k + 2);
+    for (int j = 0; j < k; ++j)
+      g += p.vc_fluid * C.H[2].vcycle_bytes(vb) + C.H[2].levels[0].A.spmv_bytes(8) + 2.0 * 8.0 * nf * (2.0 * (j + 1) + 3.0) +
+           (vb == 4 ? 2.0 * 12.0 * nf : 0.0) + 16.0 * nf;
+    b += 2.0 * g;
+  } else {
+    b += 2.0 * p.vc_fluid * C.H[2].vcycle_bytes(vb);
+  }
   const double mass_solves = C.csf_u_zero ? 1.0 : 2.0;   // step 4's S^-1 skips its mass solve when r_u = 0
   b += mass_solves * C.mass.degree * C.mass.A.spmv_bytes(vb);
   b += 2.0 * 4.0 * vb * (double)(C.off[3] - C.off[2]);
@@ -554,8 +707,9 @@ void run_iteration(Context& C) {
     return;
   }
   const bool learned = (C.prm.flags & LEARNED) != 0;
+  const int fluid = (C.prm.flags & FLUID_GMRES) ? C.prm.fluid_gmres_iters : 0;
   if (!C.iter_graph || C.iter_graph_prec != C.precision || C.iter_graph_learned != learned ||
-      C.iter_graph_harvest != C.harvest || C.iter_graph_harvest_n != C.harvest_n) {
+      C.iter_graph_harvest != C.harvest || C.iter_graph_harvest_n != C.harvest_n || C.iter_graph_fluid != fluid) {
     if (C.iter_graph) { cudaGraphExecDestroy(C.iter_graph); C.iter_graph = nullptr; }
     cudaGraph_t g;
     FSI_CUDA(cudaStreamBeginCapture(C.s, cudaStreamCaptureModeThreadLocal));
@@ -575,6 +729,7 @@ void run_iteration(Context& C) {
     C.iter_graph_learned = learned;
     C.iter_graph_harvest = C.harvest;
     C.iter_graph_harvest_n = C.harvest_n;
+    C.iter_graph_fluid = fluid;
   }
   FSI_CUDA(cudaGraphLaunch(C.iter_graph, C.s));
   g_kernel_launches += C.graph_kernels;
@@ -590,6 +745,7 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
     require(C.learned.n_nodes > 0 && C.learned.has_weights,
             "FSI_LEARNED needs fsi_learned_setup and weights (fsi_learned_load or fsi_precond_build's path)");
   ensure_krylov(C);
+  ensure_fluid_gmres(C);
   C.last_accepted = 0;
   if (C.prm.flags & LEARNED) FSI_CUDA(cudaMemsetAsync(C.learned.counters.p, 0, 2 * sizeof(int), C.s));
   const int64_t n = C.n;

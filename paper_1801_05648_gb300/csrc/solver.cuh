@@ -24,10 +24,23 @@ struct SolverParams {
   double learned_accept = 0.1;   // accept the learned correction when ||r' - A c|| < this * ||r'||
   int spmv_prefetch = 1;
   double cluster_max_bytes = 6.0e6;
+  int fluid_gmres_iters = 4;     // FLUID_GMRES: inner GMRES steps per A_ff^-1
 };
 
 enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8, LEARNED = 16, NO_PDL = 32,
-             GRID_COARSE = 64 };
+             GRID_COARSE = 64, FLUID_GMRES = 128 };
+
+constexpr int kFluidGmresMax = 32;
+
+// Workspace of the inner fluid GMRES (Sec. 4.4): k steps on the n_fv fluid-velocity
+// DOFs; basis V ((k+1) x n) and preconditioned directions Z (k x n) in FP64.
+struct FluidGmres {
+  int k = 0;
+  int64_t n = 0;
+  DBuf<double> V, Z, w, h1, h2, nrm, beta, y, part, npart;
+  DBuf<float> t32a, t32b;     // FP32 V-cycle input/output (FP32-AMG form)
+  DBuf<int> zero;             // device 0: the vector counts of mdot/maxpy are offsets from it
+};
 
 template <class T>
 struct PrecWork {
@@ -65,6 +78,7 @@ struct Context {
   int precision = 0;          // 0 FP64, 1 FP32 AMG
   PrecWork<double> pw64;
   PrecWork<float> pw32;
+  FluidGmres fg;
   DBuf<double> solid_B;       // near-nullspace of S_hat (rigid-body modes)
   // learned correction stage, its training operator A^T, and the residual harvest
   Learned learned;
@@ -85,6 +99,7 @@ struct Context {
   bool iter_graph_learned = false;
   const double* iter_graph_harvest = nullptr;
   int iter_graph_harvest_n = 0;
+  int iter_graph_fluid = 0;   // inner fluid GMRES steps the graph was captured with (0: off)
   int64_t graph_kernels = 0;  // kernel launches inside one replay of iter_graph
   int64_t last_launches = 0;  // kernels launched by the last solve
   // stats

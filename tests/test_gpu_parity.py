@@ -251,6 +251,62 @@ def test_edge_cases(torch_cuda):
     gw.close(); gn.close()
 
 
+@pytest.mark.parametrize("name", ["2d_16x16", "2d_37x19_ragged", "3d_8x4x4"])
+def test_fluid_inner_gmres_parity(name, torch_cuda):
+    """FSI_FLUID_GMRES (Sec. 4.4): every A_ff^-1 of the fluid solve is k = 4 steps of
+    V-cycle-preconditioned GMRES.  FP64 against the oracle's fluid_gmres_iters = 4:
+    the A_ff, fluid and Alg. 2 applications to rounding (GMRES keeps the V-cycle's
+    1e-11 up to the growth of its k steps), the solve to 1e-8 with the iteration
+    count within +-1; switching the flag on an existing context re-captures the
+    iteration graph; the FP32-AMG form meets the residual and the error bound."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    cfg, mr = CASES[name]
+    s = fsigen.make_system(cfg)
+    op = oracle.PrecondParams(mass_ratio=mr, fluid_gmres_iters=4)
+    o = oracle.OracleSolver.from_system(s, params=op)
+    ref = o.solve(s.rhs)
+    G = P.FSI_USE_GRAPHS
+    g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr, flags=G | P.FSI_FLUID_GMRES,
+                                                           fluid_gmres_iters=4))
+    g.precond_build("fp64")
+    for blk, sl, f in _block_slices(s, o):
+        if blk not in ("fluid_velocity", "fluid", "precond"):
+            continue
+        r = np.random.default_rng(3).standard_normal(sl.stop - sl.start)
+        rt = torch.tensor(r, device="cuda")
+        zt = torch.zeros_like(rt)
+        g.apply_block(blk, rt, zt)
+        assert rel(zt.cpu().numpy(), f(r)) <= 1e-10, blk
+    b = torch.tensor(s.rhs, device="cuda")
+    x = torch.zeros_like(b)
+    st = g.solve(b, x, 1e-8)
+    assert st.status == 0 and st.true_relres <= 1e-8
+    assert abs(st.iters - ref.iters) <= 1 and rel(x.cpu().numpy(), ref.x) <= 1e-8
+    # the same context with the flag off solves like the plain form, and on again like above
+    _, _, ref0, _, _ = case(name, torch)
+    g.set_flags(G)
+    x0 = torch.zeros_like(b)
+    st0 = g.solve(b, x0, 1e-8)
+    assert abs(st0.iters - ref0.iters) <= 1 and rel(x0.cpu().numpy(), ref0.x) <= 1e-8
+    g.set_flags(G | P.FSI_FLUID_GMRES)
+    x1 = torch.zeros_like(b)
+    st1 = g.solve(b, x1, 1e-8)
+    assert st1.iters == st.iters and np.array_equal(x1.cpu().numpy(), x.cpu().numpy())
+    g.close()
+    g32 = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr, flags=G | P.FSI_FLUID_GMRES,
+                                                             fluid_gmres_iters=4))
+    g32.precond_build("fp32")
+    x32 = torch.zeros_like(b)
+    st32 = g32.solve(b, x32, 1e-8)
+    g32.close()
+    xc = x32.cpu().numpy()
+    assert st32.status == 0
+    assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.001
+    e64 = rel(ref.x, s.x_exact)
+    assert rel(xc, s.x_exact) <= max(10.0 * e64, 1e-6)
+
+
 @pytest.mark.parametrize("name", ["2d_mid", "3d", "2d_large"])
 def test_full_size_solves(name, torch_cuda):
     """Full-size Jacobians: the solve reaches 1e-8 confirmed by an FP64 CPU residual,
