@@ -28,6 +28,11 @@ x <- x + V(r - A x) after the first); A_uu^-1 is a Chebyshev-Jacobi polynomial
 (Chebyshev semi-iteration for mass matrices, Wathen & Rees, ETNA 34, 2009).  ``exact=True`` replaces all of them by sparse LU
 solves, which turns Alg. 2 into P^-1 r with P = (D + L) D^-1 (D + U),
 D = diag(M, S, F), L/U the strict block triangles of A with C_sm = 0.
+Other block factorisations (the remark after Sec. 4.1: the LDU form depends on the
+block ordering, and other orderings give other preconditioners), chosen by
+``variant``: "lower" applies (D + L)^-1 (Alg. 2 steps 1-3), "upper" (D + U)^-1
+(x_f = F^-1 r_f, x_s = S^-1 (r_s - C_sf x_f), x_m = M^-1 (r_m - C_ms x_s)) and
+"diag" D^-1, each with the same approximate inverses.
 """
 from __future__ import annotations
 
@@ -52,6 +57,7 @@ class PrecondParams:
     vcycles_fluid: int = 1         # ... of A_ff^-1
     vcycles_pressure: int = 1      # ... of S_p^-1
     fluid_gmres_iters: int = 0     # > 0: each A_ff^-1 of the fluid solve is that many V-cycle-preconditioned GMRES steps
+    variant: str = "ldu"           # block factorisation: "ldu" (Alg. 2), "lower", "upper", "diag"
 
 
 class Blocks:
@@ -201,9 +207,21 @@ class BlockLDU:
     def __call__(self, r):
         B = self.B
         r_m, r_s, r_f = r[B.m], r[B.s], r[B.f]
+        v = self.params.variant
+        if v == "diag":                                    # D^-1
+            return np.concatenate([self.M_inv(r_m), self.S_inv(r_s), self.F_inv(r_f)])
+        if v == "upper":                                   # (D + U)^-1, backward substitution
+            x_f = self.F_inv(r_f)
+            x_s = self.S_inv(r_s - B.C_sf @ x_f)
+            x_m = self.M_inv(r_m - B.C_ms @ x_s)
+            return np.concatenate([x_m, x_s, x_f])
         x_m = self.M_inv(r_m)
         x_s = self.S_inv(r_s)
         x_f = self.F_inv(r_f - B.C_fm @ x_m - B.C_fs @ x_s)
+        if v == "lower":                                   # (D + L)^-1: steps 1-3
+            return np.concatenate([x_m, x_s, x_f])
+        if v != "ldu":
+            raise ValueError(f"unknown variant {v!r}")
         x_s = x_s - self.S_inv(B.C_sf @ x_f)
         x_m = x_m - self.M_inv(B.C_ms @ x_s)
         return np.concatenate([x_m, x_s, x_f])

@@ -249,3 +249,41 @@ def test_fluid_inner_gmres_improves_the_velocity_solve(dim):
     o = oracle.OracleSolver.from_system(s, oracle.PrecondParams(mass_ratio=mr, fluid_gmres_iters=4))
     rr = o.solve(s.rhs, tol=1e-8)
     assert rr.converged and rr.true_relres <= 1e-8
+
+
+@pytest.mark.parametrize("variant", ["lower", "upper", "diag"])
+def test_exact_block_variants_are_their_triangular_solves(variant):
+    """The block factorisations other than Alg. 2 (the remark after Sec. 4.1): with
+    exact sub-solves "lower" is (D + L)^-1, "upper" (D + U)^-1 and "diag" D^-1,
+    D = diag(M, S, F) and L (C_sm dropped) / U the strict block triangles."""
+    s = tiny(2)
+    A, I = _dense_blocks(s)
+    D = np.zeros_like(A)
+    L = np.zeros_like(A)
+    U = np.zeros_like(A)
+    for a in range(3):
+        for b in range(3):
+            blk = A[I[a], I[b]]
+            if a == b:
+                D[I[a], I[b]] = blk
+            elif a > b and not (a == 1 and b == 0):
+                L[I[a], I[b]] = blk
+            elif a < b:
+                U[I[a], I[b]] = blk
+    P = {"lower": D + L, "upper": D + U, "diag": D}[variant]
+    pre = oracle.BlockLDU(s.scipy(), s.offsets, 2, params=oracle.PrecondParams(variant=variant), exact=True)
+    r = np.random.default_rng(8).standard_normal(A.shape[0])
+    want = np.linalg.solve(P, r)
+    assert np.allclose(pre(r), want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
+    # and each differs from Alg. 2 in the mesh block (Alg. 2's last step updates x_m)
+    ldu = oracle.BlockLDU(s.scipy(), s.offsets, 2, exact=True)(r)
+    m = I[0]
+    assert np.linalg.norm(pre(r)[m] - ldu[m]) > 1e-6 * np.linalg.norm(ldu[m])
+
+
+@pytest.mark.parametrize("variant", ["lower", "upper", "diag"])
+def test_block_variants_converge_with_amg_subsolves(variant):
+    s = tiny(2)
+    o = oracle.OracleSolver.from_system(s, oracle.PrecondParams(mass_ratio=8.0, variant=variant))
+    r = o.solve(s.rhs, tol=1e-8, restart=200)
+    assert r.converged and r.true_relres <= 1e-8
