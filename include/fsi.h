@@ -116,7 +116,16 @@ typedef struct fsi_params {
   int cheb_degree_coarse;
   /* FSI_FLUID_GMRES: inner GMRES steps k per A_ff^-1, 1..32 (4) */
   int fluid_gmres_iters;
+  /* block factorisation of the preconditioner (the LDU form depends on the block
+     ordering, Sec. 4.1): FSI_PRECOND_LDU Alg. 2 (default); FSI_PRECOND_LOWER (D + L)^-1,
+     Alg. 2 steps 1-3; FSI_PRECOND_UPPER (D + U)^-1: x_f = F^-1 r_f,
+     x_s = S^-1 (r_s - C_sf x_f), x_m = M^-1 (r_m - C_ms x_s); FSI_PRECOND_DIAG D^-1.
+     D = diag(M, S, F), L (C_sm dropped) / U the strict block triangles; the same
+     approximate inverses in every variant */
+  int precond_variant;
 } fsi_params;
+
+enum { FSI_PRECOND_LDU = 0, FSI_PRECOND_LOWER = 1, FSI_PRECOND_UPPER = 2, FSI_PRECOND_DIAG = 3 };
 
 typedef struct fsi_stats {
   int iters;                /* FGMRES iterations of the last solve */

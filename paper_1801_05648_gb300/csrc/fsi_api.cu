@@ -68,6 +68,7 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.spmv_prefetch = p.spmv_prefetch;
   s.cluster_max_bytes = p.cluster_max_bytes;
   s.fluid_gmres_iters = p.fluid_gmres_iters;
+  s.precond_variant = p.precond_variant;
 }
 
 void validate_params(const fsi::SolverParams& s) {
@@ -90,6 +91,8 @@ void validate_params(const fsi::SolverParams& s) {
   require((s.flags & ~(FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED |
                        FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES)) == 0, "unknown flag bits");
   require(s.fluid_gmres_iters >= 1 && s.fluid_gmres_iters <= fsi::kFluidGmresMax, "fluid_gmres_iters must be in [1, 32]");
+  require(s.precond_variant >= FSI_PRECOND_LDU && s.precond_variant <= FSI_PRECOND_DIAG,
+          "precond_variant must be FSI_PRECOND_LDU, _LOWER, _UPPER or _DIAG");
 }
 
 void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -155,6 +158,7 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->cluster_max_bytes = 6.0e6;
   p->cheb_degree_coarse = 2;
   p->fluid_gmres_iters = 4;
+  p->precond_variant = FSI_PRECOND_LDU;
 }
 
 int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,

@@ -558,18 +558,31 @@ void precond_apply(Context& C, const T* r, T* z) {
   T* z_s = z + o[1];
   T* z_f = z + o[3];
   const int64_t nfv = o[4] - o[3], ns = o[3] - o[1], nm = o[1] - o[0];
+  const int variant = C.prm.precond_variant;
+  if (variant == 2) {
+    // (D + U)^-1: x_f = F^-1 r_f;  x_s = S^-1 (r_s - C_sf x_f);  x_m = M^-1 (r_m - C_ms x_s)
+    fluid_solve<T>(C, r_f, z_f, C.s);
+    spmv2_resid<T>(C.C_sv_f, z_f, &C.C_sv_p, z_f + nfv, r_s, W.a2_t.p, C.s);
+    solid_solve<T>(C, W.a2_t.p, z_s, C.s);
+    spmv2_resid<T>(C.C_ms, z_s, nullptr, nullptr, r_m, W.a2_t.p, C.s);
+    mesh_solve<T>(C, W.a2_t.p, z_m, C.s);
+    return;
+  }
   // 1-2: independent, the mesh solve runs on the second stream (a parallel
   // branch when captured into a graph)
   FSI_CUDA(cudaEventRecord(C.ev_fork, C.s));
   FSI_CUDA(cudaStreamWaitEvent(C.s2, C.ev_fork, 0));
   mesh_solve<T>(C, r_m, z_m, C.s2);
   solid_solve<T>(C, r_s, z_s, C.s);
+  if (variant == 3) fluid_solve<T>(C, r_f, z_f, C.s);        // D^-1: x_f = F^-1 r_f
   FSI_CUDA(cudaEventRecord(C.ev_join, C.s2));
   FSI_CUDA(cudaStreamWaitEvent(C.s, C.ev_join, 0));
+  if (variant == 3) return;
   // 3: t_f = r_f - C_fm x_m - C_fs x_s  (x_m, x_s contiguous), x_f = F^-1 t_f
   spmv2_resid<T>(C.C_fv_ms, z, nullptr, nullptr, r_f, W.a2_t.p, C.s);
   spmv2_resid<T>(C.C_p_ms, z, nullptr, nullptr, r_f + nfv, W.a2_t.p + nfv, C.s);
   fluid_solve<T>(C, W.a2_t.p, z_f, C.s);
+  if (variant == 1) return;                                    // (D + L)^-1: steps 1-3
   // 4: x_s -= S^-1 C_sf x_f
   spmv2_axpby<T>(C.C_sv_f, z_f, &C.C_sv_p, z_f + nfv, T(1), T(0), W.a2_t.p, C.s);
   solid_solve<T>(C, W.a2_t.p, W.a2_u.p, C.s, C.csf_u_zero);
@@ -619,8 +632,11 @@ double precond_bytes(const Context& C, int vb) {
   // Alg. 2: two mesh solves, two solid solves (one mass solve each, none in the
   // second when its r_u is structurally zero, and the x_u update), one fluid solve
   // (two A_ff solves and one S_p solve), and the coupling products
+  // (the other block factorisations: one mesh and one solid solve, and only their couplings)
+  const bool ldu = p.precond_variant == 0;
+  const double nmesh = ldu ? 2.0 : 1.0, nsolid = ldu ? 2.0 : 1.0;
   double b = 0;
-  b += 2.0 * p.vc_mesh * C.H[0].vcycle_bytes(vb) + 2.0 * p.vc_solid * C.H[1].vcycle_bytes(vb) +
+  b += nmesh * p.vc_mesh * C.H[0].vcycle_bytes(vb) + nsolid * p.vc_solid * C.H[1].vcycle_bytes(vb) +
        1.0 * p.vc_pressure * C.H[3].vcycle_bytes(vb);
   if (p.flags & FLUID_GMRES) {
     // per A_ff^-1: k steps of (V-cycle, FP64 A_ff product, two Gram-Schmidt passes
@@ -635,10 +651,12 @@ double precond_bytes(const Context& C, int vb) {
   } else {
     b += 2.0 * p.vc_fluid * C.H[2].vcycle_bytes(vb);
   }
-  const double mass_solves = C.csf_u_zero ? 1.0 : 2.0;   // step 4's S^-1 skips its mass solve when r_u = 0
+  const double mass_solves = ldu ? (C.csf_u_zero ? 1.0 : 2.0) : 1.0;   // step 4's S^-1 skips its mass solve when r_u = 0
   b += mass_solves * C.mass.degree * C.mass.A.spmv_bytes(vb);
-  b += 2.0 * 4.0 * vb * (double)(C.off[3] - C.off[2]);
-  for (const Bsr* B : {&C.C_ms, &C.C_sv_f, &C.C_sv_p, &C.C_fv_ms, &C.C_p_ms}) b += B->spmv_bytes(vb);
+  b += nsolid * 4.0 * vb * (double)(C.off[3] - C.off[2]);
+  const int v = p.precond_variant;
+  if (v == 0 || v == 2) for (const Bsr* B : {&C.C_ms, &C.C_sv_f, &C.C_sv_p}) b += B->spmv_bytes(vb);
+  if (v == 0 || v == 1) for (const Bsr* B : {&C.C_fv_ms, &C.C_p_ms}) b += B->spmv_bytes(vb);
   b += mass_solves * C.A_vu.spmv_bytes(vb) + C.B_vp.spmv_bytes(vb) + C.B_pv.spmv_bytes(vb);
   return b;
 }

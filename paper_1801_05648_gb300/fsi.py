@@ -19,6 +19,7 @@ FSI_OK, FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA, FSI_ENOTCONV, FSI_EBREAKDOWN, FSI_ENO
 FSI_FP64, FSI_FP32_AMG = 0, 1
 FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_LEARNED, FSI_NO_PDL = 1, 2, 4, 8, 16, 32
 FSI_GRID_COARSE, FSI_FLUID_GMRES = 64, 128
+FSI_PRECOND_LDU, FSI_PRECOND_LOWER, FSI_PRECOND_UPPER, FSI_PRECOND_DIAG = 0, 1, 2, 3
 FSI_MLP_PARAMS, FSI_MLP_INPUTS = 7941, 53
 STATUS_NAMES = {0: "FSI_OK", -1: "FSI_EINVAL", -2: "FSI_ENOMEM", -3: "FSI_ECUDA", -4: "FSI_ENOTCONV",
                 -5: "FSI_EBREAKDOWN", -6: "FSI_ENONFINITE"}
@@ -52,7 +53,7 @@ class Params(ctypes.Structure):
                 ("spmv_unroll", ctypes.c_int),
                 ("learned_accept", ctypes.c_double), ("spmv_prefetch", ctypes.c_int),
                 ("cluster_max_bytes", ctypes.c_double), ("cheb_degree_coarse", ctypes.c_int),
-                ("fluid_gmres_iters", ctypes.c_int)]
+                ("fluid_gmres_iters", ctypes.c_int), ("precond_variant", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -251,6 +251,40 @@ def test_edge_cases(torch_cuda):
     gw.close(); gn.close()
 
 
+@pytest.mark.parametrize("variant", ["lower", "upper", "diag"])
+@pytest.mark.parametrize("name", ["2d_37x19_ragged", "3d_8x4x4"])
+def test_block_factorisation_variants(name, variant, torch_cuda):
+    """precond_variant (the block orderings of the remark after Sec. 4.1): P^-1 in
+    FP64 against the oracle's variant to 1e-11, the FP64 solve within 1 iteration
+    and 1e-8 of the oracle's, and the FP32-AMG solve to the residual."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    code = {"lower": P.FSI_PRECOND_LOWER, "upper": P.FSI_PRECOND_UPPER, "diag": P.FSI_PRECOND_DIAG}[variant]
+    cfg, mr = CASES[name]
+    s = fsigen.make_system(cfg)
+    o = oracle.OracleSolver.from_system(s, params=oracle.PrecondParams(mass_ratio=mr, variant=variant))
+    ref = o.solve(s.rhs)
+    b = torch.tensor(s.rhs, device="cuda")
+    for prec in ("fp64", "fp32"):
+        g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr, flags=P.FSI_USE_GRAPHS,
+                                                               precond_variant=code))
+        g.precond_build(prec)
+        if prec == "fp64":
+            r = np.random.default_rng(3).standard_normal(s.n)
+            rt = torch.tensor(r, device="cuda")
+            zt = torch.zeros_like(rt)
+            g.apply_block("precond", rt, zt)
+            assert rel(zt.cpu().numpy(), o.P(r)) <= 1e-11
+        x = torch.zeros_like(b)
+        st = g.solve(b, x, 1e-8)
+        g.close()
+        xc = x.cpu().numpy()
+        assert st.status == 0
+        assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.001
+        if prec == "fp64":
+            assert abs(st.iters - ref.iters) <= 1 and rel(xc, ref.x) <= 1e-8
+
+
 @pytest.mark.parametrize("name", ["2d_16x16", "2d_37x19_ragged", "3d_8x4x4"])
 def test_fluid_inner_gmres_parity(name, torch_cuda):
     """FSI_FLUID_GMRES (Sec. 4.4): every A_ff^-1 of the fluid solve is k = 4 steps of
