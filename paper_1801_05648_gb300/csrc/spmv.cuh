@@ -245,10 +245,14 @@ struct EpiDinv {
 
 // ------------------------------------------------------------------ kernel
 // Unroll depth: blocks each lane has in flight per trip (register budget): the
-// requested depth UREQ (4 or 8) for small blocks, less for large ones.
+// requested depth UREQ (4 or 8) for small blocks, less for large ones; 3 for the
+// planar FP32 3 x 3 blocks (64 registers: four 256-thread CTAs per SM instead of
+// three at depth 4).  A lane visits its blocks in increasing order at any depth,
+// so the depth does not change the sums.
 template <class T, int BR, int BC, int UREQ>
 __host__ __device__ constexpr int unroll_for() {
-  return (int)(sizeof(T) * (BR * BC + BC)) <= 24 ? UREQ : ((int)(sizeof(T) * (BR * BC + BC)) <= 64 ? 4 : 2);
+  return planar_blocks<T, BR, BC>() ? 3
+         : (int)(sizeof(T) * (BR * BC + BC)) <= 24 ? UREQ : ((int)(sizeof(T) * (BR * BC + BC)) <= 64 ? 4 : 2);
 }
 
 // acc += sum over the lane's share of row entries [kb, ke) of block * x[col].
