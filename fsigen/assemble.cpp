@@ -19,8 +19,13 @@
 //                    functions vanish on the interface).
 // with F = I + grad u, J = det F, sigma_v = rho_f nu_f (grad v F^-1 + F^-T grad v^T),
 // Sigma = 2 mu E + lambda tr(E) I, E = (F^T F - I)/2 (Sec. 2).
-// Only theta = 1 (backward Euler) is supported; then every (1-theta) term of
-// F(Phi) vanishes and J^theta = J.
+// Theta scheme, 0 < theta <= 1 (Sec. 3.2): the convection, viscous-stress,
+// outflow and solid-stress terms and the kinematic velocity are weighted
+// dt*theta at the new and dt*(1-theta) at the previous time level; the pressure,
+// the incompressibility constraint and the mesh motion stay fully implicit; the
+// fluid time derivative carries J^theta = theta J + (1-theta) J_old.  theta = 1
+// is backward Euler (every previous-level term vanishes, J^theta = J),
+// theta = 1/2 Crank-Nicolson, theta = 1/2 + dt the shifted variant.
 //
 // Discretisation: Q2 velocity and displacement, continuous Q1 pressure on the
 // whole box (nodes at cell vertices), 3^d Gauss points per cell.  The Jacobian
@@ -268,6 +273,8 @@ void cell_residual(const Problem& pb, bool solid, bool outflow, const uint8_t* m
   T* Ru = R + NQ2 * D;
   T* Rp = R + 2 * NQ2 * D;
   const double dtt = P.dt * P.theta;
+  const bool prev = P.theta != 1.0;           // previous-level terms present
+  const double dto = P.dt * (1.0 - P.theta);
 
   for (int q = 0; q < pb.nqp; ++q) {
     const double* N = &pb.Nq[q * NQ2];
@@ -297,6 +304,22 @@ void cell_residual(const Problem& pb, bool solid, bool outflow, const uint8_t* m
     for (int i = 0; i < D; ++i) for (int j = 0; j < D; ++j) F.a[i][j] = Gu.a[i][j] + (i == j ? 1.0 : 0.0);
     T J = det<T, D>(F);
     if (value_of(J) < *minJ) *minJ = value_of(J);
+    // previous time level (theta < 1): gradients, F_old, J_old
+    Mat<double, D> Gvo, Fo;
+    double Jo = 1.0;
+    if (prev) {
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          double gv = 0.0, gu = 0.0;
+          for (int a = 0; a < NQ2; ++a) {
+            gv += dN[a * D + j] * Vold[a * D + i];
+            gu += dN[a * D + j] * Uold[a * D + i];
+          }
+          Gvo.a[i][j] = gv;
+          Fo.a[i][j] = gu + (i == j ? 1.0 : 0.0);
+        }
+      Jo = det<double, D>(Fo);
+    }
     if (!solid) {
       Mat<T, D> Fi = inverse<T, D>(F, J);
       T p = zero;
@@ -322,6 +345,27 @@ void cell_residual(const Problem& pb, bool solid, bool outflow, const uint8_t* m
         T s = zero;
         for (int k = 0; k < D; ++k) s += (A.a[i][k] + A.a[k][i]) * Fi.a[j][k];   // (sigma F^-T)_ij = sum_k sigma_ik F^-1_jk
         f1[i][j] = (dtt * mu) * (J * s) - (J * p) * Fi.a[j][i];
+      }
+      if (prev) {
+        // J^theta (v - v_old) instead of J (v - v_old), and the previous level's
+        // convection rho_f J_old A_old v_old and viscous stress J_old sigma_v,old F_old^-T
+        Mat<double, D> Fio = inverse<double, D>(Fo, Jo), Ao;
+        for (int i = 0; i < D; ++i) for (int j = 0; j < D; ++j) {
+          double s = 0.0;
+          for (int k = 0; k < D; ++k) s += Gvo.a[i][k] * Fio.a[k][j];
+          Ao.a[i][j] = s;
+        }
+        for (int i = 0; i < D; ++i) {
+          double co = 0.0;
+          for (int j = 0; j < D; ++j) co += Ao.a[i][j] * vo[j];
+          const T dv = v[i] - vo[i];
+          f0[i] = f0[i] + (P.rho_f * (1.0 - P.theta)) * (dv * Jo - dv * J) + P.rho_f * dto * Jo * co;
+        }
+        for (int i = 0; i < D; ++i) for (int j = 0; j < D; ++j) {
+          double s = 0.0;
+          for (int k = 0; k < D; ++k) s += (Ao.a[i][k] + Ao.a[k][i]) * Fio.a[j][k];
+          f1[i][j] = f1[i][j] + dto * mu * Jo * s;
+        }
       }
       // incompressibility g0 = J tr(A)
       T trA = zero;
@@ -370,6 +414,27 @@ void cell_residual(const Problem& pb, bool solid, bool outflow, const uint8_t* m
         f0[i] = P.rho_s * (v[i] - vo[i]);
         k0[i] = (u[i] - uo[i]) - dtt * v[i];
       }
+      if (prev) {
+        // previous level: dt (1-theta) F_old Sigma_old and dt (1-theta) v_old
+        Mat<double, D> Eo, So;
+        for (int i = 0; i < D; ++i) for (int j = 0; j < D; ++j) {
+          double s = 0.0;
+          for (int k = 0; k < D; ++k) s += Fo.a[k][i] * Fo.a[k][j];
+          Eo.a[i][j] = 0.5 * (s - (i == j ? 1.0 : 0.0));
+        }
+        double trEo = 0.0;
+        for (int i = 0; i < D; ++i) trEo += Eo.a[i][i];
+        for (int i = 0; i < D; ++i) for (int j = 0; j < D; ++j)
+          So.a[i][j] = 2.0 * P.mu_s * Eo.a[i][j] + (i == j ? P.lambda_s * trEo : 0.0);
+        for (int i = 0; i < D; ++i) {
+          for (int j = 0; j < D; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < D; ++k) s += Fo.a[i][k] * So.a[k][j];
+            f1[i][j] = f1[i][j] + dto * s;
+          }
+          k0[i] = k0[i] - dto * vo[i];
+        }
+      }
       for (int a = 0; a < NQ2; ++a) {
         for (int i = 0; i < D; ++i) {
           T& r = Rv[a * D + i];
@@ -406,10 +471,39 @@ void cell_residual(const Problem& pb, bool solid, bool outflow, const uint8_t* m
         for (int k = 0; k < D; ++k) s += Gv.a[k][j] * Fi.a[0][k];
         t[j] = s;
       }
+      // previous level: -dt (1-theta) <rho_f nu_f J_old F_old^-T grad(v_old)^T F_old^-T n, phi>
+      double bo[D];
+      for (int i = 0; i < D; ++i) bo[i] = 0.0;
+      if (prev) {
+        Mat<double, D> Gvo, Fo;
+        for (int i = 0; i < D; ++i) for (int j = 0; j < D; ++j) {
+          double gv = 0.0, gu = 0.0;
+          for (int a = 0; a < NQ2; ++a) {
+            gv += dN[a * D + j] * Vold[a * D + i];
+            gu += dN[a * D + j] * Uold[a * D + i];
+          }
+          Gvo.a[i][j] = gv;
+          Fo.a[i][j] = gu + (i == j ? 1.0 : 0.0);
+        }
+        const double Jo = det<double, D>(Fo);
+        Mat<double, D> Fio = inverse<double, D>(Fo, Jo);
+        double to[D];
+        for (int j = 0; j < D; ++j) {
+          double s = 0.0;
+          for (int k = 0; k < D; ++k) s += Gvo.a[k][j] * Fio.a[0][k];
+          to[j] = s;
+        }
+        for (int i = 0; i < D; ++i) {
+          double s = 0.0;
+          for (int j = 0; j < D; ++j) s += Fio.a[j][i] * to[j];
+          bo[i] = -dto * mu * Jo * s;
+        }
+      }
       for (int i = 0; i < D; ++i) {
         T b = zero;
         for (int j = 0; j < D; ++j) b += Fi.a[j][i] * t[j];
         T c = (-dtt * mu) * (J * b);
+        if (prev) c = c + bo[i];
         for (int a = 0; a < NQ2; ++a)
           if (N[a] != 0.0) axpy(Rv[a * D + i], w * N[a], c);
       }
@@ -752,7 +846,7 @@ struct fsigen_params {
 
 void* fsigen_create(const fsigen_params* in) {
   if (!in || (in->dim != 2 && in->dim != 3)) return nullptr;
-  if (in->theta != 1.0) return nullptr;
+  if (!(in->theta > 0.0 && in->theta <= 1.0)) return nullptr;
   Problem* p = new Problem();
   p->dim = in->dim;
   p->P.dim = in->dim;

@@ -38,7 +38,8 @@ def test_dof_counts(name, expect):
     assert pb.offsets.tolist() == expect
 
 
-@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(2, (6, 4), prev_state="zero"), small(3, (4, 2, 4))])
+@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(2, (6, 4), prev_state="zero"), small(3, (4, 2, 4)),
+                                 small(2, (8, 8), theta=0.5), small(3, (4, 2, 4), theta=0.51)])
 def test_jacobian_matches_central_differences(cfg):
     pb = fsigen.get_problem(cfg)
     U = pb.seeded_state(3, 3e-2)
@@ -177,7 +178,7 @@ def test_pressure_gradient_is_minus_divergence_transpose(cfg):
     assert abs(Bsp + Bps.T).max() <= 1e-13 * abs(Bsp).max()
 
 
-@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(3, (4, 2, 4))])
+@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(3, (4, 2, 4)), small(2, (8, 8), theta=0.5)])
 def test_solid_kinematic_rows(cfg):
     """A_uv = -dt*theta*A_uu on the free kinematic rows (Sec. 4.3 mass identity)."""
     pb = fsigen.get_problem(cfg)
@@ -212,3 +213,42 @@ def test_seeded_state_bounds_and_boundary():
     assert np.max(np.abs(U[on])) <= 1e-15
     b1, b2 = pb.rhs(0), pb.rhs(0)
     assert np.array_equal(b1, b2) and np.all(b1[pb.fixed] == 0)
+
+
+@pytest.mark.parametrize("dim,n", [(2, (8, 8)), (3, (4, 2, 4))])
+@pytest.mark.parametrize("theta", [0.5, 0.51, 0.8])
+def test_theta_scheme_at_rest_reduces_to_the_spatial_operator(dim, n, theta):
+    """With the previous step equal to the state, every time-derivative term
+    vanishes and the theta and (1 - theta) shares of each explicit-in-time term
+    add up to one: R_theta(U, U) = R_1(U, U) for any theta (a missing or
+    mis-weighted previous-level term breaks this)."""
+    U = fsigen.get_problem(small(dim, n)).seeded_state(4, 3e-2)
+    R1 = fsigen.get_problem(small(dim, n)).residual(U, U.copy())
+    Rt = fsigen.get_problem(small(dim, n, theta=theta)).residual(U, U.copy())
+    assert np.linalg.norm(Rt - R1) <= 1e-12 * np.linalg.norm(R1)
+
+
+@pytest.mark.parametrize("dim,n", [(2, (8, 8)), (3, (4, 2, 4))])
+def test_theta_scheme_jacobian_is_affine_in_theta_at_rest(dim, n):
+    """At U = U_old the Jacobian is J_1 - (1 - theta) K with K the spatial part,
+    so J_0.5 - J_1 = 2 (J_0.75 - J_1), and the two differ (K != 0)."""
+    U = fsigen.get_problem(small(dim, n)).seeded_state(4, 3e-2)
+    J = {t: fsigen.get_problem(small(dim, n, theta=t)).jacobian(U, U.copy()) for t in (1.0, 0.75, 0.5)}
+    d1 = J[0.5] - J[1.0]
+    d2 = J[0.75] - J[1.0]
+    assert np.linalg.norm(d1 - 2.0 * d2) <= 1e-12 * np.linalg.norm(d1)
+    assert np.linalg.norm(d1) > 1e-3 * np.linalg.norm(J[1.0])
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.8])
+def test_theta_scheme_moving_previous_step(theta):
+    """With U_old != U the previous level contributes: R_theta(U, U_old) differs
+    from R_1 by (1 - theta) times the change of the explicit-in-time terms, i.e.
+    R_theta is affine in theta at any (U, U_old)."""
+    pbs = {t: fsigen.get_problem(small(2, (8, 8), theta=t)) for t in (1.0, theta, 0.5 * (1.0 + theta))}
+    U = pbs[1.0].seeded_state(4, 3e-2)
+    Uold = 0.5 * U
+    R = {t: pb.residual(U, Uold) for t, pb in pbs.items()}
+    mid = 0.5 * (1.0 + theta)
+    assert np.linalg.norm(R[theta] - 2.0 * R[mid] + R[1.0]) <= 1e-11 * np.linalg.norm(R[1.0])
+    assert np.linalg.norm(R[theta] - R[1.0]) > 1e-6 * np.linalg.norm(R[1.0])

@@ -251,6 +251,40 @@ def test_edge_cases(torch_cuda):
     gw.close(); gn.close()
 
 
+@pytest.mark.parametrize("name,theta", [("2d_16x16", 0.5), ("3d_8x4x4", 0.51)])
+def test_theta_scheme_parity(name, theta, torch_cuda):
+    """Jacobians of the theta scheme (Crank-Nicolson, shifted): with
+    dt_theta = dt*theta in both, P^-1 in FP64 matches the oracle to 1e-11 and the
+    FP64 solve to 1e-8 within one iteration; the FP32-AMG form meets the residual."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    cfg0, mr = CASES[name]
+    cfg = cfg0.with_(theta=theta)
+    s = fsigen.make_system(cfg)
+    c = cfg.dt * cfg.theta
+    o = oracle.OracleSolver.from_system(s, params=oracle.PrecondParams(mass_ratio=mr, dt_theta=c))
+    ref = o.solve(s.rhs)
+    b = torch.tensor(s.rhs, device="cuda")
+    for prec in ("fp64", "fp32"):
+        g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr, dt_theta=c,
+                                                               flags=P.FSI_USE_GRAPHS))
+        g.precond_build(prec)
+        if prec == "fp64":
+            r = np.random.default_rng(3).standard_normal(s.n)
+            rt = torch.tensor(r, device="cuda")
+            zt = torch.zeros_like(rt)
+            g.apply_block("precond", rt, zt)
+            assert rel(zt.cpu().numpy(), o.P(r)) <= 1e-11
+        x = torch.zeros_like(b)
+        st = g.solve(b, x, 1e-8)
+        g.close()
+        xc = x.cpu().numpy()
+        assert st.status == 0
+        assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.001
+        if prec == "fp64":
+            assert abs(st.iters - ref.iters) <= 1 and rel(xc, ref.x) <= 1e-8
+
+
 @pytest.mark.parametrize("variant", ["lower", "upper", "diag"])
 @pytest.mark.parametrize("name", ["2d_37x19_ragged", "3d_8x4x4"])
 def test_block_factorisation_variants(name, variant, torch_cuda):

@@ -287,3 +287,22 @@ def test_block_variants_converge_with_amg_subsolves(variant):
     o = oracle.OracleSolver.from_system(s, oracle.PrecondParams(mass_ratio=8.0, variant=variant))
     r = o.solve(s.rhs, tol=1e-8, restart=200)
     assert r.converged and r.true_relres <= 1e-8
+
+
+@pytest.mark.parametrize("dim,theta", [(2, 0.5), (3, 0.51)])
+def test_theta_scheme_systems_solve(dim, theta):
+    """Crank-Nicolson (theta = 1/2) and shifted theta systems: the solid Schur
+    coupling identity holds with c = dt*theta, and FGMRES with Alg. 2 reaches the
+    tolerance when the preconditioner uses that c."""
+    base = fsigen.CONFIGS["2d_tiny"].with_(name="cn2", n=(8, 8)) if dim == 2 else \
+        fsigen.CONFIGS["3d"].with_(name="cn3", n=(4, 2, 4))
+    cfg = base.with_(theta=theta)
+    s = fsigen.make_system(cfg)
+    prm = oracle.PrecondParams(mass_ratio=8.0 if dim == 2 else 20.0, dt_theta=cfg.dt * cfg.theta)
+    pre = oracle.BlockLDU(s.scipy(), s.offsets, dim, params=prm)
+    B = pre.B
+    fixed_u = s.fixed[B.su]
+    D = (B.A_uv + prm.dt_theta * B.A_uu).tocsr()
+    assert abs(D[~fixed_u]).max() <= 1e-12 * abs(B.A_uu[~fixed_u]).max()
+    r = oracle.OracleSolver.from_system(s, prm).solve(s.rhs, tol=1e-8)
+    assert r.converged and r.true_relres <= 1e-8
