@@ -98,7 +98,10 @@ class FSIConfig:
     """Mesh, material and seed parameters of one synthetic Jacobian.
 
     Material values are the FSI-2 set of Sec. 6.1 (fluid density 1e3, viscosity
-    1e-3, solid density 1e4, Lame mu 0.5e6, lambda 2e6); backward Euler, dt = 0.01.
+    1e-3, solid density 1e4, Lame mu 0.5e6, lambda 2e6); dt = 0.01 and the theta
+    scheme of Sec. 3.2 with 0 < theta <= 1 (1: backward Euler, the default; 1/2:
+    Crank-Nicolson; 1/2 + dt: shifted).  A solve of such a Jacobian uses
+    dt_theta = dt * theta in its preconditioner.
     """
     name: str
     dim: int
