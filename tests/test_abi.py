@@ -157,3 +157,39 @@ def test_committed_weights_file_is_well_formed():
     bits, si, so = L.read_weights(path)
     assert bits.shape == (L.N_PARAMS,) and np.all(np.isfinite(L.bf16_value(bits)))
     assert np.all(si > 0) and np.all(so > 0)
+
+
+def _header_struct_fields(name):
+    text = open(os.path.join(ROOT, "include", "fsi.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct " + name + r"\s*\{(.*?)\}\s*" + name + ";", text, flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "int presmooth, postsmooth" / "const double* relres_hist" / "float sigma_in[5]"
+        head, *rest = [d.strip() for d in decl.split(",")]
+        fields.append(re.sub(r"\[.*\]", "", head.split()[-1]).lstrip("*"))
+        fields += [re.sub(r"\[.*\]", "", r).lstrip("*") for r in rest]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("fsi_params", "Params"), ("fsi_stats", "Stats")])
+def test_binding_structs_follow_the_header(cname, pyname):
+    """The ctypes mirrors list the C structs' fields in the header's order (a
+    field added to one side only would shift every later field)."""
+    from paper_1801_05648_gb300 import fsi
+    py = [f[0] for f in getattr(fsi, pyname)._fields_]
+    assert py == _header_struct_fields(cname)
+
+
+def test_binding_constants_follow_the_header():
+    """Every FSI_* enumerator of include/fsi.h has the same value in the binding."""
+    from paper_1801_05648_gb300 import fsi
+    text = open(os.path.join(ROOT, "include", "fsi.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(FSI_[A-Z0-9_]+)\s*=\s*(-?\d+)", text))
+    assert len(consts) >= 20
+    for k, v in consts.items():
+        assert getattr(fsi, k) == v, k
