@@ -12,7 +12,7 @@ block, FP64 across blocks): 5e-4 of the largest entry.  Solves with the stage
 reach the 1e-8 relative residual with iterations and accepted corrections within
 +-1 of the oracle's (a decision can only flip at a near-tie of the two residual
 norms); the FP32 MLP steers another Krylov trajectory than the FP64 oracle's,
-so, like the FP32-AMG form, the solution is judged against the manufactured x*:
+so, like the FP32-AMG form, the solution is measured against the manufactured x*:
 within 10x of the FP64 oracle's own error (1e-6 when that is smaller)."""
 import numpy as np
 import pytest
@@ -202,7 +202,7 @@ def test_learned_solve_matches_oracle(name, torch_cuda):
             assert abs(st.iters - ref.iters) <= 1, (tau, st.iters, ref.iters)
             assert abs(st.learned_accepted - ref.accepted) <= 1, (tau, st.learned_accepted, ref.accepted)
             # the FP32 MLP steers another Krylov trajectory than the FP64 oracle's:
-            # judged like the FP32-AMG form, against x*
+            # measured like the FP32-AMG form, against x*
             assert rel(xc, s.x_exact) <= max(10.0 * err64, 1e-6), (rel(xc, s.x_exact), err64)
         if tau == 1.0:
             assert ref.accepted >= 1          # the accept branch ran
