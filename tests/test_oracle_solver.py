@@ -306,3 +306,38 @@ def test_theta_scheme_systems_solve(dim, theta):
     assert abs(D[~fixed_u]).max() <= 1e-12 * abs(B.A_uu[~fixed_u]).max()
     r = oracle.OracleSolver.from_system(s, prm).solve(s.rhs, tol=1e-8)
     assert r.converged and r.true_relres <= 1e-8
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_restarted_fgmres_cycles_are_krylov_minimisers(m):
+    """Restarted FGMRES (Saad Alg. 9.6 with restart m) against what each cycle must
+    return: with a fixed (linear) preconditioner M, cycle c moves x_c to the
+    minimiser of ||b - A x|| over x_c + M K_m(A M, r_c), r_c = b - A x_c, computed
+    here by least squares on an explicit (orthonormalised) Krylov basis; m = 1 is
+    the minimal-residual step x + alpha M r.  Four cycles, so the update
+    x = x_0 + Z y and the restart from the true residual are both exercised."""
+    s = tiny(2)
+    A = s.scipy()
+    pre = oracle.BlockLDU(A, s.offsets, 2, params=params(2))
+    b = s.rhs
+    x = np.zeros(s.n)
+    for c in range(4):
+        r = b - A @ x
+        K = [r / np.linalg.norm(r)]
+        for _ in range(m - 1):
+            K.append(A @ pre(K[-1]))
+            K[-1] = K[-1] / np.linalg.norm(K[-1])
+        Q, _ = np.linalg.qr(np.column_stack(K))
+        Z = np.column_stack([pre(q) for q in Q.T])
+        y, *_ = np.linalg.lstsq(A @ Z, r, rcond=None)
+        x = x + Z @ y
+        res = fgmres(lambda v: A @ v, pre, b, tol=1e-30, restart=m, maxit=(c + 1) * m)
+        assert res.cycles == c + 1 and res.iters == (c + 1) * m
+        assert np.linalg.norm(res.x - x) <= 1e-7 * np.linalg.norm(x), c
+        # the residual estimate at the end of the cycle is the true residual of the update
+        true = np.linalg.norm(b - A @ res.x) / np.linalg.norm(b)
+        assert res.history[-1] == pytest.approx(true, rel=1e-6)
+    # restarting never increases the residual (each cycle minimises over a space containing 0)
+    ends = [np.linalg.norm(b - A @ fgmres(lambda v: A @ v, pre, b, tol=1e-30, restart=m, maxit=k * m).x)
+            for k in range(1, 5)]
+    assert np.all(np.diff(ends) <= 1e-12 * ends[0])
