@@ -25,6 +25,9 @@
  *     PyTorch tensors) and must stay valid during the call; the library works on
  *     the stream given to fsi_setup and returns after that stream has finished
  *     the call's work.
+ *   - A context belongs to the CUDA device that is current when fsi_setup is
+ *     called; the other calls taking a context switch to that device for their
+ *     duration and restore the caller's current device before they return.
  *   - Every call returns FSI_OK (0) or a negative FSI_E* code; fsi_last_error()
  *     gives the message of the last failure on that context.  No call aborts the
  *     process.  Device memory the library allocates is released by fsi_free().
@@ -266,12 +269,13 @@ int fsi_amg_export(fsi_ctx* ctx, int which, int level, int what, void* dst);
  * Allocates nothing: its two scratch vectors live in a static device array of
  * 2 x 2^20 doubles (16 MiB) that every GPU loading the library keeps until the
  * process exits, so the solid block may have at most 2^20 displacement DOFs
- * (larger blocks return FSI_EINVAL).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the array: calls whose work overlaps on the
- * GPU (other streams or devices' contexts on the same device) race on it.  Its
- * contents are fully overwritten by each call before they are read.  Enqueued on
- * the context's stream without waiting.
+ * (larger blocks return FSI_EINVAL).  The first call on a context looks up the
+ * array's device address on the context's device (cudaGetSymbolAddress) and
+ * keeps it with the context; make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (other streams,
+ * or other contexts on the same device) race on it.  Its contents are fully
+ * overwritten by each call before they are read.  Enqueued on the context's
+ * stream without waiting.
  */
 int fsi_mass_solve_noalloc(fsi_ctx* ctx, const double* in_dev, double* out_dev);
 

@@ -64,6 +64,28 @@ inline void require(bool ok, const std::string& msg) {
   if (!ok) throw Error(EINVAL_, msg);
 }
 
+// Makes `dev` the calling thread's current CUDA device while the guard lives and
+// restores the previous device afterwards (nothing to do when dev < 0 or when it
+// is current already).  A context's streams and memory belong to the device that
+// was current at fsi_setup; every entry point runs under a guard for it, so a
+// caller whose thread has since switched devices still launches on the right one.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (dev < 0) return;
+    int cur = -1;
+    FSI_CUDA(cudaGetDevice(&cur));
+    if (cur == dev) return;
+    FSI_CUDA(cudaSetDevice(dev));
+    prev = cur;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // Owning device buffer.
 template <class T>
 struct DBuf {

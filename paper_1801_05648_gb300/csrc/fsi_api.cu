@@ -26,6 +26,7 @@ template <class F>
 int guarded(fsi_ctx* ctx, F&& f) {
   std::string& err = ctx ? ctx->C.err : g_setup_error;
   try {
+    fsi::DeviceGuard on_device(ctx ? ctx->C.device : -1);
     f();
     err.clear();
     return FSI_OK;

@@ -8,8 +8,6 @@
 #include "../../include/fsi.h"
 #include "solver.cuh"
 
-#include <mutex>
-
 namespace {
 
 // Scratch of the entry point: two FP64 vectors (ping-pong iterate and Chebyshev
@@ -18,25 +16,20 @@ namespace {
 constexpr int64_t kNoAllocMaxRows = int64_t(1) << 20;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxRows];
 
-constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
-// Device address of g_noalloc_scratch on the current device, looked up once per
-// device.  (In host code the array's name is only a host-side stand-in.)
-int scratch_address(double** out, std::string& err) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) { err = cudaGetErrorString(e); return FSI_ECUDA; }
-  if (dev < 0 || dev >= kMaxDevices) { err = "device index out of range"; return FSI_EINVAL; }
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+// Device address of g_noalloc_scratch on the context's device (which the caller
+// has made current).  In host code the array's name is only a host-side stand-in,
+// not a device address.  The address is looked up on the first call on a context
+// and kept with that context: a context lives inside one CUDA context of one
+// device, so the address stays valid for as long as the context does (a device
+// reset invalidates both together, and contexts made afterwards look it up anew).
+int scratch_address(fsi::Context& C, double** out, std::string& err) {
+  if (!C.noalloc_scratch) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) { err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e); return FSI_ECUDA; }
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    C.noalloc_scratch = p;
   }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(C.noalloc_scratch);
   return FSI_OK;
 }
 
@@ -58,9 +51,10 @@ extern "C" int fsi_mass_solve_noalloc(fsi_ctx* ctx, const double* in_dev, double
               " displacement DOFs, more than the static scratch holds (" + std::to_string(kNoAllocMaxRows) + ")";
       return FSI_EINVAL;
     }
+    fsi::DeviceGuard on_device(C.device);
     double* scratch = nullptr;
     std::string err;
-    const int rc = scratch_address(&scratch, err);
+    const int rc = scratch_address(C, &scratch, err);
     if (rc != FSI_OK) { C.err = err; return rc; }
     // xb = scratch[0, n), d = scratch[max, max + n); the first Chebyshev step
     // overwrites both, so nothing needs clearing between calls.

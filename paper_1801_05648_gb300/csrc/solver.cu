@@ -416,6 +416,7 @@ void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, con
                    const double* solid_coords) {
   SetupPhase setup_phase;
   auto t0 = clk::now();
+  FSI_CUDA(cudaGetDevice(&C.device));
   FSI_CUDA(cudaStreamCreateWithFlags(&C.s2, cudaStreamNonBlocking));
   FSI_CUDA(cudaEventCreateWithFlags(&C.ev_fork, cudaEventDisableTiming));
   FSI_CUDA(cudaEventCreateWithFlags(&C.ev_join, cudaEventDisableTiming));

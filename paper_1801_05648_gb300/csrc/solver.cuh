@@ -54,6 +54,8 @@ struct PrecWork {
 struct Context {
   cudaStream_t s = nullptr;
   bool own_stream = false;
+  int device = -1;                        // CUDA device current at fsi_setup; every entry point runs on it
+  void* noalloc_scratch = nullptr;        // device address of the no-allocation entry point's scratch array
   cudaStream_t s2 = nullptr;              // second branch of Alg. 2 (mesh solve next to the solid solve)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int dim = 2;

@@ -169,11 +169,15 @@ def _np_ptr(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
-def _dev_ptr(t, dtype=None):
+def _dev_ptr(t, n=None, dtype=None):
+    """Device address of a contiguous CUDA tensor holding at least n entries
+    (the library reads or writes n of them; a shorter tensor would be overrun)."""
     import torch
     dtype = torch.float64 if dtype is None else dtype
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
         raise TypeError(f"expected a contiguous {dtype} CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"tensor has {t.numel()} entries, the call needs {n}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -230,7 +234,7 @@ class FSISolver:
     def solve(self, rhs, x, rtol=1e-8, raise_on_error=True) -> SolveStats:
         self._order()
         st = Stats()
-        rc = self._lib.fsi_solve(self._h, _dev_ptr(rhs), _dev_ptr(x), rtol, ctypes.byref(st))
+        rc = self._lib.fsi_solve(self._h, _dev_ptr(rhs, self.n), _dev_ptr(x, self.n), rtol, ctypes.byref(st))
         hist = [st.relres_hist[i] for i in range(st.hist_len)] if st.hist_len else []
         out = SolveStats(st.iters, st.cycles, st.status, st.true_relres, st.setup_s, st.precond_build_s,
                          st.solve_s, st.operator_bytes, st.precond_bytes, hist, st.kernel_launches,
@@ -242,24 +246,36 @@ class FSISolver:
     def apply_operator(self, x, y, sync=True):
         """y = A x (enqueued on the solver's stream; waits for it unless sync=False)."""
         self._order()
-        self._check(self._lib.fsi_apply_operator(self._h, _dev_ptr(x), _dev_ptr(y)))
+        self._check(self._lib.fsi_apply_operator(self._h, _dev_ptr(x, self.n), _dev_ptr(y, self.n)))
         if sync:
             self._sync()
 
     def apply_block(self, which, inp, out, sync=True):
         w = BLOCKS.get(which, which)
+        n = self.block_size(w)
         self._order()
-        self._check(self._lib.fsi_apply_block(self._h, int(w), _dev_ptr(inp), _dev_ptr(out)))
+        self._check(self._lib.fsi_apply_block(self._h, int(w), _dev_ptr(inp, n), _dev_ptr(out, n)))
         if sync:
             self._sync()
 
     def _sync(self):
         self.stream.synchronize()
 
+    def block_size(self, which) -> int:
+        """Entries of the vectors fsi_apply_block(which) reads and writes (see BLOCKS)."""
+        o = [int(v) for v in self.offsets]
+        sizes = {0: o[1] - o[0], 1: o[2] - o[1], 2: o[4] - o[3], 3: o[5] - o[4], 4: o[3] - o[2],
+                 5: o[3] - o[1], 6: o[5] - o[3], 7: self.n}
+        w = BLOCKS.get(which, which)
+        if w not in sizes:
+            raise ValueError(f"unknown block {which!r}")
+        return sizes[w]
+
     def mass_solve_noalloc(self, inp, out, sync=True):
         """A_uu^-1 in through fsi_mass_solve_noalloc (static device scratch, no allocation)."""
         self._order()
-        self._check(self._lib.fsi_mass_solve_noalloc(self._h, _dev_ptr(inp), _dev_ptr(out)))
+        n = self.block_size("solid_mass")
+        self._check(self._lib.fsi_mass_solve_noalloc(self._h, _dev_ptr(inp, n), _dev_ptr(out, n)))
         if sync:
             self._sync()
 
@@ -343,7 +359,7 @@ class FSISolver:
         if r.numel() != self.n or c.numel() != self.n:
             raise ValueError("r and c must have n entries")
         self._order()
-        self._check(self._lib.fsi_learned_apply(self._h, _dev_ptr(r), _dev_ptr(c)))
+        self._check(self._lib.fsi_learned_apply(self._h, _dev_ptr(r, self.n), _dev_ptr(c, self.n)))
         if sync:
             self._sync()
 
@@ -356,14 +372,15 @@ class FSISolver:
         if r.numel() != self.n or feat.numel() < nn * FSI_MLP_INPUTS or rho.numel() < nn:
             raise ValueError("r needs n entries, feat n_nodes x 53 and rho n_nodes")
         self._order()
-        self._check(self._lib.fsi_learned_features(self._h, _dev_ptr(r), _dev_ptr(feat, torch.float32),
-                                                   _dev_ptr(rho, torch.float32)))
+        self._check(self._lib.fsi_learned_features(self._h, _dev_ptr(r, self.n),
+                                                   _dev_ptr(feat, nn * FSI_MLP_INPUTS, torch.float32),
+                                                   _dev_ptr(rho, nn, torch.float32)))
         if sync:
             self._sync()
 
     def set_harvest(self, buf=None, nvec=0):
         """Store r'_j = v_j - A P^-1 v_j of the first nvec iterations of later solves into buf [nvec, n]."""
-        ptr = None if buf is None else _dev_ptr(buf)
+        ptr = None if buf is None else _dev_ptr(buf, int(nvec) * self.n)
         if buf is not None and (buf.dim() != 2 or buf.shape[0] < nvec or buf.shape[1] != self.n):
             raise ValueError("buf must be [>= nvec, n]")
         self._keep_harvest = buf
@@ -424,7 +441,7 @@ class Trainer:
             raise ValueError("r' must have n entries")
         loss = ctypes.c_double()
         solver._order()
-        rc = self._lib.fsi_trainer_step(self._h, solver._h, _dev_ptr(rprime), ctypes.byref(loss))
+        rc = self._lib.fsi_trainer_step(self._h, solver._h, _dev_ptr(rprime, solver.n), ctypes.byref(loss))
         solver._check(rc)
         return loss.value
 
@@ -434,7 +451,8 @@ class Trainer:
             raise ValueError("r' must have n entries")
         loss = ctypes.c_double()
         solver._order()
-        solver._check(self._lib.fsi_trainer_loss(self._h, solver._h, _dev_ptr(rprime), ctypes.byref(loss)))
+        solver._check(self._lib.fsi_trainer_loss(self._h, solver._h, _dev_ptr(rprime, solver.n),
+                                                 ctypes.byref(loss)))
         return loss.value
 
     def update(self, solver: FSISolver, lr: float = 0.0):
