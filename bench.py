@@ -410,6 +410,10 @@ def bench_ours(args):
     n_states = args.states or DEFAULT_STATES.get(args.workload, 1)
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
+    # measured FMA rates of this GPU (the pipes that bound the FP64 operator and the FP32 MLP)
+    fma64, _ = P.probe_fma_rate(64, iters=8192, reps=5)
+    fma32, _ = P.probe_fma_rate(32, iters=131072, reps=5)
+
     W = Workload(args.workload, replica_seeds(rank, n_states), flags, knobs, bs, dev)
     S = len(W.solvers)
     n = W.n
@@ -478,7 +482,7 @@ def bench_ours(args):
         bs.synchronize()
         mlp_s = e0.elapsed_time(e1) / reps / 1e3
         mlp_flops = nd.shape[0] * 2.0 * (53 * 64 + 64 * 64 + 64 * 5)
-        fp32_peak = num_sms * 128 * 2 * ((clocks or {}).get("sm_max_mhz") or 2070) * 1e6 / 1e12
+        fp32_peak = 2.0 * fma32 / 1e12
         mlp_traffic = kernel_traffic(f"mlp_apply_{args.workload}.md", ["paper_1801_05648_gb300/csrc/learned.cu",
                                                                      "paper_1801_05648_gb300/csrc/learned.cuh"])
         learned = form_summary(ms_l, st_l, {
@@ -489,7 +493,7 @@ def bench_ours(args):
             "roofline_mlp": {"kernel": "k_mlp<MODE_APPLY>: patch gather + 53-64-64-5 MLP (bfloat16 weights, "
                                        "FP32 FMA) + scatter", "bound": "alu",
                              "achieved": mlp_flops / mlp_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                             "peak_kind": f"FP32 FMA: {num_sms} SMs x 128 lanes x 2 FLOP x max SM clock",
+                             "peak_kind": "measured FP32 FMA rate x 2 (fsi_probe_fma_rate)",
                              "frac": mlp_flops / mlp_s / 1e12 / fp32_peak, "launch_us": mlp_s * 1e6,
                              "flops_per_launch": mlp_flops, "traffic": mlp_traffic}})
 
@@ -531,6 +535,7 @@ def bench_ours(args):
     spmv_s = e0.elapsed_time(e1) / reps / 1e3
     op_bytes = st[0].operator_bytes
     achieved = op_bytes / spmv_s / 1e9
+    op_fmas = float(W.systems[0].vals.size)     # one FMA per stored entry of the monolithic operator
     peak, peak_kind = measured_peak()
     traffic = kernel_traffic(f"spmv_outer_fp64_{args.workload}.md", SPMV_SRCS)
     cheb_traffic = kernel_traffic(f"spmv_cheb_fp32_{args.workload}.md", SPMV_SRCS)
@@ -674,7 +679,13 @@ def bench_ours(args):
                                           "pressure rows)",
                                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                 "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": op_bytes,
-                                "launch_us": spmv_s * 1e6},
+                                "launch_us": spmv_s * 1e6,
+                                "fp64_pipe": {"fmas_per_launch": op_fmas, "achieved_fma_per_s": op_fmas / spmv_s,
+                                              "peak_fma_per_s": fma64, "frac": op_fmas / spmv_s / fma64,
+                                              "peak_kind": "measured FP64 FMA rate (fsi_probe_fma_rate)"}},
+        "measured_fma_rates": {"fp64_fma_per_s": fma64, "fp32_fma_per_s": fma32,
+                               "how": "fsi_probe_fma_rate: 8 independent FMA chains per thread, 8 CTAs of 256 "
+                                      "threads per SM, best of 5 launches"},
         "secondary": secondary,
         "err_vs_oracle": oracle_err,
         "cpu_baseline": cpu,

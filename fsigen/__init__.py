@@ -85,6 +85,8 @@ def _load():
             lib.fsigen_num_threads.restype = ctypes.c_int
             lib.fsigen_node_map.argtypes = [vp, i32p, i32p]
             lib.fsigen_node_map.restype = ctypes.c_int
+            lib.fsigen_cell_map.argtypes = [vp, i32p, ctypes.POINTER(ctypes.c_uint32)]
+            lib.fsigen_cell_map.restype = None
             _lib = lib
     return _lib
 
@@ -253,6 +255,19 @@ class Problem:
         if rc != 0:
             raise ValueError("node_map: 2D problems only")
         return nd, pt
+
+    def cell_map(self):
+        """(cell_dof [cells, NL] int32, cell_flags [cells] uint32): per cell (lexicographic,
+        direction 0 fastest) the global DOF of each element DOF (v of Q2 node a comp i at
+        a*dim + i, u at NQ2*dim + a*dim + i, p of Q1 vertex P at 2*NQ2*dim + P) and the
+        flags bit 0 solid, bit 1 outflow-face fluid cell, bit 2 + a node a outside the
+        closed solid region.  The mesh description a device assembler consumes."""
+        n_cells = int(np.prod(self.cfg.n[:self.dim]))
+        nl = 40 if self.dim == 2 else 170
+        cd = np.empty((n_cells, nl), np.int32)
+        cf = np.empty(n_cells, np.uint32)
+        _load().fsigen_cell_map(self._h, _ptr(cd, ctypes.c_int32), _ptr(cf, ctypes.c_uint32))
+        return cd, cf
 
     def solid_node_coords(self) -> np.ndarray:
         """Coordinates of the s_v nodes (one row per node, s_v node order)."""

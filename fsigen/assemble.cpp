@@ -973,6 +973,29 @@ int fsigen_node_map(void* h, int32_t* node_dof, int32_t* patch) {
   return 0;
 }
 
+// Per cell (lexicographic, direction 0 fastest): the global DOF of each local DOF
+// in the element layout of cell_residual (v of Q2 node a comp i at a*dim + i, u at
+// NQ2*dim + a*dim + i, p of Q1 vertex P at 2*NQ2*dim + P), and flags: bit 0 solid
+// cell, bit 1 fluid cell on the outflow face x_0 = L_0, bit 2 + a local Q2 node a
+// outside the closed solid region (carries a mesh-motion row).  This is the mesh
+// description a device assembler needs; it holds no residual arithmetic.
+void fsigen_cell_map(void* h, int32_t* cell_dof, uint32_t* cell_flags) {
+  Problem* p = static_cast<Problem*>(h);
+  const int D = p->dim;
+  const int NL = p->nloc, NQ2 = p->nq2loc, NQ1 = p->nq1loc;
+  std::vector<int64_t> gdof(NL), q2n(NQ2), q1n(NQ1);
+  for (int64_t cidx = 0; cidx < p->n_cells; ++cidx) {
+    int c[3] = {0, 0, 0}; unflatten(cidx, p->P.n, D, c);
+    cell_dofs(*p, c, gdof.data(), q2n.data(), q1n.data());
+    for (int k = 0; k < NL; ++k) cell_dof[cidx * NL + k] = (int32_t)gdof[k];
+    const bool solid = p->cell_solid[cidx];
+    uint32_t f = solid ? 1u : 0u;
+    if (!solid && c[0] == p->P.n[0] - 1) f |= 2u;
+    for (int a = 0; a < NQ2; ++a) if (!p->node_solid[q2n[a]]) f |= 1u << (2 + a);
+    cell_flags[cidx] = f;
+  }
+}
+
 int fsigen_num_threads() {
 #ifdef _OPENMP
   return omp_get_max_threads();

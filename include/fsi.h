@@ -159,7 +159,10 @@ void fsi_default_params(fsi_params* p, int dim);
  *   dim            2 or 3
  *   n              number of unknowns (= block_offsets[5])
  *   rowptr/colind/vals   host CSR, n+1 / nnz / nnz entries (deep-copied; the
- *                  caller may free them after return)
+ *                  caller may free them after return).  vals may be NULL: the
+ *                  pattern only, with the values supplied later from device
+ *                  memory by fsi_update_values (e.g. a Jacobian assembled on the
+ *                  device by fsi_asm_jacobian)
  *   block_offsets  host, 6 entries: start of m, s_v, s_u, f_v, f_p, and n;
  *                  non-decreasing, vector classes multiples of dim, |s_v| = |s_u|
  *   node_coords    host, nullable: dim coordinates per s_v node (rigid-body
@@ -278,6 +281,84 @@ int fsi_amg_export(fsi_ctx* ctx, int which, int level, int what, void* dst);
  * stream without waiting.
  */
 int fsi_mass_solve_noalloc(fsi_ctx* ctx, const double* in_dev, double* out_dev);
+
+/*
+ * fsi_update_values - replace the operator's values by a new Jacobian on the
+ * same pattern, without a host round trip (Alg. 1, Sec. 3.3: a Newton step
+ * re-assembles the Jacobian, the pattern stays).
+ *   vals_dev  device, one double per stored entry of the CSR given to fsi_setup
+ *             (same order); read during the call only
+ * Re-extracts every class block on the device and drops the preconditioner:
+ * fsi_precond_build must be called again before the next solve (FSI_EINVAL
+ * otherwise).  The learned stage's node map and weights are kept.
+ */
+int fsi_update_values(fsi_ctx* ctx, const double* vals_dev);
+
+/* ------------------------------------------------------------------------
+ * Residual and Jacobian assembly on the device (Alg. 1, Sec. 3.3; variational
+ * form Eq. (fsi:all), Sec. 3.2-3.3, strong form Sec. 2) for structured box meshes
+ * of Q2 velocity, Q2 displacement and continuous Q1 pressure: the Newton loop of
+ * the time step then runs without host assembly.  The residual is
+ *   fluid cells  (rho_f J (v - v_old), phi) - (rho_f J grad(v) F^-1 (u - u_old), phi)
+ *                + dt theta [(rho_f J grad(v) F^-1 v, phi) + (J sigma_v F^-T, grad phi)]
+ *                + (J (-p) F^-T, grad phi) + (J tr(grad(v) F^-1), psi)
+ *                + (grad(u) / J, grad phi) on the mesh-motion rows
+ *                - dt theta <rho_f nu_f J F^-T grad(v)^T F^-T e_0, phi> on the outflow face
+ *   solid cells  (rho_s (v - v_old), phi) + dt theta (F Sigma, grad phi)
+ *                + (u - u_old - dt theta v, phi) on the displacement rows
+ * with F = I + grad u, J = det F, sigma_v = rho_f nu_f (grad v F^-1 + F^-T grad v^T),
+ * Sigma = 2 mu_s E + lambda_s tr(E) I, E = (F^T F - I)/2; for theta < 1 the
+ * previous level adds its dt (1 - theta) share of the convection, viscous,
+ * outflow and solid stress terms and of the kinematic velocity, and the fluid
+ * time derivative carries theta J + (1 - theta) J_old.  3^dim Gauss points per
+ * cell, 3^(dim-1) on the outflow face.  The Jacobian is the exact derivative of
+ * this discrete residual (dual numbers).  Fixed rows: residual 0, Jacobian row =
+ * the identity entry.
+ */
+typedef struct fsi_asm fsi_asm;
+
+typedef struct fsi_asm_mesh {
+  int dim;                  /* 2 or 3 */
+  int cells[3];             /* cells per direction of the box; cells are numbered
+                               lexicographically, direction 0 fastest */
+  double h[3];              /* cell size per direction */
+  int64_t n;                /* unknowns */
+  const int32_t* cell_dof;  /* host, cells x NL (NL = 40 in 2D, 170 in 3D): global DOF of each local
+                               DOF.  Local order: v of Q2 node a component i at a*dim + i, u at
+                               NQ2*dim + a*dim + i, p of Q1 vertex P at 2*NQ2*dim + P; Q2 nodes
+                               a = a0 + 3 a1 (+ 9 a2) and Q1 vertices P = P0 + 2 P1 (+ 4 P2), each
+                               index running along its direction from the cell's lower corner */
+  const uint32_t* cell_flags; /* host, one per cell: bit 0 solid cell, bit 1 the cell's upper face
+                               in direction 0 is the do-nothing outflow boundary, bit 2 + a local Q2
+                               node a carries a mesh-motion row (lies outside the closed solid) */
+  const int64_t* rowptr;    /* host, n + 1: the Jacobian's CSR pattern (as given to fsi_setup) */
+  const int32_t* colind;    /* host, rowptr[n] sorted column indices */
+  const uint8_t* row_fixed; /* host, n: identity (Dirichlet / inactive pressure) rows */
+} fsi_asm_mesh;
+
+typedef struct fsi_asm_physics {
+  double rho_f, nu_f;       /* fluid density, kinematic viscosity */
+  double mu_s, lambda_s;    /* St. Venant-Kirchhoff Lame parameters */
+  double rho_s;             /* solid density */
+  double dt, theta;         /* time step, theta of the one-step-theta scheme (0 < theta <= 1) */
+} fsi_asm_physics;
+
+/* Copy the mesh tables to the device (host arrays may be freed after return);
+ * cuda_stream as in fsi_setup.  FSI_EINVAL on inconsistent tables. */
+int fsi_asm_create(fsi_asm** out, const fsi_asm_mesh* mesh, const fsi_asm_physics* phys, void* cuda_stream);
+/* R(U) at state U_dev with previous time level Uold_dev (device, n doubles each;
+ * Uold_dev NULL = 0).  R_dev (device, n) is overwritten.  *min_J (nullable): the
+ * smallest det F over the volume quadrature points; *r_absmax (nullable):
+ * max_i |R_i|.  Waits for the stream. */
+int fsi_asm_residual(fsi_asm* a, const double* U_dev, const double* Uold_dev, double* R_dev, double* min_J,
+                     double* r_absmax);
+/* dR/dU at U_dev into vals_dev (device, rowptr[n] doubles, CSR order), which is
+ * overwritten.  FSI_EINVAL if a nonzero falls outside the pattern.  Waits. */
+int fsi_asm_jacobian(fsi_asm* a, const double* U_dev, const double* Uold_dev, double* vals_dev, double* min_J);
+/* y += alpha x (device, n doubles each): the Newton update U += dU.  Waits. */
+int fsi_asm_axpy(fsi_asm* a, double alpha, const double* x_dev, double* y_dev);
+const char* fsi_asm_last_error(const fsi_asm* a);
+void fsi_asm_free(fsi_asm* a);
 
 /* ------------------------------------------------------------------------
  * Learned correction stage (2D meshes).  The paper has no such stage: it is an

@@ -16,7 +16,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build", "fsi")
 LIB = os.path.join(HERE, "libfsi.so")
-SOURCES = ["spmv.cu", "vec.cu", "sparse_util.cu", "amg.cu", "solver.cu", "fsi_api.cu", "noalloc.cu", "coarse.cu", "learned.cu"]
+SOURCES = ["spmv.cu", "vec.cu", "sparse_util.cu", "amg.cu", "solver.cu", "fsi_api.cu", "noalloc.cu", "coarse.cu", "learned.cu",
+           "assembly.cu"]
+# throughput probes for the rooflines (include/fsi_peaks.h), a library of their own
+PEAKS_LIB = os.path.join(HERE, "libfsi_peaks.so")
+PEAKS_SOURCES = ["peaks.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -45,7 +49,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     jobs = []
-    for src in SOURCES:
+    for src in SOURCES + PEAKS_SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         if force or _stale(o, s):
@@ -64,14 +68,16 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         for s, err in ex.map(run, jobs):
             if verbose and err:
                 print(f"[{os.path.basename(s)}]\n{err}", file=sys.stderr)
-    objs = [os.path.join(BUILD, src.replace(".cu", ".o")) for src in SOURCES]
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, "-shared", ARCH, "-o", tmp, *objs, "-lcudart"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
-        os.replace(tmp, LIB)
+    rebuilt = {os.path.basename(src) for src, _ in jobs}
+    for lib, srcs in ((LIB, SOURCES), (PEAKS_LIB, PEAKS_SOURCES)):
+        objs = [os.path.join(BUILD, src.replace(".cu", ".o")) for src in srcs]
+        if rebuilt & set(srcs) or not os.path.exists(lib):
+            tmp = lib + f".tmp{os.getpid()}"
+            cmd = [cc, "-shared", ARCH, "-o", tmp, *objs, "-lcudart"]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
+            os.replace(tmp, lib)
     return LIB
 
 

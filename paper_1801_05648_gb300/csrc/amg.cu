@@ -362,10 +362,14 @@ void vcycle_level(Hierarchy& H, int l, const T* b, T* x, cudaStream_t s) {
   const AmgParams& p = H.prm;
   for (int sw = 0; sw < p.presmooth; ++sw)
     cheb_sweep<T>(L.A, dinv_of<T>(L), L.lam, p.degree(l), p.cheb_ratio, p.cheb_upper, b, x, W.xb.p, W.d.p, sw == 0, s);
-  spmv2_resid<T>(L.A, x, nullptr, nullptr, b, W.r.p, s);
   AmgLevel& C = H.levels[l + 1];
   LevelWork<T>& WC = work<T>(C);
-  spmv_axpby<T>(L.R, W.r.p, T(1), T(0), WC.b.p, s);
+  if (L.RAn.nbr) {
+    spmv_restrict<T>(L.R, b, L.RAn, x, WC.b.p, s);                 // b_c = R b - (R A) x = R (b - A x)
+  } else {
+    spmv2_resid<T>(L.A, x, nullptr, nullptr, b, W.r.p, s);         // r = b - A x
+    spmv_axpby<T>(L.R, W.r.p, T(1), T(0), WC.b.p, s);              // b_c = R r
+  }
   vcycle_level<T>(H, l + 1, WC.b.p, WC.x.p, s);
   spmv_axpby<T>(L.P, WC.x.p, T(1), T(1), x, s);
   for (int sw = 0; sw < p.postsmooth; ++sw)
@@ -411,8 +415,14 @@ double Hierarchy::vcycle_bytes(int vb) const {
   const int nl = (int)levels.size();
   for (int l = 0; l + 1 < nl; ++l) {
     const AmgLevel& L = levels[l];
-    const int sweeps = prm.presmooth * prm.degree(l) - 1 + prm.postsmooth * prm.degree(l) + 1;  // smoother + residual
-    tot += sweeps * L.A.spmv_bytes(vb) + L.R.spmv_bytes(vb) + L.P.spmv_bytes(vb);
+    // smoother SpMVs (the first two steps from zero share one pass), the restricted
+    // residual R b + RAn x (one pass over both, one output) and the prolongation
+    const int sweeps = prm.presmooth * prm.degree(l) - 1 + prm.postsmooth * prm.degree(l);
+    tot += sweeps * L.A.spmv_bytes(vb) + L.P.spmv_bytes(vb);
+    if (L.RAn.nbr)
+      tot += L.R.spmv_bytes(vb) + L.RAn.spmv_bytes(vb) - (double)vb * L.R.rows();
+    else
+      tot += L.A.spmv_bytes(vb) + (double)vb * L.A.rows() + L.R.spmv_bytes(vb);
   }
   tot += (double)ncoarse * ncoarse * vb;
   return tot;
@@ -535,6 +545,20 @@ void amg_setup(Hierarchy& H, Bsr&& A0, const double* B0, int k0, const AmgParams
     Bsr AP2, Ac;
     bsr_spgemm(L.A, L.P, AP2, s);
     bsr_spgemm(L.R, AP2, Ac, s);
+    // -(R A) where it pays: one pass over R and R A against b and x instead of the
+    // residual (A, x, b read, r written) and its restriction (R, r read); kept when
+    // that moves fewer bytes (in FP32) and the product's rows fit the SpGEMM table
+    if (bsr_spgemm_if_fits(L.R, L.A, L.RAn, s)) {
+      const double fused = L.R.spmv_bytes(4) + L.RAn.spmv_bytes(4) - 4.0 * L.R.rows();
+      const double split = L.A.spmv_bytes(4) + 4.0 * L.A.rows() + L.R.spmv_bytes(4);
+      if (fused < 0.95 * split) {
+        bsr_scale(L.RAn, -1.0, s);
+        L.RAn.tpr = lanes_for(L.RAn.nnzb + L.R.nnzb, L.RAn.nbr, 2.0);   // one lane group reads both rows
+        L.RAn.tpr64 = lanes_for(L.RAn.nnzb + L.R.nnzb, L.RAn.nbr, 8.0);
+      } else {
+        L.RAn = Bsr();
+      }
+    }
     A = std::move(Ac);
     Bcur = std::move(Bc);
     B = Bcur.p;
@@ -574,7 +598,9 @@ void amg_make_fp32(Hierarchy& H, cudaStream_t s) {
   for (auto& L : H.levels) {
     const int64_t n = L.A.rows();
     bsr_make_fp32(L.A, s);
+    bsr_make_delta16(L.A, s);
     if (L.P.nbr) { bsr_make_fp32(L.P, s); bsr_make_fp32(L.R, s); }
+    if (L.RAn.nbr) bsr_make_fp32(L.RAn, s);
     to_f32(L.dinv64.p, L.dinv32, n, s);
     alloc_work(L.w32, n);
   }
@@ -605,6 +631,7 @@ void cheb_setup(ChebSolver& C, Bsr&& A, int degree, double ratio, double upper, 
 
 void cheb_make_fp32(ChebSolver& C, cudaStream_t s) {
   bsr_make_fp32(C.A, s);
+  bsr_make_delta16(C.A, s);
   to_f32(C.dinv64.p, C.dinv32, C.A.rows(), s);
   alloc_work(C.w32, C.A.rows());
   FSI_CUDA(cudaStreamSynchronize(s));

@@ -19,6 +19,8 @@
 //              lambda = |lambda_max(D^-1 A)| by power iteration from
 //              x_i = 1 + u_i (splitmix64 stream 256 + level)
 //   A_c        R (A P),  R = P^T
+//   RAn        -(R A), so that a V-cycle forms the restricted residual R (b - A x)
+//              as R b + RAn x in one pass (the residual b - A x is never stored)
 // Coarsest level: dense inverse (all-zero rows replaced by identity rows).
 #pragma once
 #include "common.cuh"
@@ -52,6 +54,7 @@ struct AmgLevel {
   DBuf<float> dinv32;
   double lam = 0.0;
   Bsr P, R;
+  Bsr RAn;                    // -(R A): the coarse right-hand side R (b - A x) = R b + RAn x in one product
   int nagg = 0;
   DBuf<int> agg;              // aggregate of each node (-1 = none), for inspection
   LevelWork<double> w64;

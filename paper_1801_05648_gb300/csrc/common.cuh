@@ -123,14 +123,18 @@ struct Bsr {
   DBuf<int> colind;     // nnzb
   DBuf<double> v64;     // nnzb * br * bc
   DBuf<float> v32;      // optional FP32 copy
+  DBuf<int16_t> cd16;   // optional, square matrices: block column minus block row as int16 (read by the
+                        // FP32 Chebyshev steps when every offset fits; 2 bytes per block instead of 4)
   int tpr = 32;         // threads per block row of the FP32 SpMV, from the mean row length
   int tpr64 = 2;        // ... of the FP64 SpMV (fewer lanes: FP64 issue slots are scarce)
   int64_t rows() const { return (int64_t)nbr * br; }
   int64_t cols() const { return (int64_t)nbc * bc; }
   template <class T> const T* vals() const;
   // algorithmic bytes of one SpMV: values + column indices + row pointers + x + y
+  // (FP32 products of a matrix with 16-bit column offsets read 2 bytes per block index)
   double spmv_bytes(int value_bytes) const {
-    return (double)nnzb * (br * bc * value_bytes + 4) + 4.0 * (nbr + 1) + (double)value_bytes * (cols() + rows());
+    const int ib = (value_bytes == 4 && cd16.p) ? 2 : 4;
+    return (double)nnzb * (br * bc * value_bytes + ib) + 4.0 * (nbr + 1) + (double)value_bytes * (cols() + rows());
   }
 };
 // FP32 copies of blocks with 9 values (3 x 3) are stored planar (values 0-3 of

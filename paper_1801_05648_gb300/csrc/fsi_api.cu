@@ -101,7 +101,7 @@ void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* coli
   using fsi::require;
   require(dim == 2 || dim == 3, "dim must be 2 or 3");
   require(n > 0 && n < (int64_t)1 << 31, "n out of range");
-  require(rowptr && colind && vals && off, "null CSR or offsets");
+  require(rowptr && colind && off, "null CSR or offsets");
   require(off[0] == 0 && off[5] == n, "block_offsets must start at 0 and end at n");
   for (int k = 0; k < 5; ++k) require(off[k] <= off[k + 1], "block_offsets must be non-decreasing");
   for (int k = 0; k < 4; ++k) require((off[k + 1] - off[k]) % dim == 0, "vector classes must be multiples of dim");
@@ -112,7 +112,7 @@ void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* coli
     for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
       require(colind[k] >= 0 && colind[k] < n, "column index out of range");
       require(k == rowptr[r] || colind[k] > colind[k - 1], "columns must be strictly increasing within a row");
-      require(std::isfinite(vals[k]), "non-finite matrix value");
+      require(!vals || std::isfinite(vals[k]), "non-finite matrix value");
     }
   }
 }
@@ -200,6 +200,14 @@ int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const in
   }
   *out = ctx;
   return FSI_OK;
+}
+
+int fsi_update_values(fsi_ctx* ctx, const double* vals_dev) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require(vals_dev != nullptr, "null values");
+    fsi::context_update_values(ctx->C, vals_dev);
+  });
 }
 
 int fsi_precond_build(fsi_ctx* ctx, int precision, const char* learned_weights) {

@@ -412,32 +412,16 @@ Context::~Context() {
   if (own_stream && s) cudaStreamDestroy(s);
 }
 
-void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, const double* vals,
-                   const double* solid_coords) {
-  SetupPhase setup_phase;
-  auto t0 = clk::now();
-  FSI_CUDA(cudaGetDevice(&C.device));
-  FSI_CUDA(cudaStreamCreateWithFlags(&C.s2, cudaStreamNonBlocking));
-  FSI_CUDA(cudaEventCreateWithFlags(&C.ev_fork, cudaEventDisableTiming));
-  FSI_CUDA(cudaEventCreateWithFlags(&C.ev_join, cudaEventDisableTiming));
+// Class blocks of the operator (Eq. mat:small): the four pieces of the outer
+// operator and the preconditioner's blocks, all extracted on the device.
+static void extract_blocks(Context& C, const CsrView& A) {
   const int d = C.dim;
   const int64_t* o = C.off;
-  Csr A;
-  A.n = C.n;
-  A.nnz = rowptr[C.n];
-  A.rowptr.alloc(C.n + 1);
-  A.colind.alloc(A.nnz > 0 ? A.nnz : 1);
-  A.vals.alloc(A.nnz > 0 ? A.nnz : 1);
-  FSI_CUDA(cudaMemcpyAsync(A.rowptr.p, rowptr, sizeof(int64_t) * (C.n + 1), cudaMemcpyHostToDevice, C.s));
-  if (A.nnz) {
-    FSI_CUDA(cudaMemcpyAsync(A.colind.p, colind, sizeof(int) * A.nnz, cudaMemcpyHostToDevice, C.s));
-    FSI_CUDA(cudaMemcpyAsync(A.vals.p, vals, sizeof(double) * A.nnz, cudaMemcpyHostToDevice, C.s));
-  }
   const int nV = (int)(o[4] / d);
   const int nP = (int)(o[5] - o[4]);
   const int nm = (int)((o[1] - o[0]) / d), nsv = (int)((o[2] - o[1]) / d), nsu = (int)((o[3] - o[2]) / d);
   const int ns = nsv + nsu, nfv = (int)((o[4] - o[3]) / d), nms = (int)(o[3] / d);
-  auto& s = C.s;
+  cudaStream_t s = C.s;
   // outer operator
   extract_bsr(A, 0, nV, d, 0, nV, d, C.AVV, s);
   extract_bsr(A, 0, nV, d, o[4], nP, 1, C.AVP, s);
@@ -473,9 +457,54 @@ void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, con
   extract_bsr(A, o[3], nfv, d, o[4], nP, 1, C.B_vp, s);
   extract_bsr(A, o[4], nP, 1, o[3], nfv, d, C.B_pv, s);
   extract_bsr(A, o[4], nP, 1, o[4], nP, 1, C.Cpp, s);
-  if (solid_coords && !(C.prm.flags & NO_RIGID_MODES)) upload(C.solid_B, rigid_modes(solid_coords, nsv, d), s);
-  FSI_CUDA(cudaStreamSynchronize(s));
+}
+
+void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                   const double* solid_coords) {
+  SetupPhase setup_phase;
+  auto t0 = clk::now();
+  FSI_CUDA(cudaGetDevice(&C.device));
+  FSI_CUDA(cudaStreamCreateWithFlags(&C.s2, cudaStreamNonBlocking));
+  FSI_CUDA(cudaEventCreateWithFlags(&C.ev_fork, cudaEventDisableTiming));
+  FSI_CUDA(cudaEventCreateWithFlags(&C.ev_join, cudaEventDisableTiming));
+  const int d = C.dim;
+  const int64_t* o = C.off;
+  Csr A;
+  A.n = C.n;
+  A.nnz = rowptr[C.n];
+  A.rowptr.alloc(C.n + 1);
+  A.colind.alloc(A.nnz > 0 ? A.nnz : 1);
+  A.vals.alloc(A.nnz > 0 ? A.nnz : 1);
+  FSI_CUDA(cudaMemcpyAsync(A.rowptr.p, rowptr, sizeof(int64_t) * (C.n + 1), cudaMemcpyHostToDevice, C.s));
+  if (A.nnz) {
+    FSI_CUDA(cudaMemcpyAsync(A.colind.p, colind, sizeof(int) * A.nnz, cudaMemcpyHostToDevice, C.s));
+    if (vals)
+      FSI_CUDA(cudaMemcpyAsync(A.vals.p, vals, sizeof(double) * A.nnz, cudaMemcpyHostToDevice, C.s));
+    else   // pattern only: the values come later from the device (fsi_update_values)
+      FSI_CUDA(cudaMemsetAsync(A.vals.p, 0, sizeof(double) * A.nnz, C.s));
+  }
+  extract_blocks(C, A.view());
+  // keep the pattern (not the values) for fsi_update_values
+  FSI_CUDA(cudaStreamSynchronize(C.s));
+  A.vals.release();
+  C.pattern = std::move(A);
+  const int nsv = (int)((o[2] - o[1]) / d);
+  if (solid_coords && !(C.prm.flags & NO_RIGID_MODES)) upload(C.solid_B, rigid_modes(solid_coords, nsv, d), C.s);
+  FSI_CUDA(cudaStreamSynchronize(C.s));
   C.setup_s = secs(t0, clk::now());
+}
+
+void context_update_values(Context& C, const double* vals_dev) {
+  SetupPhase setup_phase;
+  CsrView v = C.pattern.view();
+  v.vals = vals_dev;
+  extract_blocks(C, v);
+  // every hierarchy, Schur operator, FP32 copy and captured graph refers to the old values
+  C.built = false;
+  C.fp32_ready = false;
+  C.At_built = false;
+  if (C.iter_graph) { cudaGraphExecDestroy(C.iter_graph); C.iter_graph = nullptr; }
+  FSI_CUDA(cudaStreamSynchronize(C.s));
 }
 
 void precond_build(Context& C, int precision) {
@@ -530,7 +559,7 @@ void precond_build(Context& C, int precision) {
     alloc_pw(C.pw64, C.n);
     C.built = true;
   }
-  if (precision == 1 && !C.pw32.ready) {
+  if (precision == 1 && !C.fp32_ready) {
     for (auto& H : C.H) amg_make_fp32(H, s);
     cheb_make_fp32(C.mass, s);
     {
@@ -541,6 +570,7 @@ void precond_build(Context& C, int precision) {
     for (Bsr* B : {&C.C_ms, &C.A_vu, &C.A_uv, &C.C_sv_f, &C.C_sv_p, &C.C_fv_ms, &C.C_p_ms, &C.B_vp, &C.B_pv})
       bsr_make_fp32(*B, s);
     alloc_pw(C.pw32, C.n);
+    C.fp32_ready = true;
   }
   C.precision = precision;
   if (C.iter_graph) { cudaGraphExecDestroy(C.iter_graph); C.iter_graph = nullptr; }

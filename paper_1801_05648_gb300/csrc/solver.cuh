@@ -78,6 +78,8 @@ struct Context {
   Hierarchy H[4];             // M, S_hat, A_ff, S_p
   ChebSolver mass;            // A_uu (solid mass)
   bool built = false;
+  bool fp32_ready = false;    // FP32 copies of the current hierarchies and couplings exist
+  Csr pattern;                // device CSR pattern of the operator (values not kept), for fsi_update_values
   int precision = 0;          // 0 FP64, 1 FP32 AMG
   PrecWork<double> pw64;
   PrecWork<float> pw32;
@@ -115,6 +117,9 @@ struct Context {
 
 void context_setup(Context& C, const int64_t* rowptr, const int32_t* colind, const double* vals,
                    const double* solid_coords);
+// New operator values (device, CSR order of the pattern given to context_setup):
+// re-extract every class block; the preconditioner must be built again.
+void context_update_values(Context& C, const double* vals_dev);
 void precond_build(Context& C, int precision);
 template <class T> void precond_apply(Context& C, const T* r, T* z);
 void apply_operator(Context& C, const double* x, double* y);

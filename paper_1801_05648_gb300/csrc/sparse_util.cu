@@ -330,6 +330,20 @@ __global__ void k_scale_rows(int nbr, int br, int bc, const int* __restrict__ rp
     for (int i = 0; i < br; ++i)
       for (int j = 0; j < bc; ++j) va[((int64_t)k * br + i) * bc + j] *= w[(int64_t)row * br + i];
 }
+__global__ void k_scale_all(int64_t n, double alpha, double* __restrict__ va) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) va[i] *= alpha;
+}
+__global__ void k_delta16(int nbr, const int* __restrict__ rp, const int* __restrict__ ci, int16_t* __restrict__ d,
+                          int* __restrict__ overflow) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  for (int k = rp[row]; k < rp[row + 1]; ++k) {
+    const int off = ci[k] - row;
+    if (off < -32768 || off > 32767) { atomicExch(overflow, 1); return; }
+    d[k] = (int16_t)off;
+  }
+}
 __global__ void k_point_diag(int nbr, int b, const int* __restrict__ rp, const int* __restrict__ ci,
                              const double* __restrict__ va, double* __restrict__ diag) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -435,6 +449,8 @@ void spgemm_dispatch(int br, int bk, int bc, F&& f) {
   FSI_G(1, 1, 1) FSI_G(2, 2, 2) FSI_G(3, 3, 3) FSI_G(2, 2, 3) FSI_G(3, 3, 6) FSI_G(6, 6, 6)
   // R * (A P)  (k x b times b x k)
   FSI_G(3, 2, 3) FSI_G(6, 3, 6)
+  // R * A on the first level of the rigid-body solid hierarchy (k x b times b x b)
+  FSI_G(3, 2, 2) FSI_G(6, 3, 3)
   // pressure Schur: (1 x d) * (d x 1)
   FSI_G(1, 2, 1) FSI_G(1, 3, 1)
 #undef FSI_G
@@ -465,21 +481,22 @@ int64_t exclusive_scan(const int* in, int* out, int64_t n, cudaStream_t s) {
   return total;
 }
 
-void extract_bsr(const Csr& A, int64_t r0, int nbr, int br, int64_t c0, int nbc, int bc, Bsr& out, cudaStream_t s) {
+void extract_bsr(const CsrView& A, int64_t r0, int nbr, int br, int64_t c0, int nbc, int bc, Bsr& out,
+                 cudaStream_t s) {
   require(br <= 6, "extract_bsr: block rows > 6");
   out = Bsr();
   out.nbr = nbr; out.nbc = nbc; out.br = br; out.bc = bc;
   DBuf<int> cnt(nbr > 0 ? nbr : 1);
   const int64_t c1 = c0 + (int64_t)nbc * bc;
   if (nbr > 0) {
-    k_extract<false><<<div_up(nbr, 128), 128, 0, s>>>(A.rowptr.p, A.colind.p, A.vals.p, r0, nbr, br, c0, c1, bc,
-                                                    cnt.p, nullptr, nullptr, nullptr);
+    k_extract<false><<<div_up(nbr, 128), 128, 0, s>>>(A.rowptr, A.colind, A.vals, r0, nbr, br, c0, c1, bc, cnt.p,
+                                                    nullptr, nullptr, nullptr);
     FSI_CHECK_LAUNCH();
   }
   finalize_rowptr(cnt.p, out, s);
   if (nbr > 0) {
-    k_extract<true><<<div_up(nbr, 128), 128, 0, s>>>(A.rowptr.p, A.colind.p, A.vals.p, r0, nbr, br, c0, c1, bc,
-                                                   nullptr, out.rowptr.p, out.colind.p, out.v64.p);
+    k_extract<true><<<div_up(nbr, 128), 128, 0, s>>>(A.rowptr, A.colind, A.vals, r0, nbr, br, c0, c1, bc, nullptr,
+                                                   out.rowptr.p, out.colind.p, out.v64.p);
     FSI_CHECK_LAUNCH();
   }
   set_tpr(out);
@@ -532,6 +549,10 @@ void bsr_transpose(const Bsr& A, Bsr& C, cudaStream_t s) {
 }
 
 void bsr_spgemm(const Bsr& A, const Bsr& B, Bsr& C, cudaStream_t s) {
+  require(bsr_spgemm_if_fits(A, B, C, s), "bsr_spgemm: a product row has more than 768 block columns");
+}
+
+bool bsr_spgemm_if_fits(const Bsr& A, const Bsr& B, Bsr& C, cudaStream_t s) {
   require(A.bc == B.br && A.nbc == B.nbr, "bsr_spgemm: inner dimensions differ");
   C = Bsr();
   C.nbr = A.nbr; C.nbc = B.nbc; C.br = A.br; C.bc = B.bc;
@@ -546,7 +567,10 @@ void bsr_spgemm(const Bsr& A, const Bsr& B, Bsr& C, cudaStream_t s) {
   int of = 0;
   FSI_CUDA(cudaMemcpyAsync(&of, overflow.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   FSI_CUDA(cudaStreamSynchronize(s));
-  require(!of, "bsr_spgemm: a product row has more than 768 block columns");
+  if (of) {
+    C = Bsr();
+    return false;
+  }
   finalize_rowptr(cnt.p, C, s);
   if (A.nbr > 0) {
     k_spgemm_sym<true><<<grid, kWarpsPerBlock * 32, 0, s>>>(A.nbr, A.rowptr.p, A.colind.p, B.rowptr.p, B.colind.p,
@@ -559,6 +583,7 @@ void bsr_spgemm(const Bsr& A, const Bsr& B, Bsr& C, cudaStream_t s) {
     });
   }
   set_tpr(C);
+  return true;
 }
 
 void sort_segments(int nseg, const int* off, int* key, int* pay, cudaStream_t s) {
@@ -570,6 +595,13 @@ void sort_segments(int nseg, const int* off, int* key, int* pay, cudaStream_t s)
 void bsr_scale_rows(Bsr& A, const double* w, cudaStream_t s) {
   if (A.nbr == 0) return;
   k_scale_rows<<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, A.br, A.bc, A.rowptr.p, A.v64.p, w);
+  FSI_CHECK_LAUNCH();
+}
+
+void bsr_scale(Bsr& A, double alpha, cudaStream_t s) {
+  const int64_t n = A.nnzb * A.br * A.bc;
+  if (n == 0) return;
+  k_scale_all<<<div_up(n, 256), 256, 0, s>>>(n, alpha, A.v64.p);
   FSI_CHECK_LAUNCH();
 }
 
@@ -596,6 +628,21 @@ void bsr_make_fp32(Bsr& A, cudaStream_t s) {
       k_to_f32<<<div_up(n, 256), 256, 0, s>>>(n, A.v64.p, A.v32.p);
     FSI_CHECK_LAUNCH();
   }
+}
+
+bool bsr_make_delta16(Bsr& A, cudaStream_t s) {
+  A.cd16.release();
+  if (A.nbr == 0 || A.nbr != A.nbc || A.nnzb == 0) return false;
+  DBuf<int> of(1);
+  FSI_CUDA(cudaMemsetAsync(of.p, 0, sizeof(int), s));
+  A.cd16.alloc(A.nnzb);
+  k_delta16<<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, A.rowptr.p, A.colind.p, A.cd16.p, of.p);
+  FSI_CHECK_LAUNCH();
+  int h = 0;
+  FSI_CUDA(cudaMemcpyAsync(&h, of.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  if (h) A.cd16.release();
+  return !h;
 }
 
 void bsr_to_dense(const Bsr& A, double* dense, cudaStream_t s) {

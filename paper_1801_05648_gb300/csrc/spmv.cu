@@ -8,7 +8,9 @@ namespace fsi {
 
 namespace {
 
-template <class T, int BR, int BC1, int BC2, class Epi, class G1>
+// ALLOW16: the first matrix's 16-bit column offsets are read when present (FP32
+// Chebyshev steps on the square level matrices).
+template <class T, int BR, int BC1, int BC2, class Epi, class G1, bool ALLOW16 = false>
 void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi& epi, cudaStream_t s) {
   if (A1.nbr == 0) return;
   const int tpr = sizeof(T) == 8 ? A1.tpr64 : A1.tpr;
@@ -28,6 +30,14 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
   if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; nnzb2 = A2->nnzb; }
   const int pre_wait = tu.setup_depth == 0 ? 1 : 0;
   const int pf = tu.prefetch > 0 ? 1 : 0;
+  if constexpr (ALLOW16 && sizeof(T) == 4 && BC2 == 0) {
+    if (A1.cd16.p) {
+      launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4, int16_t>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf,
+               pre_wait, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2,
+               epi);
+      return;
+    }
+  }
   if (tu.unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
     launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf, pre_wait,
              A1.rowptr.p, A1.colind.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2, epi);
@@ -36,9 +46,9 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
              A1.rowptr.p, A1.colind.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2, epi);
 }
 
-template <class T, int BR, int BC1, int BC2, class Epi>
+template <class T, int BR, int BC1, int BC2, class Epi, bool ALLOW16 = false>
 void launch(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const Epi& epi, cudaStream_t s) {
-  launch_g<T, BR, BC1, BC2, Epi, GatherX<T, BC1>>(A1, GatherX<T, BC1>{x1}, A2, x2, epi, s);
+  launch_g<T, BR, BC1, BC2, Epi, GatherX<T, BC1>, ALLOW16>(A1, GatherX<T, BC1>{x1}, A2, x2, epi, s);
 }
 
 // Calls f.template operator()<BR, BC1, BC2>() for the runtime shape.
@@ -87,9 +97,30 @@ void spmv2_resid(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const T
 }
 
 template <class T>
+void spmv_restrict(const Bsr& R, const T* b, const Bsr& RAn, const T* x, T* y, cudaStream_t s) {
+  require(RAn.nbr == R.nbr && RAn.br == R.br && RAn.bc == R.bc, "spmv_restrict: R and -(R A) shapes differ");
+  // coarse block k x fine block b: translations (k = b = 1, 2, 3), rigid-body modes
+  // on the first solid level (3 x 2, 6 x 3) and below it (3 x 3, 6 x 6)
+  // RAn leads (its lane count is set from both matrices' row lengths), R b follows
+  auto run = [&]<int BR, int BC>() {
+    launch<T, BR, BC, BC>(RAn, x, &R, b, EpiAxpby<T, BR>{y, T(1), T(0)}, s);
+  };
+  const int br = R.br, bc = R.bc;
+  if (br == 1 && bc == 1) run.template operator()<1, 1>();
+  else if (br == 2 && bc == 2) run.template operator()<2, 2>();
+  else if (br == 3 && bc == 3) run.template operator()<3, 3>();
+  else if (br == 6 && bc == 6) run.template operator()<6, 6>();
+  else if (br == 3 && bc == 2) run.template operator()<3, 2>();
+  else if (br == 6 && bc == 3) run.template operator()<6, 3>();
+  else throw Error(EINVAL_, "spmv_restrict: unsupported block shape " + std::to_string(br) + "x" + std::to_string(bc));
+}
+
+template <class T>
 void spmv_cheb(const Bsr& A, const T* x, const T* b, const T* dinv, T* d, T* xo, T c1, T c2, cudaStream_t s) {
+  require(A.br == A.bc, "spmv_cheb: square blocks only");
   dispatch(A.br, A.bc, 0, [&]<int BR, int BC1, int BC2>() {
-    launch<T, BR, BC1, 0>(A, x, nullptr, nullptr, EpiCheb<T, BR>{b, dinv, x, d, xo, c1, c2}, s);
+    if constexpr (BR == BC1)
+      launch<T, BR, BC1, 0, EpiCheb<T, BR>, true>(A, x, nullptr, nullptr, EpiCheb<T, BR>{b, dinv, x, d, xo, c1, c2}, s);
   });
 }
 
@@ -106,8 +137,9 @@ void spmv_cheb_from_zero(const Bsr& A, const T* b, const T* dinv, T* d, T* xo, T
   require(A.br == A.bc, "spmv_cheb_from_zero: square blocks only");
   dispatch(A.br, A.bc, 0, [&]<int BR, int BC1, int BC2>() {
     if constexpr (BR == BC1) {
-      launch_g<T, BR, BC1, 0>(A, GatherScaled<T, BC1>{b, dinv, inv_theta}, nullptr, (const T*)nullptr,
-                              EpiChebFromZero<T, BR>{b, dinv, d, xo, inv_theta, c1, c2}, s);
+      launch_g<T, BR, BC1, 0, EpiChebFromZero<T, BR>, GatherScaled<T, BC1>, true>(
+          A, GatherScaled<T, BC1>{b, dinv, inv_theta}, nullptr, (const T*)nullptr,
+          EpiChebFromZero<T, BR>{b, dinv, d, xo, inv_theta, c1, c2}, s);
     }
   });
 }
@@ -117,6 +149,7 @@ void spmv_cheb_from_zero(const Bsr& A, const T* b, const T* dinv, T* d, T* xo, T
   template void spmv2_axpby<T>(const Bsr&, const T*, const Bsr*, const T*, T, T, T*, cudaStream_t);         \
   template void spmv2_resid<T>(const Bsr&, const T*, const Bsr*, const T*, const T*, T*, cudaStream_t);     \
   template void spmv_cheb<T>(const Bsr&, const T*, const T*, const T*, T*, T*, T, T, cudaStream_t);         \
+  template void spmv_restrict<T>(const Bsr&, const T*, const Bsr&, const T*, T*, cudaStream_t);             \
   template void spmv_dinv<T>(const Bsr&, const T*, const T*, T*, cudaStream_t);                             \
   template void spmv_cheb_from_zero<T>(const Bsr&, const T*, const T*, T*, T*, T, T, T, cudaStream_t);
 FSI_INST(double)

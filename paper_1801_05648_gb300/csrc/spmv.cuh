@@ -259,9 +259,11 @@ __host__ __device__ constexpr int unroll_for() {
 // The U column indices and the U blocks are requested together (which entries
 // exist follows from the position alone), then the x segments, which need the
 // indices: one dependent memory round trip for the matrix data, one for x.
-template <class T, int BR, int BC, int UREQ, class G>
-__device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const T* __restrict__ v, int64_t nnzb,
-                                               const G& gx, int kb, int ke, int lane, int tpr, T* acc) {
+// Column indices are int32 block columns (base 0), or int16 offsets from the
+// block row (base = the row) for square matrices whose offsets fit.
+template <class T, int BR, int BC, int UREQ, class G, class CI = int>
+__device__ __forceinline__ void row_accumulate(const CI* __restrict__ ci, int base, const T* __restrict__ v,
+                                               int64_t nnzb, const G& gx, int kb, int ke, int lane, int tpr, T* acc) {
   constexpr int U = unroll_for<T, BR, BC, UREQ>();
   for (int k0 = kb + lane; k0 < ke; k0 += tpr * U) {
     int col[U];
@@ -270,7 +272,7 @@ __device__ __forceinline__ void row_accumulate(const int* __restrict__ ci, const
     for (int u = 0; u < U; ++u) {
       const int k = k0 + u * tpr;
       if (k < ke) {
-        col[u] = __ldcs(ci + k);
+        col[u] = base + (int)__ldcs(ci + k);
         load_block<T, BR, BC>(v, nnzb, k, blk[u]);
       } else {
         col[u] = -1;
@@ -328,9 +330,9 @@ __device__ __forceinline__ void prefetch_blocks(const T* v, int64_t nnzb, int a,
 // that kernel drains and while the CTA works through its first rows.  Reading the
 // row pointers before the wait is only allowed once the matrices are built
 // (pre_wait != 0); during set-up the previous kernel may still be writing them.
-template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4>
+template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4, class CI1 = int>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per_cta, int prefetch, int pre_wait,
-    const int* __restrict__ rp1, const int* __restrict__ ci1, const T* __restrict__ v1, int64_t nnzb1, G1 g1,
+    const int* __restrict__ rp1, const CI1* __restrict__ ci1, const T* __restrict__ v1, int64_t nnzb1, G1 g1,
     const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, int64_t nnzb2,
     const T* __restrict__ x2,
     Epi epi) {
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
   if (prefetch && threadIdx.x == 0 && r0 < r1) {
     const int a = rp1[r0], b = rp1[r1];
     prefetch_blocks<T, BR, BC1>(v1, nnzb1, a, b);
-    prefetch_l2(ci1 + a, sizeof(int) * (size_t)(b - a));
+    prefetch_l2(ci1 + a, sizeof(CI1) * (size_t)(b - a));
     if constexpr (BC2 > 0) {
       const int a2 = rp2[r0], b2 = rp2[r1];
       prefetch_blocks<T, BR, BC2>(v2, nnzb2, a2, b2);
@@ -359,9 +361,10 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
     typename Epi::Pre pre;
     if (valid && lane == 0) pre = epi.load(row);
     if (valid) {
-      row_accumulate<T, BR, BC1, UREQ>(ci1, v1, nnzb1, g1, rp1[row], rp1[row + 1], lane, tpr, acc);
+      row_accumulate<T, BR, BC1, UREQ, G1, CI1>(ci1, sizeof(CI1) == 4 ? 0 : row, v1, nnzb1, g1, rp1[row],
+                                                rp1[row + 1], lane, tpr, acc);
       if constexpr (BC2 > 0)
-        row_accumulate<T, BR, BC2, UREQ>(ci2, v2, nnzb2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr,
+        row_accumulate<T, BR, BC2, UREQ>(ci2, 0, v2, nnzb2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr,
                                          acc);
     }
     for (int off = tpr >> 1; off > 0; off >>= 1)
@@ -378,6 +381,10 @@ template <class T> void spmv_axpby(const Bsr& A, const T* x, T alpha, T beta, T*
 template <class T> void spmv2_axpby(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, T alpha, T beta, T* y, cudaStream_t s);
 // r = b - A1 x1 - A2 x2
 template <class T> void spmv2_resid(const Bsr& A1, const T* x1, const Bsr* A2, const T* x2, const T* b, T* r, cudaStream_t s);
+// Coarse right-hand side of a V-cycle level in one pass: y = RAn x + R b with
+// RAn = -(R A), i.e. y = R (b - A x), the restricted residual, without forming
+// b - A x (R: k x b blocks, RAn: the same block rows and k x b blocks).
+template <class T> void spmv_restrict(const Bsr& R, const T* b, const Bsr& RAn, const T* x, T* y, cudaStream_t s);
 // Chebyshev step epilogue (see EpiCheb)
 template <class T> void spmv_cheb(const Bsr& A, const T* x, const T* b, const T* dinv, T* d, T* xo, T c1, T c2, cudaStream_t s);
 // y = dinv * (A x)

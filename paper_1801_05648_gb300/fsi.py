@@ -33,7 +33,8 @@ EXPORTED = ["fsi_default_params", "fsi_setup", "fsi_precond_build", "fsi_solve",
             "fsi_learned_apply", "fsi_learned_features", "fsi_set_harvest", "fsi_default_train_params",
             "fsi_trainer_create", "fsi_trainer_step", "fsi_trainer_loss", "fsi_trainer_update",
             "fsi_trainer_set_master", "fsi_trainer_get", "fsi_trainer_save", "fsi_trainer_free", "fsi_set_flags",
-            "fsi_set_learned_accept"]
+            "fsi_set_learned_accept", "fsi_update_values", "fsi_asm_create", "fsi_asm_residual",
+            "fsi_asm_jacobian", "fsi_asm_axpy", "fsi_asm_last_error", "fsi_asm_free"]
 
 
 class FSIError(RuntimeError):
@@ -54,6 +55,19 @@ class Params(ctypes.Structure):
                 ("learned_accept", ctypes.c_double), ("spmv_prefetch", ctypes.c_int),
                 ("cluster_max_bytes", ctypes.c_double), ("cheb_degree_coarse", ctypes.c_int),
                 ("fluid_gmres_iters", ctypes.c_int), ("precond_variant", ctypes.c_int)]
+
+
+class AsmMesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("cells", ctypes.c_int * 3), ("h", ctypes.c_double * 3), ("n", ctypes.c_int64),
+                ("cell_dof", ctypes.POINTER(ctypes.c_int32)), ("cell_flags", ctypes.POINTER(ctypes.c_uint32)),
+                ("rowptr", ctypes.POINTER(ctypes.c_int64)), ("colind", ctypes.POINTER(ctypes.c_int32)),
+                ("row_fixed", ctypes.POINTER(ctypes.c_uint8))]
+
+
+class AsmPhysics(ctypes.Structure):
+    _fields_ = [("rho_f", ctypes.c_double), ("nu_f", ctypes.c_double), ("mu_s", ctypes.c_double),
+                ("lambda_s", ctypes.c_double), ("rho_s", ctypes.c_double), ("dt", ctypes.c_double),
+                ("theta", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -146,6 +160,17 @@ def load_library(path: str = LIB_PATH):
     lib.fsi_trainer_save.argtypes = [vp, ctypes.c_char_p]
     lib.fsi_trainer_free.argtypes = [vp]
     lib.fsi_trainer_free.restype = None
+    lib.fsi_update_values.argtypes = [vp, vp]
+    lib.fsi_asm_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(AsmMesh), ctypes.POINTER(AsmPhysics), vp]
+    lib.fsi_asm_residual.argtypes = [vp, vp, vp, vp, f64p, f64p]
+    lib.fsi_asm_jacobian.argtypes = [vp, vp, vp, vp, f64p]
+    lib.fsi_asm_axpy.argtypes = [vp, ctypes.c_double, vp, vp]
+    lib.fsi_asm_last_error.argtypes = [vp]
+    lib.fsi_asm_last_error.restype = ctypes.c_char_p
+    lib.fsi_asm_free.argtypes = [vp]
+    lib.fsi_asm_free.restype = None
+    for name in ("fsi_update_values", "fsi_asm_create", "fsi_asm_residual", "fsi_asm_jacobian", "fsi_asm_axpy"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("fsi_learned_setup", "fsi_learned_load", "fsi_learned_set_weights", "fsi_learned_apply",
                  "fsi_learned_features", "fsi_set_harvest", "fsi_trainer_create", "fsi_trainer_step",
                  "fsi_trainer_loss", "fsi_trainer_update", "fsi_trainer_set_master", "fsi_trainer_get",
@@ -153,6 +178,24 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+PEAKS_LIB_PATH = os.path.join(_HERE, "libfsi_peaks.so")
+PEAKS_EXPORTED = ["fsi_probe_fma_rate"]
+
+
+def probe_fma_rate(bits: int, iters: int = 4096, reps: int = 5):
+    """Measured FMA throughput of the current device (libfsi_peaks.so, include/fsi_peaks.h):
+    (FMAs per second, best launch ms) for bits = 64 or 32."""
+    lib = ctypes.CDLL(PEAKS_LIB_PATH)
+    lib.fsi_probe_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.fsi_probe_fma_rate.restype = ctypes.c_int
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib.fsi_probe_fma_rate(int(bits), int(iters), int(reps), ctypes.byref(rate), ctypes.byref(ms))
+    if rc != 0:
+        raise FSIError(rc, "fsi_probe_fma_rate failed")
+    return rate.value, ms.value
 
 
 def default_params(dim: int, **overrides) -> Params:
@@ -191,9 +234,10 @@ class FSISolver:
         self._h = ctypes.c_void_p()
         rowptr = np.ascontiguousarray(rowptr, np.int64)
         colind = np.ascontiguousarray(colind, np.int32)
-        vals = np.ascontiguousarray(vals, np.float64)
+        vals = None if vals is None else np.ascontiguousarray(vals, np.float64)   # None: pattern only
         offsets = np.ascontiguousarray(offsets, np.int64)
         self.n = int(offsets[5])
+        self.nnz = int(rowptr[-1])
         self.dim = dim
         self.flags = int(params.flags) if params is not None else 0
         self.offsets = offsets.copy()
@@ -206,7 +250,7 @@ class FSISolver:
         self._stream = stream
         self._order()
         rc = lib.fsi_setup(ctypes.byref(self._h), dim, self.n, _np_ptr(rowptr, ctypes.c_int64),
-                           _np_ptr(colind, ctypes.c_int32), _np_ptr(vals, ctypes.c_double),
+                           _np_ptr(colind, ctypes.c_int32), None if vals is None else _np_ptr(vals, ctypes.c_double),
                            _np_ptr(offsets, ctypes.c_int64),
                            None if coords is None else _np_ptr(coords, ctypes.c_double),
                            None if params is None else ctypes.byref(params), ctypes.c_void_p(stream))
@@ -386,6 +430,13 @@ class FSISolver:
         self._keep_harvest = buf
         self._check(self._lib.fsi_set_harvest(self._h, ptr, int(nvec if buf is not None else 0)))
 
+    def update_values(self, vals):
+        """New operator values on the same CSR pattern (float64 CUDA tensor, nnz entries);
+        precond_build must follow before the next solve."""
+        nnz = getattr(self, "nnz", None)
+        self._order()
+        self._check(self._lib.fsi_update_values(self._h, _dev_ptr(vals, nnz)))
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self._lib.fsi_free(self._h)
@@ -402,6 +453,99 @@ class FSISolver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class FSIAssembler:
+    """fsi_asm: residual R(U) and Jacobian dR/dU of the ALE-FSI system on the device
+    (include/fsi.h), for the Newton loop without host assembly.
+
+    mesh: the cell map of a structured box mesh (cells per direction, cell size,
+    element-DOF map, cell flags, the Jacobian's CSR pattern and fixed rows);
+    physics: rho_f, nu_f, mu_s, lambda_s, rho_s, dt, theta."""
+
+    def __init__(self, dim, cells, h, n, cell_dof, cell_flags, rowptr, colind, row_fixed, physics, stream=None):
+        import torch
+        lib = load_library()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        self.n = int(n)
+        self.dim = int(dim)
+        self._keep = [np.ascontiguousarray(cell_dof, np.int32), np.ascontiguousarray(cell_flags, np.uint32),
+                      np.ascontiguousarray(rowptr, np.int64), np.ascontiguousarray(colind, np.int32),
+                      np.ascontiguousarray(row_fixed, np.uint8)]
+        self.nnz = int(self._keep[2][-1])
+        m = AsmMesh()
+        m.dim = self.dim
+        for d in range(3):
+            m.cells[d] = int(cells[d]) if d < dim else 1
+            m.h[d] = float(h[d]) if d < dim else 1.0
+        m.n = self.n
+        m.cell_dof = _np_ptr(self._keep[0], ctypes.c_int32)
+        m.cell_flags = _np_ptr(self._keep[1], ctypes.c_uint32)
+        m.rowptr = _np_ptr(self._keep[2], ctypes.c_int64)
+        m.colind = _np_ptr(self._keep[3], ctypes.c_int32)
+        m.row_fixed = _np_ptr(self._keep[4], ctypes.c_uint8)
+        ph = AsmPhysics(**{k: float(physics[k]) for k in ("rho_f", "nu_f", "mu_s", "lambda_s", "rho_s", "dt",
+                                                           "theta")})
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        rc = lib.fsi_asm_create(ctypes.byref(self._h), ctypes.byref(m), ctypes.byref(ph),
+                                ctypes.c_void_p(self.stream.cuda_stream))
+        self._keep = None                       # copied to the device
+        if rc != FSI_OK:
+            raise FSIError(rc, lib.fsi_asm_last_error(None).decode())
+
+    @classmethod
+    def from_problem(cls, pb, stream=None):
+        """From a problem of the seeded input generator (its cell map, pattern and material)."""
+        cfg = pb.cfg
+        cd, cf = pb.cell_map()
+        h = [cfg.L[d] / cfg.n[d] for d in range(pb.dim)]
+        phys = dict(rho_f=cfg.rho_f, nu_f=cfg.nu_f, mu_s=cfg.mu_s, lambda_s=cfg.lambda_s, rho_s=cfg.rho_s,
+                    dt=cfg.dt, theta=cfg.theta)
+        return cls(pb.dim, cfg.n, h, pb.n, cd, cf, pb.rowptr, pb.colind, pb.fixed, phys, stream)
+
+    def _check(self, rc):
+        if rc != FSI_OK:
+            raise FSIError(rc, self._lib.fsi_asm_last_error(self._h).decode())
+
+    def _order(self):
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+
+    def residual(self, U, Uold, R):
+        """R = R(U) (float64 CUDA tensors of n entries; Uold None = 0); returns (min det F, max |R_i|)."""
+        mj, rm = ctypes.c_double(), ctypes.c_double()
+        self._order()
+        self._check(self._lib.fsi_asm_residual(self._h, _dev_ptr(U, self.n),
+                                               None if Uold is None else _dev_ptr(Uold, self.n), _dev_ptr(R, self.n),
+                                               ctypes.byref(mj), ctypes.byref(rm)))
+        return mj.value, rm.value
+
+    def jacobian(self, U, Uold, vals):
+        """vals = dR/dU in CSR order (float64 CUDA tensor of nnz entries); returns min det F."""
+        mj = ctypes.c_double()
+        self._order()
+        self._check(self._lib.fsi_asm_jacobian(self._h, _dev_ptr(U, self.n),
+                                               None if Uold is None else _dev_ptr(Uold, self.n),
+                                               _dev_ptr(vals, self.nnz), ctypes.byref(mj)))
+        return mj.value
+
+    def axpy(self, alpha, x, y):
+        """y += alpha x (float64 CUDA tensors of n entries)."""
+        self._order()
+        self._check(self._lib.fsi_asm_axpy(self._h, float(alpha), _dev_ptr(x, self.n), _dev_ptr(y, self.n)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.fsi_asm_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def default_train_params(**overrides) -> TrainParams:

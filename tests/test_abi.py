@@ -34,6 +34,27 @@ def test_header_symbols_exported(lib):
     assert sorted(P.EXPORTED) == names
 
 
+def test_peaks_library_exports_its_header(lib):
+    """libfsi_peaks.so (the FMA-throughput probes of the rooflines) loads and exports
+    every function include/fsi_peaks.h declares."""
+    import paper_1801_05648_gb300 as P
+    text = open(os.path.join(ROOT, "include", "fsi_peaks.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = sorted(set(re.findall(r"\b(fsi_[a-z_]+)\s*\(", text)))
+    assert names == sorted(P.fsi.PEAKS_EXPORTED)
+    peaks = ctypes.CDLL(P.fsi.PEAKS_LIB_PATH)
+    for name in names:
+        assert hasattr(peaks, name), name
+    # argument validation needs no device
+    f = peaks.fsi_probe_fma_rate
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_double)]
+    out = ctypes.c_double()
+    assert f(16, 10, 1, ctypes.byref(out), None) == -1
+    assert f(64, 0, 1, ctypes.byref(out), None) == -1
+    assert f(64, 10, 1, None, None) == -1
+
+
 def test_default_params(lib):
     import paper_1801_05648_gb300 as P
     p2, p3 = P.default_params(2), P.default_params(3)
@@ -175,7 +196,8 @@ def _header_struct_fields(name):
     return fields
 
 
-@pytest.mark.parametrize("cname,pyname", [("fsi_params", "Params"), ("fsi_stats", "Stats")])
+@pytest.mark.parametrize("cname,pyname", [("fsi_params", "Params"), ("fsi_stats", "Stats"),
+                                          ("fsi_asm_mesh", "AsmMesh"), ("fsi_asm_physics", "AsmPhysics")])
 def test_binding_structs_follow_the_header(cname, pyname):
     """The ctypes mirrors list the C structs' fields in the header's order (a
     field added to one side only would shift every later field)."""
