@@ -60,7 +60,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3),
                 ("solid_h", ctypes.c_double), ("rho_f", ctypes.c_double), ("nu_f", ctypes.c_double),
                 ("mu_s", ctypes.c_double), ("lambda_s", ctypes.c_double), ("rho_s", ctypes.c_double),
-                ("dt", ctypes.c_double), ("theta", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("theta", ctypes.c_double), ("pressure", ctypes.c_int)]
 
 
 def _load():
@@ -122,6 +122,7 @@ class FSIConfig:
     theta: float = 1.0
     prev_state: str = "rest"      # U^{n-1} = U ("rest") or 0 ("zero")
     rhs_kind: str = "manufactured"  # b = A x*, x* ~ N(0,1) ("manufactured") or b ~ N(0,1) ("normal")
+    pressure: str = "q1"          # "q1": continuous Q1 pressure; "p1disc": discontinuous P1 per fluid cell (Sec. 3.4)
 
     def with_(self, **kw) -> "FSIConfig":
         return replace(self, **kw)
@@ -157,6 +158,9 @@ class Problem:
             p.L[d] = cfg.L[d]
         p.solid_h, p.rho_f, p.nu_f = cfg.solid_h, cfg.rho_f, cfg.nu_f
         p.mu_s, p.lambda_s, p.rho_s, p.dt, p.theta = cfg.mu_s, cfg.lambda_s, cfg.rho_s, cfg.dt, cfg.theta
+        if cfg.pressure not in ("q1", "p1disc"):
+            raise ValueError(f"unknown pressure space {cfg.pressure!r}")
+        p.pressure = 1 if cfg.pressure == "p1disc" else 0
         self._h = lib.fsigen_create(ctypes.byref(p))
         if not self._h:
             raise ValueError(f"fsigen: invalid configuration {cfg}")
@@ -304,7 +308,7 @@ _problem_cache: dict = {}
 
 def get_problem(cfg: FSIConfig) -> Problem:
     key = (cfg.dim, tuple(cfg.n), tuple(cfg.L), cfg.solid_h, cfg.rho_f, cfg.nu_f, cfg.mu_s,
-           cfg.lambda_s, cfg.rho_s, cfg.dt, cfg.theta)
+           cfg.lambda_s, cfg.rho_s, cfg.dt, cfg.theta, cfg.pressure)
     if key not in _problem_cache:
         _problem_cache[key] = Problem(cfg)
     return _problem_cache[key]

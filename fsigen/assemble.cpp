@@ -27,8 +27,12 @@
 // is backward Euler (every previous-level term vanishes, J^theta = J),
 // theta = 1/2 Crank-Nicolson, theta = 1/2 + dt the shifted variant.
 //
-// Discretisation: Q2 velocity and displacement, continuous Q1 pressure on the
-// whole box (nodes at cell vertices), 3^d Gauss points per cell.  The Jacobian
+// Discretisation: Q2 velocity and displacement; pressure either continuous Q1 on
+// the whole box (nodes at cell vertices; the configurations' default) or the
+// paper's discontinuous P1 (Sec. 3.4: Q2-Q2-P1disc), one linear polynomial per
+// fluid cell, p = p_0 + p_1 (2 xi_1 - 1) + ... + p_d (2 xi_d - 1) in the cell's
+// reference coordinates xi (linear in x on the affine box cells), no pressure in
+// solid cells; 3^d Gauss points per cell.  The Jacobian
 // is the exact derivative of the discrete residual, taken by forward-mode
 // dual numbers per cell (Thm. 3.3 lists the derivatives this reproduces).
 //
@@ -95,6 +99,7 @@ struct Params {
   double L[3];       // box lengths
   double solid_h;    // solid = cells whose centroid has last coordinate < solid_h
   double rho_f, nu_f, mu_s, lambda_s, rho_s, dt, theta;
+  int pressure;      // 0: continuous Q1, 1: discontinuous P1 (Q2-Q2-P1disc)
 };
 
 // 1D Q2 Lagrange basis on [0,1] with nodes 0, 1/2, 1, and derivatives.
@@ -122,7 +127,9 @@ struct Problem {
   std::vector<uint8_t> node_udir;      // Q2 node: u Dirichlet
   std::vector<uint8_t> p_active;       // Q1 node touches a fluid cell
   std::vector<int64_t> dof_v, dof_u;   // Q2 node -> first global DOF of its v / u block
-  std::vector<int64_t> dof_p;          // Q1 node -> global DOF
+  std::vector<int64_t> dof_p;          // Q1 node -> global DOF (continuous Q1 pressure)
+  std::vector<int64_t> cell_pdof;      // cell -> first of its d+1 pressure DOFs, -1 in solid cells (P1disc)
+  bool pdisc = false;                  // discontinuous P1 pressure
   int64_t off[6];                      // m | s_v | s_u | f_v | f_p | n
   int64_t ndof;
   // CSR pattern
@@ -167,7 +174,7 @@ inline void cells_of_q1(int i, int ncell, int& lo, int& hi) {
 void build_tables(Problem& p) {
   const int D = p.dim;
   p.nq2loc = (D == 2) ? 9 : 27;
-  p.nq1loc = (D == 2) ? 4 : 8;
+  p.nq1loc = p.pdisc ? D + 1 : ((D == 2) ? 4 : 8);   // pressure basis functions per cell
   p.nloc = 2 * p.nq2loc * D + p.nq1loc;
   p.nqp = (D == 2) ? 9 : 27;
   p.nfqp = (D == 2) ? 3 : 9;
@@ -192,9 +199,13 @@ void build_tables(Problem& p) {
       }
     }
     for (int a = 0; a < p.nq1loc; ++a) {
-      int ai[3] = {a % 2, (a / 2) % 2, a / 4};
       double val = 1.0;
-      for (int d = 0; d < D; ++d) val *= q1(ai[d], xi[d]);
+      if (p.pdisc) {
+        val = (a == 0) ? 1.0 : 2.0 * xi[a - 1] - 1.0;
+      } else {
+        int ai[3] = {a % 2, (a / 2) % 2, a / 4};
+        for (int d = 0; d < D; ++d) val *= q1(ai[d], xi[d]);
+      }
       p.Npq[q * p.nq1loc + a] = val;
     }
   }
@@ -261,7 +272,7 @@ template <int D, class T>
 void cell_residual(const Problem& pb, bool solid, bool outflow, const uint8_t* mesh_row,
                    const T* U, const double* Vold, const double* Uold, T* R, double* minJ) {
   constexpr int NQ2 = (D == 2) ? 9 : 27;
-  constexpr int NQ1 = (D == 2) ? 4 : 8;
+  const int NQ1 = pb.nq1loc;   // pressure basis functions of the cell
   const Params& P = pb.P;
   const int NL = 2 * NQ2 * D + NQ1;
   const T zero = Zero<T>::get();
@@ -572,7 +583,9 @@ void classify(Problem& p) {
   p.off[2] = p.off[1] + n_s * D;
   p.off[3] = p.off[2] + n_s * D;
   p.off[4] = p.off[3] + n_f * D;
-  p.off[5] = p.off[4] + p.n_q1;
+  int64_t n_fluid_cells = 0;
+  for (int64_t c = 0; c < p.n_cells; ++c) n_fluid_cells += p.cell_solid[c] ? 0 : 1;
+  p.off[5] = p.off[4] + (p.pdisc ? (int64_t)(D + 1) * n_fluid_cells : p.n_q1);
   p.ndof = p.off[5];
   p.dof_v.assign(p.n_q2, -1); p.dof_u.assign(p.n_q2, -1); p.dof_p.assign(p.n_q1, -1);
   int64_t is = 0, jf = 0;
@@ -580,7 +593,15 @@ void classify(Problem& p) {
     if (p.node_solid[a]) { p.dof_v[a] = p.off[1] + is * D; p.dof_u[a] = p.off[2] + is * D; ++is; }
     else { p.dof_u[a] = p.off[0] + jf * D; p.dof_v[a] = p.off[3] + jf * D; ++jf; }
   }
-  for (int64_t a = 0; a < p.n_q1; ++a) p.dof_p[a] = p.off[4] + a;
+  if (!p.pdisc) {
+    for (int64_t a = 0; a < p.n_q1; ++a) p.dof_p[a] = p.off[4] + a;
+  } else {
+    p.cell_pdof.assign(p.n_cells, -1);
+    int64_t k = p.off[4];
+    for (int64_t c = 0; c < p.n_cells; ++c)
+      if (!p.cell_solid[c]) { p.cell_pdof[c] = k; k += D + 1; }
+    for (int64_t a = 0; a < p.n_q1; ++a) p.p_active[a] = 0;   // no nodal pressure
+  }
 }
 
 // Shared-cell flags between two Q2 nodes (or a Q1 node and a Q2 node): bit0 = a
@@ -665,8 +686,27 @@ void row_columns(const Problem& p, int kind, int64_t a, int64_t row, std::vector
                  std::vector<NodeNbr>& nb1, std::vector<int64_t>& cols) {
   const int D = p.dim;
   cols.clear();
-  bool fixed = (kind == 0 && p.node_vdir[a]) || (kind == 1 && p.node_udir[a]) || (kind == 2 && !p.p_active[a]);
+  bool fixed = (kind == 0 && p.node_vdir[a]) || (kind == 1 && p.node_udir[a]) ||
+               (kind == 2 && !p.pdisc && !p.p_active[a]);
   if (fixed) { cols.push_back(row); return; }
+  if (kind == 2 && p.pdisc) {
+    // discontinuous pressure row of fluid cell a: the v and u DOFs of the cell's Q2
+    // nodes, class by class (m, s_v, s_u, f_v), nodes in increasing index order
+    int c[3] = {0, 0, 0}; unflatten(a, p.P.n, D, c);
+    std::vector<int64_t> nodes;
+    const int NQ2 = p.nq2loc;
+    for (int l = 0; l < NQ2; ++l) {
+      int ai[3] = {l % 3, (l / 3) % 3, l / 9}, ii[3] = {0, 0, 0};
+      for (int d = 0; d < D; ++d) ii[d] = 2 * c[d] + ai[d];
+      nodes.push_back(q2_index(p, ii));
+    }
+    std::sort(nodes.begin(), nodes.end());
+    for (int64_t b : nodes) if (!p.node_solid[b] && !p.node_udir[b]) for (int i = 0; i < D; ++i) cols.push_back(p.dof_u[b] + i);
+    for (int64_t b : nodes) if (p.node_solid[b] && !p.node_vdir[b]) for (int i = 0; i < D; ++i) cols.push_back(p.dof_v[b] + i);
+    for (int64_t b : nodes) if (p.node_solid[b] && !p.node_udir[b]) for (int i = 0; i < D; ++i) cols.push_back(p.dof_u[b] + i);
+    for (int64_t b : nodes) if (!p.node_solid[b] && !p.node_vdir[b]) for (int i = 0; i < D; ++i) cols.push_back(p.dof_v[b] + i);
+    return;
+  }
   nb2.clear(); nb1.clear();
   int need = 0;   // bit0: fluid-cell couplings, bit1: solid-cell couplings
   bool want_v = true, want_p = false;
@@ -689,7 +729,21 @@ void row_columns(const Problem& p, int kind, int64_t a, int64_t row, std::vector
   if (want_v) for (auto& b : nb2) if ((b.flags & need) && !p.node_solid[b.node] && !p.node_vdir[b.node])
     for (int i = 0; i < D; ++i) cols.push_back(p.dof_v[b.node] + i);
   // f_p (only through fluid cells)
-  if (want_p) for (auto& b : nb1) if ((b.flags & 1) && p.p_active[b.node]) cols.push_back(p.dof_p[b.node]);
+  if (want_p && !p.pdisc)
+    for (auto& b : nb1) if ((b.flags & 1) && p.p_active[b.node]) cols.push_back(p.dof_p[b.node]);
+  if (want_p && p.pdisc) {
+    // the pressure DOFs of the fluid cells containing node a (cells in lexicographic order)
+    int ii[3] = {0, 0, 0}; unflatten(a, p.nq2, D, ii);
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) cells_of_q2(ii[d], p.P.n[d], lo[d], hi[d]);
+    int c[3] = {0, 0, 0};
+    for (c[2] = lo[2]; c[2] <= hi[2]; ++c[2])
+      for (c[1] = lo[1]; c[1] <= hi[1]; ++c[1])
+        for (c[0] = lo[0]; c[0] <= hi[0]; ++c[0]) {
+          const int64_t pd = p.cell_pdof[cell_index(p, c)];
+          if (pd >= 0) for (int k = 0; k <= D; ++k) cols.push_back(pd + k);
+        }
+  }
 }
 
 struct RowInfo { std::vector<int8_t> kind; std::vector<int64_t> node; };
@@ -701,7 +755,13 @@ void build_row_info(const Problem& p, RowInfo& ri) {
       ri.kind[p.dof_v[a] + i] = 0; ri.node[p.dof_v[a] + i] = a;
       ri.kind[p.dof_u[a] + i] = 1; ri.node[p.dof_u[a] + i] = a;
     }
-  for (int64_t a = 0; a < p.n_q1; ++a) { ri.kind[p.dof_p[a]] = 2; ri.node[p.dof_p[a]] = a; }
+  if (!p.pdisc) {
+    for (int64_t a = 0; a < p.n_q1; ++a) { ri.kind[p.dof_p[a]] = 2; ri.node[p.dof_p[a]] = a; }
+  } else {
+    for (int64_t c = 0; c < p.n_cells; ++c)
+      if (p.cell_pdof[c] >= 0)
+        for (int k = 0; k <= p.dim; ++k) { ri.kind[p.cell_pdof[c] + k] = 2; ri.node[p.cell_pdof[c] + k] = c; }
+  }
 }
 
 void build_pattern(Problem& p) {
@@ -718,7 +778,8 @@ void build_pattern(Problem& p) {
       row_columns(p, ri.kind[r], ri.node[r], r, nb2, nb1, cols);
       counts[r] = (int64_t)cols.size();
       int k = ri.kind[r]; int64_t a = ri.node[r];
-      p.row_fixed[r] = ((k == 0 && p.node_vdir[a]) || (k == 1 && p.node_udir[a]) || (k == 2 && !p.p_active[a])) ? 1 : 0;
+      p.row_fixed[r] = ((k == 0 && p.node_vdir[a]) || (k == 1 && p.node_udir[a]) ||
+                        (k == 2 && !p.pdisc && !p.p_active[a])) ? 1 : 0;
     }
   }
   for (int64_t r = 0; r < n; ++r) p.rowptr[r + 1] = p.rowptr[r] + counts[r];
@@ -748,6 +809,12 @@ void cell_dofs(const Problem& p, const int* c, int64_t* gdof, int64_t* q2nodes, 
       gdof[a * D + i] = p.dof_v[node] + i;
       gdof[NQ2 * D + a * D + i] = p.dof_u[node] + i;
     }
+  }
+  if (p.pdisc) {
+    // solid cells carry no pressure: their pressure slots point at the first p DOF and are masked
+    const int64_t pd = p.cell_pdof[cell_index(p, c)];
+    for (int a = 0; a < NQ1; ++a) { q1nodes[a] = -1; gdof[2 * NQ2 * D + a] = pd >= 0 ? pd + a : p.off[4]; }
+    return;
   }
   for (int a = 0; a < NQ1; ++a) {
     int ai[3] = {a % 2, (a / 2) % 2, a / 4};
@@ -831,6 +898,12 @@ int assemble(Problem& p, const double* Uglob, const double* Uold, double* Rglob,
   return fail;
 }
 
+// Element assembly for the problem's element (NL = 2 * NQ2 * dim + pressure basis size).
+int assemble_any(Problem& p, const double* U, const double* Uold, double* R, double* vals, double* minJ) {
+  if (p.dim == 2) return p.pdisc ? assemble<2, 39>(p, U, Uold, R, vals, minJ) : assemble<2, 40>(p, U, Uold, R, vals, minJ);
+  return p.pdisc ? assemble<3, 166>(p, U, Uold, R, vals, minJ) : assemble<3, 170>(p, U, Uold, R, vals, minJ);
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -842,6 +915,7 @@ struct fsigen_params {
   double L[3];
   double solid_h;
   double rho_f, nu_f, mu_s, lambda_s, rho_s, dt, theta;
+  int pressure;   // 0: continuous Q1 pressure, 1: discontinuous P1 (Q2-Q2-P1disc)
 };
 
 void* fsigen_create(const fsigen_params* in) {
@@ -855,6 +929,9 @@ void* fsigen_create(const fsigen_params* in) {
   p->P.solid_h = in->solid_h;
   p->P.rho_f = in->rho_f; p->P.nu_f = in->nu_f; p->P.mu_s = in->mu_s; p->P.lambda_s = in->lambda_s;
   p->P.rho_s = in->rho_s; p->P.dt = in->dt; p->P.theta = in->theta;
+  if (in->pressure != 0 && in->pressure != 1) { delete p; return nullptr; }
+  p->P.pressure = in->pressure;
+  p->pdisc = in->pressure == 1;
   classify(*p);
   build_tables(*p);
   build_pattern(*p);
@@ -894,6 +971,19 @@ void fsigen_dof_info(void* h, double* coords, int32_t* field, int32_t* comp, uin
       }
     }
   }
+  if (p->pdisc) {
+    // discontinuous pressure: the cell centre, component = basis function index
+    for (int64_t c = 0; c < p->n_cells; ++c) {
+      if (p->cell_pdof[c] < 0) continue;
+      int ci[3] = {0, 0, 0}; unflatten(c, p->P.n, D, ci);
+      for (int k = 0; k <= D; ++k) {
+        const int64_t g = p->cell_pdof[c] + k;
+        for (int d = 0; d < D; ++d) coords[g * D + d] = (2.0 * ci[d] + 1.0) * hq[d];
+        field[g] = 2; comp[g] = k; fixed[g] = p->row_fixed[g];
+      }
+    }
+    return;
+  }
   for (int64_t a = 0; a < p->n_q1; ++a) {
     int ii[3] = {0, 0, 0}; unflatten(a, p->nq1, D, ii);
     int64_t g = p->dof_p[a];
@@ -902,15 +992,14 @@ void fsigen_dof_info(void* h, double* coords, int32_t* field, int32_t* comp, uin
   }
 }
 
+
 // Jacobian values on the pattern at state U (previous step Uold, nullable = 0).
 // Returns 0, or 1 if a nonzero fell outside the pattern, 2 if J <= 0 somewhere.
 int fsigen_jacobian(void* h, const double* U, const double* Uold, double* vals, double* minJ) {
   Problem* p = static_cast<Problem*>(h);
   const int64_t nnz = p->rowptr.back();
   std::memset(vals, 0, sizeof(double) * nnz);
-  int fail;
-  if (p->dim == 2) fail = assemble<2, 40>(*p, U, Uold, nullptr, vals, minJ);
-  else fail = assemble<3, 170>(*p, U, Uold, nullptr, vals, minJ);
+  const int fail = assemble_any(*p, U, Uold, nullptr, vals, minJ);
   for (int64_t r = 0; r < p->ndof; ++r)
     if (p->row_fixed[r]) vals[p->rowptr[r]] = 1.0;
   if (fail) return 1;
@@ -921,8 +1010,7 @@ int fsigen_jacobian(void* h, const double* U, const double* Uold, double* vals, 
 int fsigen_residual(void* h, const double* U, const double* Uold, double* R, double* minJ) {
   Problem* p = static_cast<Problem*>(h);
   std::memset(R, 0, sizeof(double) * p->ndof);
-  if (p->dim == 2) assemble<2, 40>(*p, U, Uold, R, nullptr, minJ);
-  else assemble<3, 170>(*p, U, Uold, R, nullptr, minJ);
+  assemble_any(*p, U, Uold, R, nullptr, minJ);
   for (int64_t r = 0; r < p->ndof; ++r) if (p->row_fixed[r]) R[r] = 0.0;
   return (*minJ <= 0.0) ? 2 : 0;
 }
@@ -936,7 +1024,7 @@ int fsigen_residual(void* h, const double* U, const double* Uold, double* R, dou
 // for 3D problems.
 int fsigen_node_map(void* h, int32_t* node_dof, int32_t* patch) {
   Problem* p = static_cast<Problem*>(h);
-  if (p->dim != 2) return -1;
+  if (p->dim != 2 || p->pdisc) return -1;   // the stage's patch layout assumes nodal Q1 pressure
   const int nx = p->nq2[0], ny = p->nq2[1];
   for (int64_t a = 0; a < p->n_q2; ++a) {
     const int i = (int)(a % nx), j = (int)(a / nx);

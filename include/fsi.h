@@ -57,14 +57,14 @@ enum {
   FSI_X0_GIVEN = 1,        /* fsi_solve starts from the x passed in (else from 0) */
   FSI_USE_GRAPHS = 2,      /* replay each FGMRES iteration as one captured CUDA graph */
   FSI_NO_RIGID_MODES = 4,  /* solid AMG with translations only, even when coordinates are given */
-  FSI_CLUSTER_COARSE = 8,  /* run the coarse AMG levels (matrices <= 6 MB) of each V-cycle in one
-                              16-CTA thread-block-cluster launch instead of one launch per step
-                              (fewer launches, but slower on the 256x128 case: 26.7 vs 15.7 ms) */
+  FSI_CLUSTER_COARSE = 8,  /* run the coarse AMG levels (matrices <= cluster_max_bytes) of each
+                              V-cycle in one 16-CTA thread-block-cluster launch instead of one launch
+                              per step (fewer launches, but measured slower than the per-level path) */
   FSI_LEARNED = 16,        /* apply the learned correction stage after P^-1 in every FGMRES
                               iteration (needs fsi_learned_setup and weights; see below) */
-  FSI_NO_PDL = 32,         /* launch the solve's kernels without programmatic dependent launch
+  FSI_NO_PDL = 32,         /* launch the context's kernels without programmatic dependent launch
                               (each kernel then waits for the previous one to finish before it
-                              is scheduled).  Process-wide: the last fsi_setup's choice applies */
+                              is scheduled) */
   FSI_GRID_COARSE = 64,    /* like FSI_CLUSTER_COARSE, but the coarse levels run as one cooperative
                               launch over half the GPU with a software grid barrier (bounded
                               waits: a barrier that times out makes fsi_solve return FSI_ECUDA).
@@ -101,21 +101,19 @@ typedef struct fsi_params {
   /* SpMV launch shape: lanes per block row follow the mean row length (each lane
      takes at least 2 blocks in FP32, 8 in FP64); each lane loads spmv_unroll blocks
      (4 or 8; 8 applies to blocks of at most 24 bytes) before multiplying (4).
-     Process-wide: the last fsi_setup's values apply. */
+     Like every launch knob, it applies to the calls on this context only. */
   int spmv_unroll;
   /* learned stage: take the correction only when ||r' - A c|| < learned_accept * ||r'||
      (0.1; at 0.3 and above the trained stage's accepted corrections stall FGMRES) */
   double learned_accept;
   /* SpMV L2 prefetch: 0 none, 1 each CTA bulk-prefetches its slice of the matrix arrays
      into L2 before waiting for the previous kernel, 2 the same with at most 5 persistent
-     CTAs per SM walking longer slices (1; measured on the 256x128 case: FP64 solve
-     52.2 -> 49.2 ms, FP32 unchanged, 2 slower).  Process-wide, like the other SpMV knobs. */
+     CTAs per SM walking longer slices (1) */
   int spmv_prefetch;
   /* FSI_CLUSTER_COARSE / FSI_GRID_COARSE: levels whose matrix values take at most this
-     many bytes run in the single coarse launch (6e6).  Process-wide. */
+     many bytes run in the single coarse launch (6e6) */
   double cluster_max_bytes;
-  /* Chebyshev degree on the coarser AMG levels (>= 1); 0 = cheb_degree on every level (2:
-     256x128 solve 14.3 -> 13.0 ms at 11-12 iterations; 1024x512 +3%, 35 vs 33 iterations) */
+  /* Chebyshev degree on the coarser AMG levels (>= 1); 0 = cheb_degree on every level (2) */
   int cheb_degree_coarse;
   /* FSI_FLUID_GMRES: inner GMRES steps k per A_ff^-1, 1..32 (4) */
   int fluid_gmres_iters;

@@ -69,7 +69,7 @@ constexpr int kCoarseMaxLevels = 8;
 constexpr int kCoarseMaxDeg = 16;
 // levels whose matrix has at most this many value bytes run in the cluster (fsi_params.cluster_max_bytes)
 inline double& coarse_max_bytes() {
-  static double b = 6.0e6;
+  thread_local double b = 6.0e6;   // per thread, like the other launch knobs (common.cuh)
   return b;
 }
 

@@ -660,7 +660,8 @@ void asm_jacobian(Assembler& A, const double* U, const double* Uold, double* val
 }
 
 void asm_axpy(Assembler& A, double alpha, const double* x, double* y) {
-  k_axpy_inplace<<<div_up(A.n, 256) < 152 * 16 ? div_up(A.n, 256) : 152 * 16, 256, 0, A.s>>>(A.n, alpha, x, y);
+  const int cap = device_sms() * 16;
+  k_axpy_inplace<<<div_up(A.n, 256) < cap ? div_up(A.n, 256) : cap, 256, 0, A.s>>>(A.n, alpha, x, y);
   FSI_CHECK_LAUNCH();
   FSI_CUDA(cudaStreamSynchronize(A.s));
 }

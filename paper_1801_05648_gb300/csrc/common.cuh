@@ -52,9 +52,27 @@ __device__ __forceinline__ void dep_wait() {
 #endif
 }
 
+// Launch knobs (programmatic dependent launch here; the SpMV shape and the coarse
+// V-cycle threshold below) are per thread: every entry point that takes a context
+// applies that context's values for the duration of the call (KnobScope in
+// fsi_api.cu), so contexts with different parameters do not interfere.
 inline bool& pdl_enabled() {
-  static bool on = true;
+  thread_local bool on = true;
   return on;
+}
+
+// Streaming multiprocessors of the current device (looked up once per device).
+inline int device_sms() {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152;
+  int v = __atomic_load_n(&cache[dev], __ATOMIC_RELAXED);
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    __atomic_store_n(&cache[dev], v, __ATOMIC_RELAXED);
+  }
+  return v;
 }
 
 template <class... KArgs, class... Args>
@@ -167,7 +185,7 @@ struct SpmvTuning {
   int setup_depth = 0; // > 0 while matrices are being built: no reads before the dependency wait
 };
 inline SpmvTuning& spmv_tuning() {
-  static SpmvTuning t;
+  thread_local SpmvTuning t;
   return t;
 }
 
@@ -204,10 +222,5 @@ void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
   ++g_kernel_launches;
 }
 
-// Streams and scratch shared by one context.
-struct Exec {
-  cudaStream_t stream = nullptr;
-  int num_sms = 152;
-};
 
 }  // namespace fsi

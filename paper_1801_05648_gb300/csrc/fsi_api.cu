@@ -20,13 +20,40 @@ namespace {
 
 thread_local std::string g_setup_error;
 
+// The context's launch knobs (SpMV unroll depth and L2 prefetch, programmatic
+// dependent launch, the coarse V-cycle threshold) applied to this thread for one
+// call, the thread's previous values restored afterwards.
+struct KnobScope {
+  fsi::SpmvTuning tuning;
+  bool pdl;
+  double coarse_bytes;
+  explicit KnobScope(const fsi::SolverParams& p)
+      : tuning(fsi::spmv_tuning()), pdl(fsi::pdl_enabled()), coarse_bytes(fsi::coarse_max_bytes()) {
+    fsi::spmv_tuning().unroll = p.spmv_unroll;
+    fsi::spmv_tuning().prefetch = p.spmv_prefetch;
+    fsi::pdl_enabled() = (p.flags & FSI_NO_PDL) == 0;
+    fsi::coarse_max_bytes() = p.cluster_max_bytes;
+  }
+  ~KnobScope() {
+    const int depth = fsi::spmv_tuning().setup_depth;
+    fsi::spmv_tuning() = tuning;
+    fsi::spmv_tuning().setup_depth = depth;
+    fsi::pdl_enabled() = pdl;
+    fsi::coarse_max_bytes() = coarse_bytes;
+  }
+  KnobScope(const KnobScope&) = delete;
+  KnobScope& operator=(const KnobScope&) = delete;
+};
+
 // Run f, turning exceptions into status codes; the message goes to the context
-// (or, for calls without one, to the thread's fsi_last_error(NULL) text).
+// (or, for calls without one, to the thread's fsi_last_error(NULL) text).  Calls
+// with a context run on its device and with its launch knobs.
 template <class F>
 int guarded(fsi_ctx* ctx, F&& f) {
   std::string& err = ctx ? ctx->C.err : g_setup_error;
   try {
     fsi::DeviceGuard on_device(ctx ? ctx->C.device : -1);
+    KnobScope knobs(ctx ? ctx->C.prm : fsi::SolverParams());
     f();
     err.clear();
     return FSI_OK;
@@ -187,10 +214,7 @@ int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const in
       FSI_CUDA(cudaStreamCreateWithFlags(&ctx->C.s, cudaStreamNonBlocking));
       ctx->C.own_stream = true;
     }
-    fsi::spmv_tuning().unroll = ctx->C.prm.spmv_unroll;
-    fsi::spmv_tuning().prefetch = ctx->C.prm.spmv_prefetch;
-    fsi::coarse_max_bytes() = ctx->C.prm.cluster_max_bytes;
-    fsi::pdl_enabled() = (ctx->C.prm.flags & FSI_NO_PDL) == 0;
+    KnobScope knobs(ctx->C.prm);
     fsi::context_setup(ctx->C, rowptr, colind, vals, node_coords);
   });
   if (rc != FSI_OK) {

@@ -230,7 +230,7 @@ void launch_mlp(const MlpGeom& g, const uint16_t* w16, const double* rp, double*
     attr = true;
   }
   int64_t b = (g.n_nodes + kNodeThreads - 1) / kNodeThreads;
-  if (b > 152 * 3) b = 152 * 3;   // three 64 KB blocks fit one SM: one wave, weights loaded once per block
+  if (b > device_sms() * 3) b = device_sms() * 3;   // three 64 KB blocks fit one SM: one wave, weights loaded once per block
   launch_k(k_mlp<MODE>, (int)(b < 1 ? 1 : b), kNodeThreads, kMlpSmem, s, g, w16, rp, c, F, rho, H1, H2, ld);
 }
 
@@ -507,13 +507,13 @@ __global__ void k_square_partial(int64_t n, const double* __restrict__ x, double
 
 inline int grid_elem(int64_t n) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > device_sms() * 8) b = device_sms() * 8;
   return (int)(b < 1 ? 1 : b);
 }
 
 inline int grid_nodes(int64_t n_nodes) {
   int64_t b = (n_nodes + kNodeThreads - 1) / kNodeThreads;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > device_sms() * 8) b = device_sms() * 8;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -769,7 +769,7 @@ double trainer_step(Trainer& T, Context& C, const double* rp, bool grad) {
                                                     T.dH2.p, ld);
   FSI_CHECK_LAUNCH();
   // weight gradients: dW1 = [F;1] dH1^T, dW2 = [gelu(H1);1] dH2^T, dW3 = [gelu(H2);1] dY^T
-  const int G = (int)std::min<int64_t>(2 * 152, std::max<int64_t>(1, (nn + 255) / 256));
+  const int G = (int)std::min<int64_t>(2 * device_sms(), std::max<int64_t>(1, (nn + 255) / 256));
   const int64_t chunk = ((nn + G - 1) / G + 31) / 32 * 32;
   const size_t need = (size_t)G * (kMlpHidden + 1) * kMlpHidden;
   if (T.partial.n < need) T.partial.alloc(need);

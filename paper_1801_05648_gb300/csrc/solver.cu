@@ -147,7 +147,7 @@ __global__ void k_set_first(double* __restrict__ g, int len, double beta) {
 
 inline int grid_n(int64_t n) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > device_sms() * 8) b = device_sms() * 8;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -330,9 +330,9 @@ void aff_gmres(Context& C, const T* r, T* x, cudaStream_t st) {
     double* hj1 = F.h1.p + (size_t)j * ld;
     double* hj2 = F.h2.p + (size_t)j * ld;
     mdot(n, V, n, F.zero.p, j + 1, F.w.p, F.part.p, hj1, ld, st);              // CGS, twice
-    maxpy(n, V, n, F.zero.p, j + 1, hj1, 1.0, F.w.p, nullptr, st);
+    maxpy(n, V, n, F.zero.p, j + 1, hj1, 1.0, F.w.p, nullptr, k + 1, st);
     mdot(n, V, n, F.zero.p, j + 1, F.w.p, F.part.p, hj2, ld, st);
-    maxpy(n, V, n, F.zero.p, j + 1, hj2, 1.0, F.w.p, F.npart.p, st);
+    maxpy(n, V, n, F.zero.p, j + 1, hj2, 1.0, F.w.p, F.npart.p, k + 1, st);
     finish_norm(F.npart.p, F.nrm.p + j, st);                                    // h_{j+1,j} = ||w||
     if (j + 1 < k)
       launch_k(k_unit_scale, grid_n(n), 256, 0, st, n, (const double*)F.w.p, (const double*)(F.nrm.p + j), 0,
@@ -341,7 +341,7 @@ void aff_gmres(Context& C, const T* r, T* x, cudaStream_t st) {
   launch_k(k_inner_ls, 1, 32, 0, st, k, (const double*)F.h1.p, (const double*)F.h2.p, ld, (const double*)F.nrm.p,
            (const double*)F.beta.p, F.y.p);
   FSI_CUDA(cudaMemsetAsync(F.w.p, 0, sizeof(double) * n, st));
-  maxpy(n, Z, n, F.zero.p, k, F.y.p, -1.0, F.w.p, nullptr, st);                 // x = Z y
+  maxpy(n, Z, n, F.zero.p, k, F.y.p, -1.0, F.w.p, nullptr, k, st);              // x = Z y
   copy_as<double, T>(n, F.w.p, x, st);
 }
 
@@ -699,8 +699,9 @@ void ensure_krylov(Context& C) {
   const int m = C.prm.restart;
   if (C.m_alloc == m) return;
   const int64_t n = C.n;
-  C.V.alloc((size_t)(m + 1) * n);
-  C.Z.alloc((size_t)m * n);
+  C.ldv = (n + 31) / 32 * 32;
+  C.V.alloc((size_t)(m + 1) * C.ldv);
+  C.Z.alloc((size_t)m * C.ldv);
   C.Hh.alloc((size_t)(m + 1) * m);
   C.cs.alloc(m + 1); C.sn.alloc(m + 1); C.g.alloc(m + 2); C.y.alloc(m + 1);
   C.h1.alloc(m + 2); C.h2.alloc(m + 2); C.scal.alloc(8);
@@ -724,29 +725,30 @@ void iteration_body(Context& C) {
   const int64_t n = C.n;
   const int m = C.prm.restart;
   PrecWork<T>& W = pwork<T>(C);
-  launch_k(k_col_in<double, T>, grid_n(n), 256, 0, C.s, n, (const double*)C.V.p, n, (const int*)C.jdev.p, 0, W.in.p);
+  launch_k(k_col_in<double, T>, grid_n(n), 256, 0, C.s, n, (const double*)C.V.p, C.ldv, (const int*)C.jdev.p, 0,
+           W.in.p);
   precond_apply<T>(C, W.in.p, W.out.p);
-  launch_k(k_col_out<T>, grid_n(n), 256, 0, C.s, n, (const T*)W.out.p, C.zfix.p, C.Z.p, n, (const int*)C.jdev.p);
+  launch_k(k_col_out<T>, grid_n(n), 256, 0, C.s, n, (const T*)W.out.p, C.zfix.p, C.Z.p, C.ldv, (const int*)C.jdev.p);
   apply_operator(C, C.zfix.p, C.wfix.p);
-  if (C.harvest) harvest_residual(n, C.V.p, n, C.jdev.p, C.wfix.p, C.harvest, C.harvest_n, C.s);
+  if (C.harvest) harvest_residual(n, C.V.p, C.ldv, C.jdev.p, C.wfix.p, C.harvest, C.harvest_n, C.s);
   if (C.prm.flags & LEARNED) {
     // learned stage: r' = v_j - A z_j, c = MLP(r'), t = A c; take z_j + c only
     // when ||r' - t|| < tau ||r'|| (otherwise the plain preconditioner's z_j stands)
     Learned& L = C.learned;
-    learned_residual(n, C.V.p, n, C.jdev.p, C.wfix.p, L.rp.p, L.part.p, C.s);
+    learned_residual(n, C.V.p, C.ldv, C.jdev.p, C.wfix.p, L.rp.p, L.part.p, C.s);
     mlp_apply(learned_geom(L, C.off), L.w16.p, L.rp.p, L.c.p, C.s);
     apply_operator(C, L.c.p, L.t.p);
     learned_decide(n, L.rp.p, L.t.p, C.prm.learned_accept, L.part.p, L.counters.p, C.s);
-    learned_commit(n, L.counters.p, L.c.p, L.t.p, C.Z.p, n, C.jdev.p, C.wfix.p, C.s);
+    learned_commit(n, L.counters.p, L.c.p, L.t.p, C.Z.p, C.ldv, C.jdev.p, C.wfix.p, C.s);
   }
-  mdot(n, C.V.p, n, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h1.p, m + 1, C.s);
-  maxpy(n, C.V.p, n, C.jdev.p, 1, C.h1.p, 1.0, C.wfix.p, nullptr, C.s);
-  mdot(n, C.V.p, n, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h2.p, m + 1, C.s);
-  maxpy(n, C.V.p, n, C.jdev.p, 1, C.h2.p, 1.0, C.wfix.p, C.npart.p, C.s);
+  mdot(n, C.V.p, C.ldv, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h1.p, m + 1, C.s);
+  maxpy(n, C.V.p, C.ldv, C.jdev.p, 1, C.h1.p, 1.0, C.wfix.p, nullptr, m + 1, C.s);
+  mdot(n, C.V.p, C.ldv, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h2.p, m + 1, C.s);
+  maxpy(n, C.V.p, C.ldv, C.jdev.p, 1, C.h2.p, 1.0, C.wfix.p, C.npart.p, m + 1, C.s);
   finish_norm(C.npart.p, C.scal.p, C.s);
   launch_k(k_givens, 1, 32, 0, C.s, m + 1, C.jdev.p, C.h1.p, C.h2.p, C.scal.p, C.Hh.p, C.cs.p, C.sn.p, C.g.p,
            C.scal.p + 5, C.pinned_dev);
-  launch_k(k_scale_col, grid_n(n), 256, 0, C.s, n, C.wfix.p, C.scal.p, C.V.p, n, C.jdev.p);
+  launch_k(k_scale_col, grid_n(n), 256, 0, C.s, n, C.wfix.p, C.scal.p, C.V.p, C.ldv, C.jdev.p);
 }
 
 void run_iteration(Context& C) {
@@ -850,7 +852,7 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
     C.pinned_j[1] = k;
     FSI_CUDA(cudaMemcpyAsync(C.kdev.p, C.pinned_j + 1, sizeof(int), cudaMemcpyHostToDevice, C.s));
     launch_k(k_backsolve, 1, 32, 0, C.s, m + 1, C.kdev.p, C.Hh.p, C.g.p, C.y.p);
-    maxpy(n, C.Z.p, n, C.kdev.p, 0, C.y.p, -1.0, x, nullptr, C.s);
+    maxpy(n, C.Z.p, C.ldv, C.kdev.p, 0, C.y.p, -1.0, x, nullptr, m, C.s);
     ++C.last_cycles;
   }
   FSI_CUDA(cudaStreamSynchronize(C.s));

@@ -92,8 +92,9 @@ struct Context {
   double* harvest = nullptr;  // device, harvest_n x n: V_j - A z_j of the first iterations
   int harvest_n = 0;
   int last_accepted = 0;      // learned corrections taken in the last solve
-  // FGMRES storage
+  // FGMRES storage; basis columns V_i, Z_i at stride ldv (n rounded up to 32: 16-byte aligned columns)
   int m_alloc = 0;
+  int64_t ldv = 0;
   DBuf<double> V, Z, Hh, cs, sn, g, y, h1, h2, scal, partials, npart, zfix, wfix, rvec;
   DBuf<int> jdev, kdev;
   double* pinned = nullptr;   // host-mapped: [0] |g_{j+1}|/|b|, [1] breakdown flag, [2] h_{j+1,j}

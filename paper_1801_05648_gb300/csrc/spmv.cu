@@ -19,9 +19,9 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
   const SpmvTuning& tu = spmv_tuning();
   int rows_per_cta = per_pass;
   int blocks = div_up(A1.nbr, per_pass);
-  if (tu.prefetch >= 2 && blocks > 152 * tu.ctas_per_sm) {
+  if (tu.prefetch >= 2 && blocks > device_sms() * tu.ctas_per_sm) {
     // persistent: at most ctas_per_sm CTAs per SM, each over a longer contiguous slice
-    const int passes = div_up(blocks, 152 * tu.ctas_per_sm);
+    const int passes = div_up(blocks, device_sms() * tu.ctas_per_sm);
     rows_per_cta = passes * per_pass;
     blocks = div_up(A1.nbr, rows_per_cta);
   }

@@ -8,7 +8,7 @@ constexpr int kThreads = 256;
 
 inline int grid_for(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > device_sms() * 16) b = device_sms() * 16;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -158,6 +158,110 @@ __global__ void __launch_bounds__(kRedThreads) k_maxpy(int64_t n, const double* 
   }
 }
 
+// ---- 16-byte variants of the Gram-Schmidt products (basis columns, w and the
+// chunk starts 16-byte aligned): the FP64 products are issue-bound, so each thread
+// takes two consecutive elements per load instruction and the multi-dot eight
+// basis vectors per pass over its chunk, cutting the load, address and loop
+// instructions per FMA.  A block's chunk starts at an even element.
+constexpr int kDotCols = 8;
+
+__device__ __forceinline__ void chunk_of(int64_t n, int64_t& lo, int64_t& hi) {
+  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  chunk = (chunk + 1) & ~(int64_t)1;
+  lo = blockIdx.x * chunk;
+  hi = lo + chunk < n ? lo + chunk : n;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_mdot_partial_v2(int64_t n, const double* __restrict__ V,
+                                                                 int64_t ldv, const int* __restrict__ jcount,
+                                                                 int joff, const double* __restrict__ w,
+                                                                 double* __restrict__ partials) {
+  dep_wait();
+  __shared__ double sh[kDotCols][kRedThreads / 32];
+  const int J = *jcount + joff;
+  int64_t lo, hi;
+  chunk_of(n, lo, hi);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < J; i0 += kDotCols) {
+    const int ni = J - i0 < kDotCols ? J - i0 : kDotCols;
+    const double* v0 = V + (size_t)i0 * ldv;
+    double acc[kDotCols];
+#pragma unroll
+    for (int u = 0; u < kDotCols; ++u) acc[u] = 0.0;
+    for (int64_t r = lo + 2 * threadIdx.x; r < hi; r += 2 * blockDim.x) {
+      if (r + 1 < hi) {
+        const double2 wr = __ldg(reinterpret_cast<const double2*>(w + r));
+#pragma unroll
+        for (int u = 0; u < kDotCols; ++u)
+          if (u < ni) {
+            const double2 v = __ldcs(reinterpret_cast<const double2*>(v0 + (size_t)u * ldv + r));
+            acc[u] = fma(v.y, wr.y, fma(v.x, wr.x, acc[u]));
+          }
+      } else {
+        const double wr = __ldg(w + r);
+#pragma unroll
+        for (int u = 0; u < kDotCols; ++u)
+          if (u < ni) acc[u] = fma(__ldcs(v0 + (size_t)u * ldv + r), wr, acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kDotCols; ++u) {
+      double a = acc[u];
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+      if (lane == 0) sh[u][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < ni) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[threadIdx.x][q];
+      partials[(size_t)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// w -= sign * sum_i h[i] V_i over the block's chunk, two elements per thread and
+// load; each element sums the basis vectors in increasing order (as k_maxpy).
+__global__ void __launch_bounds__(kRedThreads) k_maxpy_v2(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                                          const int* __restrict__ jcount, int joff,
+                                                          const double* __restrict__ h, double sign,
+                                                          double* __restrict__ w, double* __restrict__ nrm_partials) {
+  dep_wait();
+  extern __shared__ double hs[];
+  __shared__ double sh[32];
+  const int J = *jcount + joff;
+  int64_t lo, hi;
+  chunk_of(n, lo, hi);
+  for (int i = threadIdx.x; i < J; i += blockDim.x) hs[i] = sign * h[i];
+  __syncthreads();
+  double nacc = 0.0;
+  for (int64_t r = lo + 2 * threadIdx.x; r < hi; r += 2 * blockDim.x) {
+    if (r + 1 < hi) {
+      double2 acc = *reinterpret_cast<const double2*>(w + r);
+      const double* vp = V + r;
+      for (int i = 0; i < J; ++i) {
+        const double hv = hs[i];
+        const double2 v = __ldcs(reinterpret_cast<const double2*>(vp + (size_t)i * ldv));
+        acc.x -= hv * v.x;
+        acc.y -= hv * v.y;
+      }
+      *reinterpret_cast<double2*>(w + r) = acc;
+      nacc += acc.x * acc.x + acc.y * acc.y;
+    } else {
+      double acc = w[r];
+      for (int i = 0; i < J; ++i) acc -= hs[i] * __ldcs(V + (size_t)i * ldv + r);
+      w[r] = acc;
+      nacc += acc * acc;
+    }
+  }
+  if (nrm_partials) {
+    nacc = block_sum(nacc, sh);
+    if (threadIdx.x == 0) nrm_partials[blockIdx.x] = nacc;
+  }
+}
+
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 }  // namespace
 
 template <class T>
@@ -201,13 +305,20 @@ double dot_host(int64_t n, const T* x, const T* y, double* partials, double* out
 
 void mdot(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* w, double* partials,
           double* h, int maxcols, cudaStream_t s) {
-  launch_k(k_mdot_partial, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, w, partials);
+  if (ldv % 2 == 0 && aligned16(V) && aligned16(w))
+    launch_k(k_mdot_partial_v2, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, w, partials);
+  else
+    launch_k(k_mdot_partial, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, w, partials);
   launch_k(k_reduce_cols, maxcols, kRedThreads, 0, s, partials, kRedBlocks, jcount, joff, h, 0);
 }
 
 void maxpy(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* h, double sign,
-           double* w, double* nrm_partials, cudaStream_t s) {
-  launch_k(k_maxpy, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, h, sign, w, nrm_partials);
+           double* w, double* nrm_partials, int maxcols, cudaStream_t s) {
+  if (maxcols > 0 && ldv % 2 == 0 && aligned16(V) && aligned16(w))
+    launch_k(k_maxpy_v2, kRedBlocks, kRedThreads, sizeof(double) * maxcols, s, n, V, ldv, jcount, joff, h, sign, w,
+             nrm_partials);
+  else
+    launch_k(k_maxpy, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, h, sign, w, nrm_partials);
 }
 
 void finish_norm(const double* partials, double* out, cudaStream_t s) {

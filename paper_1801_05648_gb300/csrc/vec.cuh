@@ -7,7 +7,9 @@
 
 namespace fsi {
 
-constexpr int kRedBlocks = 4 * 152;   // partial sums per reduction (4 CTAs per SM)
+// Partial sums per reduction: a fixed width, independent of the device, so that a
+// sum is formed in the same order everywhere (4 CTAs per SM on a 152-SM GB300).
+constexpr int kRedBlocks = 608;
 constexpr int kRedThreads = 256;
 
 // y = a x + b y  (y not read when b == 0)
@@ -31,9 +33,12 @@ template <class T> double dot_host(int64_t n, const T* x, const T* y, double* pa
 // h[i] = <V_i, w>, i < *jcount + joff
 void mdot(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* w, double* partials,
           double* h, int maxcols, cudaStream_t s);
-// w -= sum_i h[i] V_i; if nrm_partials != nullptr also writes per-block sums of w^2
+// w -= sum_i h[i] V_i; if nrm_partials != nullptr also writes per-block sums of w^2.
+// maxcols bounds the number of vectors (*jcount + joff) for the shared-memory copy
+// of h (0: unknown, the unvectorised kernel runs).  Both multi-products use 16-byte
+// loads when V's columns and w are 16-byte aligned (ldv even).
 void maxpy(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* h, double sign,
-           double* w, double* nrm_partials, cudaStream_t s);
+           double* w, double* nrm_partials, int maxcols, cudaStream_t s);
 // out = sqrt(sum partials)
 void finish_norm(const double* partials, double* out, cudaStream_t s);
 

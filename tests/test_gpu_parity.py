@@ -176,7 +176,7 @@ def test_graph_replay_is_bit_identical(torch_cuda):
 def test_launch_modes_are_bit_identical(torch_cuda):
     """Programmatic dependent launch on/off and the SpMV prefetch modes change only
     launch attributes and the assignment of rows to CTAs: every solve is bit-identical.
-    (Both knobs are process-wide; each fsi_setup sets them from its parameters.)"""
+    (Both knobs belong to the context: each call applies its own context's values.)"""
     torch = torch_cuda
     import paper_1801_05648_gb300 as P
     s, o, ref, _, mr = case("2d_64x32", torch)
