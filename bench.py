@@ -45,8 +45,10 @@ WORKLOAD_DESC = {
     "3d": "3D ALE-FSI Jacobian, 32x16x16 Q2/Q2/Q1 hex cells on [0,2]x[0,1]^2, solid slab z<0.25, n=434247",
     "2d_tiny": "2D ALE-FSI Jacobian, 16x16 Q2/Q2/Q1 cells, n=4645",
     "2d_512x256": "2D ALE-FSI Jacobian, 512x256 Q2/Q2/Q1 cells, n=2235141",
+    "2d_mid_p1disc": "2D ALE-FSI Jacobian, 256x128 cells with the Q2-Q2-P1disc element (discontinuous linear "
+                     "pressure per fluid cell), n=601092",
 }
-DEFAULT_STATES = {"2d_large": 1, "2d_mid": 5, "3d": 1}
+DEFAULT_STATES = {"2d_large": 1, "2d_mid": 5, "3d": 1, "2d_mid_p1disc": 1}
 
 
 def parse_args(argv=None):
@@ -57,7 +59,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="2d_large")
     ap.add_argument("--states", type=int, default=0, help="resident Jacobians (0: the workload's default)")
-    ap.add_argument("--secondary", default="2d_mid,3d", help="comma-separated secondary workloads ('' for none)")
+    ap.add_argument("--secondary", default="2d_mid,3d,2d_mid_p1disc",
+                    help="comma-separated secondary workloads ('' for none)")
+    ap.add_argument("--no-newton", action="store_true", help="skip the timed Newton step")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form timing")
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
@@ -564,7 +568,7 @@ def bench_ours(args):
                  "setup_s": statistics.mean(x.setup_s for x in st32[:ns]),
                  "precond_build_s_fp64": statistics.mean(V.build_s)}
         xl = None
-        if V.dim == 2 and not args.no_learned:
+        if V.dim == 2 and not args.no_learned and V.systems[0].cfg.pressure == "q1":
             pb = fsigen.get_problem(V.systems[0].cfg)
             nd, pt = pb.node_map()
             for g in V.solvers:
@@ -580,6 +584,13 @@ def bench_ours(args):
                           "iters64": st64[first0].iters}
         V.close()
         torch.cuda.empty_cache()
+
+    # ---- one quasi-Newton time step (Sec. 6 settings) on the 256x128 channel from rest with
+    # the FSI-2 inflow profile: residual and Jacobian assembled on the host (fsigen) against
+    # the whole loop on the device (fsi_asm_* + fsi_update_values)
+    newton_res = None
+    if world == 1 and not args.no_newton:
+        newton_res = newton_timing("2d_mid")
 
     # ---- the oracle on the host cores (child processes: no CUDA there)
     cpu = None
@@ -687,6 +698,7 @@ def bench_ours(args):
                                "how": "fsi_probe_fma_rate: 8 independent FMA chains per thread, 8 CTAs of 256 "
                                       "threads per SM, best of 5 launches"},
         "secondary": secondary,
+        "newton_step": newton_res,
         "err_vs_oracle": oracle_err,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -697,6 +709,55 @@ def bench_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def newton_timing(name: str):
+    """Wall seconds of one quasi-Newton time step (linear solves FP32-AMG to 1e-3,
+    stop at 1e-6 of the initial residual) with host and with device assembly."""
+    import numpy as np
+    import torch
+    import fsigen
+    import paper_1801_05648_gb300 as P
+    from paper_1801_05648_gb300 import learned, newton
+    cfg = fsigen.CONFIGS[name]
+    pb = fsigen.get_problem(cfg)
+    idx, prof = learned.inflow(pb)
+    bc = (idx, prof * learned.ramp(cfg.dt))
+    U = np.zeros(pb.n)
+    out = {"workload": name, "case": "first step of the channel from rest, FSI-2 inflow profile x ramp(dt)"}
+    newton.newton_step_device(pb, U, U.copy(), "fp32", fixed_values=bc)          # warm-up (builds, graphs)
+    t0 = time.perf_counter()
+    host = newton.newton_step(pb, U, U.copy(), newton.gpu_solver_factory("fp32"), fixed_values=bc)
+    host_s = time.perf_counter() - t0
+    dev = newton.newton_step_device(pb, U, U.copy(), "fp32", fixed_values=bc)
+    for k, r, sec in (("host_assembly", host, host_s), ("device_assembly", dev, dev.seconds)):
+        out[k] = {"seconds": sec, "iterations": r.iterations, "assemblies": r.assemblies,
+                  "linear_iters": r.linear_iters, "residual_reduction": r.residuals[-1] / r.residuals[0],
+                  "converged": bool(r.converged)}
+    # the assembly kernels alone at the converged state, against the host assembly
+    asm = P.FSIAssembler.from_problem(pb)
+    Ud = torch.tensor(dev.U, device="cuda")
+    R = torch.empty_like(Ud)
+    vals = torch.empty(int(pb.rowptr[-1]), dtype=torch.float64, device="cuda")
+    asm.residual(Ud, Ud, R)
+    asm.jacobian(Ud, Ud, vals)
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        asm.residual(Ud, Ud, R)
+    out["device_residual_s"] = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        asm.jacobian(Ud, Ud, vals)
+    out["device_jacobian_s"] = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    pb.jacobian(dev.U, dev.U)
+    out["host_jacobian_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pb.residual(dev.U, dev.U)
+    out["host_residual_s"] = time.perf_counter() - t0
+    asm.close()
+    return out
 
 
 # ------------------------------------------------------------------ reference arm

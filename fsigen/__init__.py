@@ -142,6 +142,8 @@ CONFIGS = {
     # Kirchhoff law (indefinite solid block, see the next entry)
     "2d_large": FSIConfig("2d_large", 2, (1024, 512)),
     "2d_large_amp5e-2": FSIConfig("2d_large_amp5e-2", 2, (1024, 512), amplitude=5e-2),
+    # the paper's Q2-Q2-P1disc element (Sec. 3.4) on the 256x128 mesh: 3 pressure DOFs per fluid cell
+    "2d_mid_p1disc": FSIConfig("2d_mid_p1disc", 2, (256, 128), pressure="p1disc"),
 }
 
 
@@ -263,11 +265,14 @@ class Problem:
     def cell_map(self):
         """(cell_dof [cells, NL] int32, cell_flags [cells] uint32): per cell (lexicographic,
         direction 0 fastest) the global DOF of each element DOF (v of Q2 node a comp i at
-        a*dim + i, u at NQ2*dim + a*dim + i, p of Q1 vertex P at 2*NQ2*dim + P) and the
+        a*dim + i, u at NQ2*dim + a*dim + i, pressure basis function P at 2*NQ2*dim + P:
+        the Q1 vertices, or with P1disc the cell's d + 1 coefficients) and the
         flags bit 0 solid, bit 1 outflow-face fluid cell, bit 2 + a node a outside the
         closed solid region.  The mesh description a device assembler consumes."""
         n_cells = int(np.prod(self.cfg.n[:self.dim]))
-        nl = 40 if self.dim == 2 else 170
+        nq2 = 9 if self.dim == 2 else 27
+        npres = self.dim + 1 if self.cfg.pressure == "p1disc" else 2 ** self.dim
+        nl = 2 * nq2 * self.dim + npres
         cd = np.empty((n_cells, nl), np.int32)
         cf = np.empty(n_cells, np.uint32)
         _load().fsigen_cell_map(self._h, _ptr(cd, ctypes.c_int32), _ptr(cf, ctypes.c_uint32))

@@ -317,15 +317,21 @@ typedef struct fsi_asm fsi_asm;
 
 typedef struct fsi_asm_mesh {
   int dim;                  /* 2 or 3 */
+  int pressure;             /* 0: continuous Q1 pressure (vertex functions); 1: the discontinuous P1
+                               pressure of the Q2-Q2-P1disc pair (Sec. 3.4), per fluid cell
+                               p = p_0 + sum_k p_k (2 xi_k - 1) in the cell's reference coordinates */
   int cells[3];             /* cells per direction of the box; cells are numbered
                                lexicographically, direction 0 fastest */
   double h[3];              /* cell size per direction */
   int64_t n;                /* unknowns */
-  const int32_t* cell_dof;  /* host, cells x NL (NL = 40 in 2D, 170 in 3D): global DOF of each local
-                               DOF.  Local order: v of Q2 node a component i at a*dim + i, u at
-                               NQ2*dim + a*dim + i, p of Q1 vertex P at 2*NQ2*dim + P; Q2 nodes
-                               a = a0 + 3 a1 (+ 9 a2) and Q1 vertices P = P0 + 2 P1 (+ 4 P2), each
-                               index running along its direction from the cell's lower corner */
+  const int32_t* cell_dof;  /* host, cells x NL (Q1: NL = 40 in 2D, 170 in 3D; P1disc: 39, 166):
+                               global DOF of each local DOF.  Local order: v of Q2 node a component i
+                               at a*dim + i, u at NQ2*dim + a*dim + i, pressure function P at
+                               2*NQ2*dim + P; Q2 nodes a = a0 + 3 a1 (+ 9 a2) and Q1 vertices
+                               P = P0 + 2 P1 (+ 4 P2), each index running along its direction from
+                               the cell's lower corner; P1disc: P = 0 the constant, P = k the k-th
+                               centred linear.  Entries of the pressure slots of solid cells are any
+                               valid DOF (solid cells carry no pressure) */
   const uint32_t* cell_flags; /* host, one per cell: bit 0 solid cell, bit 1 the cell's upper face
                                in direction 0 is the do-nothing outflow boundary, bit 2 + a local Q2
                                node a carries a mesh-motion row (lies outside the closed solid) */

@@ -55,13 +55,15 @@ __device__ __forceinline__ D1 inv(D1 b) {
   return {r, -b.d * r * r};
 }
 
-template <int D> struct Sh;
-template <> struct Sh<2> {
-  static constexpr int NQ2 = 9, NQ1 = 4, NL = 40, NQP = 9, NFP = 3;
+// Element shape: PD = 0 continuous Q1 pressure (2^D vertex functions), PD = 1 the
+// discontinuous P1 pressure of the paper's Q2-Q2-P1disc pair (D + 1 functions per cell).
+template <int D, int PD> struct Sh;
+template <int PD> struct Sh<2, PD> {
+  static constexpr int NQ2 = 9, NQ1 = PD ? 3 : 4, NL = 36 + NQ1, NQP = 9, NFP = 3;
   static constexpr int CHUNK = 40;   // columns per CTA (all)
 };
-template <> struct Sh<3> {
-  static constexpr int NQ2 = 27, NQ1 = 8, NL = 170, NQP = 27, NFP = 9;
+template <int PD> struct Sh<3, PD> {
+  static constexpr int NQ2 = 27, NQ1 = PD ? 4 : 8, NL = 162 + NQ1, NQP = 27, NFP = 9;
   static constexpr int CHUNK = 17;   // 10 chunks of columns
 };
 // shared slots per (point, column): f0 (D), f1 (D x D), then hm (D x D) and g0 (fluid) or k0 (solid)
@@ -134,7 +136,7 @@ struct Old {
 template <int D>
 __device__ __forceinline__ void old_point(const double* N, const double* dN, const double* Vo, const double* Uo,
                                           bool need_grad, Old<D>& o) {
-  constexpr int NQ2 = Sh<D>::NQ2;
+  constexpr int NQ2 = Sh<D, 0>::NQ2;
   for (int i = 0; i < D; ++i) {
     double a = 0.0, b = 0.0;
     for (int k = 0; k < NQ2; ++k) { a += N[k] * Vo[k * D + i]; b += N[k] * Uo[k * D + i]; }
@@ -161,7 +163,7 @@ __device__ __forceinline__ void old_point(const double* N, const double* dN, con
 template <int D>
 __device__ __forceinline__ void fields(const double* N, const double* dN, const double* U, int dir, D1 (&v)[D],
                                        D1 (&u)[D], D1 (&Gv)[D][D], D1 (&Gu)[D][D]) {
-  constexpr int NQ2 = Sh<D>::NQ2;
+  constexpr int NQ2 = Sh<D, 0>::NQ2;
   for (int i = 0; i < D; ++i) {
     double a = 0.0, b = 0.0;
     for (int k = 0; k < NQ2; ++k) { a += N[k] * U[k * D + i]; b += N[k] * U[NQ2 * D + k * D + i]; }
@@ -186,7 +188,7 @@ __device__ __forceinline__ void fields(const double* N, const double* dN, const 
   }
 }
 
-template <int D, bool JAC>
+template <int D, int PD, bool JAC>
 __global__ void __launch_bounds__(kAsmThreads) k_assemble(CellGeom geom, int chunk0_stride, Tables T, Phys P,
                                                           const int* __restrict__ cell_dof,
                                                           const unsigned* __restrict__ cell_flags,
@@ -197,10 +199,11 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(CellGeom geom, int chu
                                                           const double* __restrict__ Uold,
                                                           double* __restrict__ out, double* __restrict__ cell_minJ,
                                                           int* __restrict__ err) {
-  constexpr int NQ2 = Sh<D>::NQ2, NQ1 = Sh<D>::NQ1, NL = Sh<D>::NL, NQP = Sh<D>::NQP, NFP = Sh<D>::NFP;
+  using E = Sh<D, PD>;
+  constexpr int NQ2 = E::NQ2, NQ1 = E::NQ1, NL = E::NL, NQP = E::NQP, NFP = E::NFP;
   constexpr int S = kSlots<D>;
   constexpr int NPT = NQP + NFP;
-  constexpr int C = JAC ? Sh<D>::CHUNK : 1;
+  constexpr int C = JAC ? E::CHUNK : 1;
   extern __shared__ double smem[];
   double* U = smem;                        // NL
   double* Vo = U + NL;                     // NQ2 * D
@@ -498,6 +501,7 @@ double q1b(int a, double x) { return a == 0 ? 1.0 - x : x; }
 
 struct Assembler {
   int dim = 2;
+  int pdisc = 0;                  // pressure: 0 continuous Q1, 1 discontinuous P1
   int64_t n = 0, ncell = 0;
   int ncd[3] = {1, 1, 1};
   Phys phys{};
@@ -523,7 +527,7 @@ namespace {
 
 void build_tables(Assembler& A, const double* h) {
   const int D = A.dim;
-  const int NQ2 = D == 2 ? 9 : 27, NQ1 = D == 2 ? 4 : 8, NQP = NQ2, NFP = D == 2 ? 3 : 9;
+  const int NQ2 = D == 2 ? 9 : 27, NQ1 = A.pdisc ? D + 1 : (D == 2 ? 4 : 8), NQP = NQ2, NFP = D == 2 ? 3 : 9;
   // 3-point Gauss-Legendre rule on [0, 1]: nodes 1/2 -+ sqrt(3/5)/2, weights 5/18, 8/18, 5/18
   const double r = std::sqrt(0.6);
   const double gx[3] = {0.5 - 0.5 * r, 0.5, 0.5 + 0.5 * r};
@@ -546,9 +550,13 @@ void build_tables(Assembler& A, const double* h) {
     }
     if (Nprow)
       for (int a = 0; a < NQ1; ++a) {
-        const int ai[3] = {a % 2, (a / 2) % 2, a / 4};
         double val = 1.0;
-        for (int d = 0; d < D; ++d) val *= q1b(ai[d], xi[d]);
+        if (A.pdisc) {
+          val = a == 0 ? 1.0 : 2.0 * xi[a - 1] - 1.0;   // P1disc: 1 and the centred linears of the cell
+        } else {
+          const int ai[3] = {a % 2, (a / 2) % 2, a / 4};
+          for (int d = 0; d < D; ++d) val *= q1b(ai[d], xi[d]);
+        }
         Nprow[a] = val;
       }
   };
@@ -582,17 +590,19 @@ void build_tables(Assembler& A, const double* h) {
                A.tab.p + off[4], A.tab.p + off[5], A.tab.p + off[6]};
 }
 
-template <int D, bool JAC>
+template <int D, int PD, bool JAC>
 size_t smem_bytes() {
-  constexpr int C = JAC ? Sh<D>::CHUNK : 1;
-  return sizeof(double) * (Sh<D>::NL + 2 * Sh<D>::NQ2 * D + (size_t)(Sh<D>::NQP + Sh<D>::NFP) * C * kSlots<D>);
+  using E = Sh<D, PD>;
+  constexpr int C = JAC ? E::CHUNK : 1;
+  return sizeof(double) * (E::NL + 2 * E::NQ2 * D + (size_t)(E::NQP + E::NFP) * C * kSlots<D>);
 }
 
-template <int D, bool JAC>
+template <int D, int PD, bool JAC>
 void run_colours(Assembler& A, const double* U, const double* Uold, double* out) {
-  const size_t sm = smem_bytes<D, JAC>();
-  FSI_CUDA(cudaFuncSetAttribute(k_assemble<D, JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  const int chunks = JAC ? (Sh<D>::NL + Sh<D>::CHUNK - 1) / Sh<D>::CHUNK : 1;
+  using E = Sh<D, PD>;
+  const size_t sm = smem_bytes<D, PD, JAC>();
+  FSI_CUDA(cudaFuncSetAttribute(k_assemble<D, PD, JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const int chunks = JAC ? (E::NL + E::CHUNK - 1) / E::CHUNK : 1;
   for (int col = 0; col < (1 << D); ++col) {
     CellGeom g{};
     int64_t cnt = 1;
@@ -610,7 +620,7 @@ void run_colours(Assembler& A, const double* U, const double* Uold, double* out)
     if (cnt == 0) continue;
     const int64_t blocks = cnt * chunks;
     require(blocks < ((int64_t)1 << 31), "fsi_asm: too many cells for one launch");
-    k_assemble<D, JAC><<<(unsigned)blocks, kAsmThreads, sm, A.s>>>(g, chunks, A.T, A.phys, A.cell_dof.p,
+    k_assemble<D, PD, JAC><<<(unsigned)blocks, kAsmThreads, sm, A.s>>>(g, chunks, A.T, A.phys, A.cell_dof.p,
                                                                     A.cell_flags.p, A.rowptr.p, A.colind.p, A.fixed.p,
                                                                     U, Uold, out, A.cell_minJ.p, A.err.p);
     FSI_CHECK_LAUNCH();
@@ -637,7 +647,11 @@ double finish(Assembler& A, double* out, bool jac, double* minJ) {
 void asm_residual(Assembler& A, const double* U, const double* Uold, double* R, double* minJ, double* rmax) {
   FSI_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * A.n, A.s));
   FSI_CUDA(cudaMemsetAsync(A.err.p, 0, sizeof(int), A.s));
-  if (A.dim == 2) run_colours<2, false>(A, U, Uold, R); else run_colours<3, false>(A, U, Uold, R);
+  if (A.dim == 2) {
+    if (A.pdisc) run_colours<2, 1, false>(A, U, Uold, R); else run_colours<2, 0, false>(A, U, Uold, R);
+  } else {
+    if (A.pdisc) run_colours<3, 1, false>(A, U, Uold, R); else run_colours<3, 0, false>(A, U, Uold, R);
+  }
   finish(A, R, false, minJ);
   if (rmax) {
     const int nb = 256;
@@ -655,7 +669,11 @@ void asm_residual(Assembler& A, const double* U, const double* Uold, double* R, 
 void asm_jacobian(Assembler& A, const double* U, const double* Uold, double* vals, double* minJ) {
   FSI_CUDA(cudaMemsetAsync(vals, 0, sizeof(double) * A.nnz, A.s));
   FSI_CUDA(cudaMemsetAsync(A.err.p, 0, sizeof(int), A.s));
-  if (A.dim == 2) run_colours<2, true>(A, U, Uold, vals); else run_colours<3, true>(A, U, Uold, vals);
+  if (A.dim == 2) {
+    if (A.pdisc) run_colours<2, 1, true>(A, U, Uold, vals); else run_colours<2, 0, true>(A, U, Uold, vals);
+  } else {
+    if (A.pdisc) run_colours<3, 1, true>(A, U, Uold, vals); else run_colours<3, 0, true>(A, U, Uold, vals);
+  }
   finish(A, vals, true, minJ);
 }
 
@@ -670,7 +688,9 @@ void asm_create(Assembler& A, const fsi_asm_mesh& m, const fsi_asm_physics& p, v
   require(m.dim == 2 || m.dim == 3, "fsi_asm: dim must be 2 or 3");
   require(m.n > 0 && m.n < ((int64_t)1 << 31), "fsi_asm: n out of range");
   require(m.cell_dof && m.cell_flags && m.rowptr && m.colind && m.row_fixed, "fsi_asm: null mesh array");
+  require(m.pressure == 0 || m.pressure == 1, "fsi_asm: pressure must be 0 (continuous Q1) or 1 (P1disc)");
   A.dim = m.dim;
+  A.pdisc = m.pressure;
   A.n = m.n;
   A.ncell = 1;
   for (int d = 0; d < m.dim; ++d) {
@@ -686,7 +706,7 @@ void asm_create(Assembler& A, const fsi_asm_mesh& m, const fsi_asm_physics& p, v
     FSI_CUDA(cudaStreamCreateWithFlags(&A.s, cudaStreamNonBlocking));
     A.own_stream = true;
   }
-  const int NL = m.dim == 2 ? 40 : 170;
+  const int NL = 2 * (m.dim == 2 ? 9 : 27) * m.dim + (m.pressure ? m.dim + 1 : (m.dim == 2 ? 4 : 8));
   A.nnz = m.rowptr[m.n];
   for (int64_t c = 0; c < A.ncell * NL; ++c)
     require(m.cell_dof[c] >= 0 && m.cell_dof[c] < m.n, "fsi_asm: cell DOF out of range");

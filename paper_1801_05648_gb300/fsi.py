@@ -58,7 +58,8 @@ class Params(ctypes.Structure):
 
 
 class AsmMesh(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int), ("cells", ctypes.c_int * 3), ("h", ctypes.c_double * 3), ("n", ctypes.c_int64),
+    _fields_ = [("dim", ctypes.c_int), ("pressure", ctypes.c_int), ("cells", ctypes.c_int * 3),
+                ("h", ctypes.c_double * 3), ("n", ctypes.c_int64),
                 ("cell_dof", ctypes.POINTER(ctypes.c_int32)), ("cell_flags", ctypes.POINTER(ctypes.c_uint32)),
                 ("rowptr", ctypes.POINTER(ctypes.c_int64)), ("colind", ctypes.POINTER(ctypes.c_int32)),
                 ("row_fixed", ctypes.POINTER(ctypes.c_uint8))]
@@ -463,7 +464,8 @@ class FSIAssembler:
     element-DOF map, cell flags, the Jacobian's CSR pattern and fixed rows);
     physics: rho_f, nu_f, mu_s, lambda_s, rho_s, dt, theta."""
 
-    def __init__(self, dim, cells, h, n, cell_dof, cell_flags, rowptr, colind, row_fixed, physics, stream=None):
+    def __init__(self, dim, cells, h, n, cell_dof, cell_flags, rowptr, colind, row_fixed, physics, stream=None,
+                 pressure="q1"):
         import torch
         lib = load_library()
         self._lib = lib
@@ -474,8 +476,15 @@ class FSIAssembler:
                       np.ascontiguousarray(rowptr, np.int64), np.ascontiguousarray(colind, np.int32),
                       np.ascontiguousarray(row_fixed, np.uint8)]
         self.nnz = int(self._keep[2][-1])
+        if pressure not in ("q1", "p1disc"):
+            raise ValueError(f"unknown pressure space {pressure!r}")
+        nq2 = 9 if self.dim == 2 else 27
+        nl = 2 * nq2 * self.dim + (self.dim + 1 if pressure == "p1disc" else 2 ** self.dim)
+        if self._keep[0].ndim != 2 or self._keep[0].shape[1] != nl:
+            raise ValueError(f"cell_dof must be [cells, {nl}]")
         m = AsmMesh()
         m.dim = self.dim
+        m.pressure = 1 if pressure == "p1disc" else 0
         for d in range(3):
             m.cells[d] = int(cells[d]) if d < dim else 1
             m.h[d] = float(h[d]) if d < dim else 1.0
@@ -503,7 +512,8 @@ class FSIAssembler:
         h = [cfg.L[d] / cfg.n[d] for d in range(pb.dim)]
         phys = dict(rho_f=cfg.rho_f, nu_f=cfg.nu_f, mu_s=cfg.mu_s, lambda_s=cfg.lambda_s, rho_s=cfg.rho_s,
                     dt=cfg.dt, theta=cfg.theta)
-        return cls(pb.dim, cfg.n, h, pb.n, cd, cf, pb.rowptr, pb.colind, pb.fixed, phys, stream)
+        return cls(pb.dim, cfg.n, h, pb.n, cd, cf, pb.rowptr, pb.colind, pb.fixed, phys, stream,
+                   pressure=getattr(cfg, "pressure", "q1"))
 
     def _check(self, rc):
         if rc != FSI_OK:

@@ -39,7 +39,9 @@ def test_dof_counts(name, expect):
 
 
 @pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(2, (6, 4), prev_state="zero"), small(3, (4, 2, 4)),
-                                 small(2, (8, 8), theta=0.5), small(3, (4, 2, 4), theta=0.51)])
+                                 small(2, (8, 8), theta=0.5), small(3, (4, 2, 4), theta=0.51),
+                                 small(2, (8, 8), pressure="p1disc"), small(3, (4, 2, 4), pressure="p1disc"),
+                                 small(2, (6, 4), prev_state="zero", pressure="p1disc")])
 def test_jacobian_matches_central_differences(cfg):
     pb = fsigen.get_problem(cfg)
     U = pb.seeded_state(3, 3e-2)
@@ -163,7 +165,8 @@ def test_stvk_frame_invariance_under_finite_rotation():
     assert np.max(np.abs(res[m & ~pb.fixed])) <= 1e-12
 
 
-@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(3, (4, 2, 4))])
+@pytest.mark.parametrize("cfg", [small(2, (8, 8)), small(3, (4, 2, 4)), small(2, (8, 8), pressure="p1disc"),
+                                 small(3, (4, 2, 4), pressure="p1disc")])
 def test_pressure_gradient_is_minus_divergence_transpose(cfg):
     pb = fsigen.get_problem(cfg)
     U = pb.seeded_state(1, 3e-2)
@@ -252,3 +255,58 @@ def test_theta_scheme_moving_previous_step(theta):
     mid = 0.5 * (1.0 + theta)
     assert np.linalg.norm(R[theta] - 2.0 * R[mid] + R[1.0]) <= 1e-11 * np.linalg.norm(R[1.0])
     assert np.linalg.norm(R[theta] - R[1.0]) > 1e-6 * np.linalg.norm(R[1.0])
+
+
+@pytest.mark.parametrize("name,expect", [
+    # Q2-Q2-P1disc: d + 1 pressure DOFs per fluid cell (16 x 12 = 192 in 2D, 32 x 16 x 12 in 3D)
+    ("2d_tiny", [0, 1584, 2178, 2772, 4356, 4932]),
+    ("3d", [0, 154440, 212355, 270270, 424710, 449286]),
+])
+def test_p1disc_dof_counts(name, expect):
+    pb = fsigen.get_problem(fsigen.CONFIGS[name].with_(pressure="p1disc"))
+    assert pb.offsets.tolist() == expect
+    # every pressure row is a live row of one fluid cell (no identity rows)
+    o = pb.offsets
+    assert not pb.fixed[o[4]:o[5]].any()
+
+
+@pytest.mark.parametrize("dim,n", [(2, (8, 8)), (3, (4, 4, 4))])
+def test_p1disc_divergence_of_a_linear_field(dim, n):
+    """Q2-Q2-P1disc (Sec. 3.4): at the state of rest (F = I, J = 1) the
+    incompressibility rows are (div v, psi_k)_K with psi_0 = 1 and the centred
+    linears psi_k = 2 xi_k - 1.  For a linear velocity field with divergence c
+    (interpolated exactly by Q2 and integrated exactly by 3-point Gauss) row 0 of
+    every fluid cell is c |K| and the linear rows vanish."""
+    cfg = small(dim, n, pressure="p1disc")
+    pb = fsigen.get_problem(cfg)
+    z = np.zeros(pb.n)
+    A = A_of(pb, pb.jacobian(z, z))
+    o = pb.offsets
+    v = np.zeros(pb.n)
+    coef = [1.0, 0.5, -0.25][:dim]
+    sel = (pb.field == 0)
+    for i in range(dim):
+        m = sel & (pb.comp == i)
+        v[m] = coef[i] * pb.coords[m, i] + 0.3 * pb.coords[m, (i + 1) % dim]   # grad v has trace sum(coef)
+    v[pb.fixed] = 0.0          # Dirichlet velocity rows are dropped columns: use interior cells only
+    r = (A @ v)[o[4]:o[5]].reshape(-1, dim + 1)
+    h = [cfg.L[d] / cfg.n[d] for d in range(dim)]
+    vol = float(np.prod(h))
+    c = sum(coef)
+    # cells whose nodes are all free: pick by checking every node DOF of the cell is free
+    cd, cf = pb.cell_map()
+    fluid = (cf & 1) == 0
+    nq2 = 9 if dim == 2 else 27
+    vdofs = cd[:, :nq2 * dim]
+    interior = fluid & ~pb.fixed[vdofs].any(axis=1)
+    assert interior.sum() > 0
+    pdof0 = cd[interior, 2 * nq2 * dim]
+    rows = (pdof0 - o[4]) // (dim + 1)
+    np.testing.assert_allclose(r[rows, 0], c * vol, rtol=1e-12)
+    assert np.max(np.abs(r[rows, 1:])) <= 1e-12 * vol
+
+
+def test_p1disc_has_no_learned_node_map():
+    pb = fsigen.get_problem(small(2, (8, 8), pressure="p1disc"))
+    with pytest.raises(ValueError):
+        pb.node_map()

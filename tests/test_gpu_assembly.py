@@ -3,7 +3,8 @@ against the input generator's host assembly, which is pinned separately against
 central differences and closed forms (tests/test_fsigen.py): same pattern, every
 residual entry and every Jacobian value within 1e-12 of its row's largest
 magnitude, min det F equal.  Covered: the 16x16 and ragged 37x19 meshes and the
-8x4x4 hex mesh, backward Euler at the seeded state with a moving mesh (previous
+8x4x4 hex mesh, with continuous Q1 and with discontinuous P1 pressure (the
+Q2-Q2-P1disc pair of Sec. 3.4), backward Euler at the seeded state with a moving mesh (previous
 step 0: the ALE velocity (u - u_old)/dt is nonzero) and the theta scheme
 (Crank-Nicolson: every previous-level term active).  Then fsi_update_values
 (a context given the device Jacobian solves exactly like a context set up from
@@ -19,6 +20,9 @@ CASES = {
     "2d_16x16": fsigen.CONFIGS["2d_tiny"],
     "2d_37x19_ragged": fsigen.CONFIGS["2d_tiny"].with_(name="2d_37x19", n=(37, 19), state_seed=3),
     "3d_8x4x4": fsigen.CONFIGS["3d"].with_(name="3d_8x4x4", n=(8, 4, 4)),
+    # the paper's Q2-Q2-P1disc element (Sec. 3.4)
+    "2d_16x16_p1disc": fsigen.CONFIGS["2d_tiny"].with_(name="a16p", pressure="p1disc"),
+    "3d_8x4x4_p1disc": fsigen.CONFIGS["3d"].with_(name="a3p", n=(8, 4, 4), pressure="p1disc"),
 }
 VARIANTS = {
     "rest": dict(),

@@ -552,3 +552,79 @@ def test_short_tensors_are_refused(torch_cuda):
         g.apply_block("mesh", full[:n_m - 1], full[:n_m])
     with pytest.raises(ValueError):
         g.mass_solve_noalloc(full[:3], full[:3])
+
+
+@pytest.mark.parametrize("cfg", [fsigen.CONFIGS["2d_tiny"].with_(name="pd16", pressure="p1disc"),
+                                 fsigen.CONFIGS["2d_tiny"].with_(name="pd37", n=(37, 19), state_seed=3, rhs_seed=5,
+                                                                 pressure="p1disc"),
+                                 fsigen.CONFIGS["3d"].with_(name="pd3", n=(8, 4, 4), pressure="p1disc")],
+                         ids=["2d_16x16", "2d_37x19_ragged", "3d_8x4x4"])
+def test_p1disc_parity(cfg, torch_cuda):
+    """Q2-Q2-P1disc Jacobians (Sec. 3.4): the same solver, unchanged, on the paper's
+    pressure element.  P^-1 in FP64 against the oracle to 1e-11, the FP64 solve within
+    1e-8 and one iteration of the oracle's, the FP32-AMG form to the residual."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    s = fsigen.make_system(cfg)
+    mr = 8.0 if s.dim == 2 else 20.0
+    o = oracle.OracleSolver.from_system(s, params=oracle.PrecondParams(mass_ratio=mr))
+    ref = o.solve(s.rhs)
+    b = torch.tensor(s.rhs, device="cuda")
+    for prec in ("fp64", "fp32"):
+        g = P.FSISolver.from_system(s, params=P.default_params(s.dim, mass_ratio=mr, flags=P.FSI_USE_GRAPHS))
+        g.precond_build(prec)
+        if prec == "fp64":
+            r = np.random.default_rng(3).standard_normal(s.n)
+            rt = torch.tensor(r, device="cuda")
+            zt = torch.zeros_like(rt)
+            g.apply_block("precond", rt, zt)
+            assert rel(zt.cpu().numpy(), o.P(r)) <= 1e-11
+        x = torch.zeros_like(b)
+        st = g.solve(b, x, 1e-8)
+        g.close()
+        xc = x.cpu().numpy()
+        assert st.status == 0
+        assert np.linalg.norm(s.rhs - s.scipy() @ xc) / np.linalg.norm(s.rhs) <= 1e-8 * 1.001
+        if prec == "fp64":
+            assert abs(st.iters - ref.iters) <= 1 and rel(xc, ref.x) <= 1e-8, (st.iters, ref.iters)
+
+
+def _read_oracle_samples(workload):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"oracle_{workload}_samples.txt")
+    head, idx, val = {}, [], []
+    for line in open(path):
+        if line.startswith("#"):
+            parts = line[1:].split()
+            if len(parts) == 2:
+                head[parts[0]] = float(parts[1])
+            continue
+        i, v = line.split()
+        idx.append(int(i))
+        val.append(float(v))
+    return head, np.array(idx), np.array(val)
+
+
+def test_2d_large_fp64_matches_sampled_oracle(torch_cuda):
+    """The 8.9M-DOF Jacobian (1024x512): the FP64 GPU solve against the FP64 oracle's
+    own full solve of it, stored at 4000 seeded indices with the solution's 2-norm by
+    tests/golden/make_oracle_samples.py (the oracle takes minutes at this size):
+    iteration count within +-1, sampled entries and the 2-norm within 1e-8."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    head, idx, ref = _read_oracle_samples("2d_large")
+    s = fsigen.make_system("2d_large")
+    assert s.n == int(head["n"])
+    g = P.FSISolver.from_system(s, params=P.default_params(2, mass_ratio=8.0, flags=P.FSI_USE_GRAPHS))
+    g.precond_build("fp64")
+    b = torch.tensor(s.rhs, device="cuda")
+    x = torch.zeros_like(b)
+    st = g.solve(b, x, 1e-8)
+    g.close()
+    xc = x.cpu().numpy()
+    e = rel(xc[idx], ref)
+    print(f"[parity] 2d_large: GPU FP64 {st.iters} it, oracle {int(head['iters'])} it, sampled rel. difference "
+          f"{e:.3e}, norm {abs(np.linalg.norm(xc) - head['norm2']) / head['norm2']:.3e}")
+    assert st.status == 0 and abs(st.iters - int(head["iters"])) <= 1
+    assert e <= 1e-8
+    assert abs(np.linalg.norm(xc) - head["norm2"]) <= 1e-8 * head["norm2"]

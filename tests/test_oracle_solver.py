@@ -341,3 +341,23 @@ def test_restarted_fgmres_cycles_are_krylov_minimisers(m):
     ends = [np.linalg.norm(b - A @ fgmres(lambda v: A @ v, pre, b, tol=1e-30, restart=m, maxit=k * m).x)
             for k in range(1, 5)]
     assert np.all(np.diff(ends) <= 1e-12 * ends[0])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_p1disc_systems_solve_like_dense_lu(dim):
+    """Q2-Q2-P1disc Jacobians (the paper's pressure element, Sec. 3.4): no pressure
+    rows couple to each other (C_pp = 0, so S_p = -B_pv diag(A_ff)^-1 B_vp), and
+    FGMRES with Alg. 2 reaches the tolerance and the dense solution like the Q1 form."""
+    cfg = (fsigen.CONFIGS["2d_tiny"].with_(name="pd2", n=(8, 8), pressure="p1disc") if dim == 2 else
+           fsigen.CONFIGS["3d"].with_(name="pd3", n=(4, 2, 4), pressure="p1disc"))
+    s = fsigen.make_system(cfg)
+    B = oracle.Blocks(s.scipy(), s.offsets, dim)
+    assert B.C_pp.nnz == 0
+    S_p = oracle.pressure_schur(B).toarray()
+    ref = -(B.B_pv @ np.diag(1.0 / B.A_ff.diagonal()) @ B.B_vp)
+    assert np.allclose(S_p, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+    xd = sla.solve(s.scipy().toarray(), s.rhs)
+    o = oracle.OracleSolver.from_system(s, params(dim))
+    r = o.solve(s.rhs, tol=1e-8)
+    assert r.converged and r.true_relres <= 1e-8
+    assert np.linalg.norm(r.x - xd) / np.linalg.norm(xd) <= np.linalg.cond(s.scipy().toarray(), 1) * 1e-8
