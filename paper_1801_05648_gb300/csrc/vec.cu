@@ -172,7 +172,7 @@ __device__ __forceinline__ void chunk_of(int64_t n, int64_t& lo, int64_t& hi) {
   hi = lo + chunk < n ? lo + chunk : n;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_mdot_partial_v2(int64_t n, const double* __restrict__ V,
+__global__ void __launch_bounds__(kRedThreads, 4) k_mdot_partial_v2(int64_t n, const double* __restrict__ V,
                                                                  int64_t ldv, const int* __restrict__ jcount,
                                                                  int joff, const double* __restrict__ w,
                                                                  double* __restrict__ partials) {
