@@ -243,6 +243,14 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def measured_bf16_tflops():
+    """Dense bf16 GEMM TFLOP/s (burst) of MEASURED_PEAKS.json, None if absent."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        return None
+
+
 def source_hash(source_files) -> str:
     h = hashlib.sha256()
     for f in source_files:
@@ -475,31 +483,48 @@ def bench_ours(args):
             g.set_flags(flags)
         reps = 30
         cs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(S)]
-        for k in range(S):
-            W.solvers[k].learned_apply(W.rhs[k], cs[k], sync=False)
-        bs.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(bs)
-        for k in range(reps):
-            W.solvers[k % S].learned_apply(W.rhs[k % S], cs[k % S], sync=False)
-        e1.record(bs)
-        bs.synchronize()
-        mlp_s = e0.elapsed_time(e1) / reps / 1e3
+
+        def time_mlp(unit_flags):
+            for g in W.solvers:
+                g.set_flags(flags | unit_flags)
+            for k in range(S):
+                W.solvers[k].learned_apply(W.rhs[k], cs[k], sync=False)
+            bs.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(bs)
+            for k in range(reps):
+                W.solvers[k % S].learned_apply(W.rhs[k % S], cs[k % S], sync=False)
+            e1.record(bs)
+            bs.synchronize()
+            for g in W.solvers:
+                g.set_flags(flags)
+            return e0.elapsed_time(e1) / reps / 1e3
+
+        mlp_s = time_mlp(0)                          # tcgen05 (the default)
+        mlp_cc_s = time_mlp(P.FSI_MLP_CUDA_CORES)    # FP32 FMAs on the CUDA cores
         mlp_flops = nd.shape[0] * 2.0 * (53 * 64 + 64 * 64 + 64 * 5)
         fp32_peak = 2.0 * fma32 / 1e12
-        mlp_traffic = kernel_traffic(f"mlp_apply_{args.workload}.md", ["paper_1801_05648_gb300/csrc/learned.cu",
+        # TF32 dense peak: the measured bf16 GEMM rate x the nominal TF32 / bf16 ratio (1.1 / 2.25)
+        bf16_peak = measured_bf16_tflops()
+        tf32_peak = bf16_peak * (1.1 / 2.25) if bf16_peak else 2250.0 * (1.1 / 2.25)
+        mlp_traffic = kernel_traffic(f"mlp_apply_{args.workload}.md", ["paper_1801_05648_gb300/csrc/mlp_tc.cu",
                                                                      "paper_1801_05648_gb300/csrc/learned.cuh"])
         learned = form_summary(ms_l, st_l, {
             "form": "FP32-AMG + learned stage" if args.precision == "fp32" else "FP64 + learned stage",
             "accepted_total": sum(x.learned_accepted for x in st_l),
             "accept_ratio": float(P.default_params(2).learned_accept), "err_vs_exact_max": W.err_vs_exact(),
             "weights": os.path.relpath(LEARNED_WEIGHTS, ROOT),
-            "roofline_mlp": {"kernel": "k_mlp<MODE_APPLY>: patch gather + 53-64-64-5 MLP (bfloat16 weights, "
-                                       "FP32 FMA) + scatter", "bound": "alu",
-                             "achieved": mlp_flops / mlp_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                             "peak_kind": "measured FP32 FMA rate x 2 (fsi_probe_fma_rate)",
-                             "frac": mlp_flops / mlp_s / 1e12 / fp32_peak, "launch_us": mlp_s * 1e6,
-                             "flops_per_launch": mlp_flops, "traffic": mlp_traffic}})
+            "roofline_mlp": {"kernel": "k_mlp_tc: patch gather + 53-64-64-5 MLP on tcgen05 (kind::tf32, "
+                                       "activations as two TF32 terms, bfloat16 weights) + scatter", "bound": "tensor",
+                             "achieved": mlp_flops / mlp_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                             "peak_kind": "measured bf16 GEMM x 1.1/2.25 (nominal TF32 / bf16)" if bf16_peak
+                                          else "nominal bf16 x 1.1/2.25",
+                             "frac": mlp_flops / mlp_s / 1e12 / tf32_peak, "launch_us": mlp_s * 1e6,
+                             "flops_per_launch": mlp_flops, "traffic": mlp_traffic,
+                             "cuda_cores": {"kernel": "k_mlp<MODE_APPLY> (FP32 FMA)", "launch_us": mlp_cc_s * 1e6,
+                                            "achieved": mlp_flops / mlp_cc_s / 1e12, "peak": fp32_peak,
+                                            "peak_kind": "measured FP32 FMA rate x 2 (fsi_probe_fma_rate)",
+                                            "frac": mlp_flops / mlp_cc_s / 1e12 / fp32_peak}}})
 
     # ---- roofline of the dominant kernel: the fused FP32 Chebyshev SpMV step of the
     # V-cycles on level 0 of the mesh and fluid-velocity hierarchies of each resident

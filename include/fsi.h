@@ -69,19 +69,26 @@ enum {
                               launch over half the GPU with a software grid barrier (bounded
                               waits: a barrier that times out makes fsi_solve return FSI_ECUDA).
                               Not together with FSI_CLUSTER_COARSE */
-  FSI_FLUID_GMRES = 128    /* Sec. 4.4: every A_ff^-1 of the fluid Schur solve (and fsi_apply_block 2)
+  FSI_FLUID_GMRES = 128,   /* Sec. 4.4: every A_ff^-1 of the fluid Schur solve (and fsi_apply_block 2)
                               is fluid_gmres_iters steps of GMRES on A_ff from a zero start,
                               right-preconditioned by the A_ff V-cycle(s), Arnoldi in FP64 (classical
                               Gram-Schmidt twice), least squares by Givens rotations on the device; a
                               fixed step count, no stopping test.  The preconditioner then depends
                               nonlinearly on its input, which FGMRES allows */
+  FSI_MLP_CUDA_CORES = 256 /* evaluate the learned stage's MLP with FP32 FMAs on the CUDA cores instead
+                              of tcgen05 MMAs on the tensor cores (TF32 operands, the activations split
+                              into two TF32 terms, FP32 accumulation).  Both agree with FP32 arithmetic
+                              to about 1e-6 relative.  A tensor-core wait that gives up (about one
+                              second; not seen in correct operation) sets a flag that the next
+                              fsi_solve of the context reports as FSI_ECUDA */
 };
 
 typedef struct fsi_params {
   int restart;              /* FGMRES restart length m (default 100) */
   int maxit;                /* maximum FGMRES iterations (default 1000) */
   int flags;                /* FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE |
-                               FSI_LEARNED | FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES */
+                               FSI_LEARNED | FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES |
+                               FSI_MLP_CUDA_CORES */
   double dt_theta;          /* c = dt*theta of the solid Schur complement S_hat = A_vv + c A_vu (0.01) */
   /* smoothed-aggregation AMG */
   double strength_theta;    /* strength threshold on node-block Frobenius norms (0.08) */
@@ -415,7 +422,8 @@ int fsi_learned_apply(fsi_ctx* ctx, const double* r_dev, double* c_dev);
 int fsi_learned_features(fsi_ctx* ctx, const double* r_dev, float* feat_dev, float* rho_dev);
 /* Change fsi_params.learned_accept (in (0, 1]) of a context. */
 int fsi_set_learned_accept(fsi_ctx* ctx, double tau);
-/* Change the run-time flags of a context (FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_LEARNED);
+/* Change the run-time flags of a context (FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_LEARNED, FSI_FLUID_GMRES,
+ * FSI_MLP_CUDA_CORES);
  * FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_GRID_COARSE and FSI_NO_PDL are fixed at fsi_setup
  * (FSI_EINVAL if they differ). */
 int fsi_set_flags(fsi_ctx* ctx, int flags);

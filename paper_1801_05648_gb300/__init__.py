@@ -8,11 +8,11 @@ training / evaluation driver of the learned correction stage.
 from .fsi import (FSISolver, FSIAssembler, FSIError, Params, SolveStats, Trainer, TrainParams, default_params,
                   default_train_params, load_library, BLOCKS, EXPORTED, FSI_FP64, FSI_FP32_AMG, FSI_X0_GIVEN,
                   FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_LEARNED, FSI_NO_PDL, FSI_GRID_COARSE,
-                  FSI_FLUID_GMRES, FSI_PRECOND_LDU, FSI_PRECOND_LOWER, FSI_PRECOND_UPPER, FSI_PRECOND_DIAG,
-                  FSI_MLP_PARAMS, LIB_PATH, probe_fma_rate)
+                  FSI_FLUID_GMRES, FSI_MLP_CUDA_CORES, FSI_PRECOND_LDU, FSI_PRECOND_LOWER, FSI_PRECOND_UPPER,
+                  FSI_PRECOND_DIAG, FSI_MLP_PARAMS, LIB_PATH, probe_fma_rate)
 
 __all__ = ["FSISolver", "FSIAssembler", "FSIError", "Params", "SolveStats", "Trainer", "TrainParams", "default_params",
            "default_train_params", "load_library", "BLOCKS", "EXPORTED", "FSI_FP64", "FSI_FP32_AMG", "FSI_X0_GIVEN",
            "FSI_USE_GRAPHS", "FSI_NO_RIGID_MODES", "FSI_CLUSTER_COARSE", "FSI_LEARNED", "FSI_NO_PDL",
-           "FSI_GRID_COARSE", "FSI_FLUID_GMRES", "FSI_PRECOND_LDU", "FSI_PRECOND_LOWER", "FSI_PRECOND_UPPER",
-           "FSI_PRECOND_DIAG", "FSI_MLP_PARAMS", "LIB_PATH", "probe_fma_rate"]
+           "FSI_GRID_COARSE", "FSI_FLUID_GMRES", "FSI_MLP_CUDA_CORES", "FSI_PRECOND_LDU", "FSI_PRECOND_LOWER",
+           "FSI_PRECOND_UPPER", "FSI_PRECOND_DIAG", "FSI_MLP_PARAMS", "LIB_PATH", "probe_fma_rate"]

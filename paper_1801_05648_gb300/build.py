@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build", "fsi")
 LIB = os.path.join(HERE, "libfsi.so")
 SOURCES = ["spmv.cu", "vec.cu", "sparse_util.cu", "amg.cu", "solver.cu", "fsi_api.cu", "noalloc.cu", "coarse.cu", "learned.cu",
-           "assembly.cu"]
+           "assembly.cu", "mlp_tc.cu"]
 # throughput probes for the rooflines (include/fsi_peaks.h), a library of their own
 PEAKS_LIB = os.path.join(HERE, "libfsi_peaks.so")
 PEAKS_SOURCES = ["peaks.cu"]

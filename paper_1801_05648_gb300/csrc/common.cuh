@@ -60,6 +60,11 @@ inline bool& pdl_enabled() {
   thread_local bool on = true;
   return on;
 }
+// Learned-stage MLP on the tensor cores (else on the CUDA cores).
+inline bool& mlp_tensor_cores() {
+  thread_local bool on = true;
+  return on;
+}
 
 // Streaming multiprocessors of the current device (looked up once per device).
 inline int device_sms() {

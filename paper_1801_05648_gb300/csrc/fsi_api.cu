@@ -21,17 +21,19 @@ namespace {
 thread_local std::string g_setup_error;
 
 // The context's launch knobs (SpMV unroll depth and L2 prefetch, programmatic
-// dependent launch, the coarse V-cycle threshold) applied to this thread for one
+// dependent launch, the coarse V-cycle threshold, the MLP's unit) applied to this thread for one
 // call, the thread's previous values restored afterwards.
 struct KnobScope {
   fsi::SpmvTuning tuning;
-  bool pdl;
+  bool pdl, mlp_tc;
   double coarse_bytes;
   explicit KnobScope(const fsi::SolverParams& p)
-      : tuning(fsi::spmv_tuning()), pdl(fsi::pdl_enabled()), coarse_bytes(fsi::coarse_max_bytes()) {
+      : tuning(fsi::spmv_tuning()), pdl(fsi::pdl_enabled()), mlp_tc(fsi::mlp_tensor_cores()),
+        coarse_bytes(fsi::coarse_max_bytes()) {
     fsi::spmv_tuning().unroll = p.spmv_unroll;
     fsi::spmv_tuning().prefetch = p.spmv_prefetch;
     fsi::pdl_enabled() = (p.flags & FSI_NO_PDL) == 0;
+    fsi::mlp_tensor_cores() = (p.flags & FSI_MLP_CUDA_CORES) == 0;
     fsi::coarse_max_bytes() = p.cluster_max_bytes;
   }
   ~KnobScope() {
@@ -39,6 +41,7 @@ struct KnobScope {
     fsi::spmv_tuning() = tuning;
     fsi::spmv_tuning().setup_depth = depth;
     fsi::pdl_enabled() = pdl;
+    fsi::mlp_tensor_cores() = mlp_tc;
     fsi::coarse_max_bytes() = coarse_bytes;
   }
   KnobScope(const KnobScope&) = delete;
@@ -117,7 +120,8 @@ void validate_params(const fsi::SolverParams& s) {
   require(!((s.flags & FSI_CLUSTER_COARSE) && (s.flags & FSI_GRID_COARSE)),
           "FSI_CLUSTER_COARSE and FSI_GRID_COARSE exclude each other");
   require((s.flags & ~(FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED |
-                       FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES)) == 0, "unknown flag bits");
+                       FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES | FSI_MLP_CUDA_CORES)) == 0,
+                 "unknown flag bits");
   require(s.fluid_gmres_iters >= 1 && s.fluid_gmres_iters <= fsi::kFluidGmresMax, "fluid_gmres_iters must be in [1, 32]");
   require(s.precond_variant >= FSI_PRECOND_LDU && s.precond_variant <= FSI_PRECOND_DIAG,
           "precond_variant must be FSI_PRECOND_LDU, _LOWER, _UPPER or _DIAG");
@@ -438,7 +442,7 @@ int fsi_set_flags(fsi_ctx* ctx, int flags) {
   return guarded(ctx, [&] {
     constexpr int fixed = FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_NO_PDL | FSI_GRID_COARSE;
     constexpr int known = FSI_X0_GIVEN | FSI_USE_GRAPHS | FSI_NO_RIGID_MODES | FSI_CLUSTER_COARSE | FSI_LEARNED |
-                          FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES;
+                          FSI_NO_PDL | FSI_GRID_COARSE | FSI_FLUID_GMRES | FSI_MLP_CUDA_CORES;
     fsi::require((flags & ~known) == 0, "unknown flag bits");
     fsi::require((flags & fixed) == (ctx->C.prm.flags & fixed),
                  "FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_GRID_COARSE and FSI_NO_PDL are fixed at fsi_setup");

@@ -556,8 +556,8 @@ void learned_set_geometry(Learned& L, int64_t n, int64_t n_nodes, const int32_t*
   L.c.alloc((size_t)n);
   L.t.alloc((size_t)n);
   L.part.alloc(2 * kRedBlocks);
-  L.counters.alloc(2);
-  FSI_CUDA(cudaMemsetAsync(L.counters.p, 0, 2 * sizeof(int), s));
+  L.counters.alloc(3);
+  FSI_CUDA(cudaMemsetAsync(L.counters.p, 0, 3 * sizeof(int), s));
   FSI_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -620,11 +620,16 @@ MlpGeom learned_geom(const Learned& L, const int64_t off[6]) {
     g.inv_in[k] = 1.0f / L.sig_in[k];
     g.sig_out[k] = L.sig_out[k];
   }
+  g.err = L.counters.p ? L.counters.p + 2 : nullptr;
   return g;
 }
 
 
 void mlp_apply(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, cudaStream_t s) {
+  if (mlp_tensor_cores() && g.err) {
+    mlp_apply_tc(g, w16, rp, c, g.err, s);
+    return;
+  }
   launch_mlp<MODE_APPLY>(g, w16, rp, c, nullptr, nullptr, nullptr, nullptr, 0, s);
 }
 

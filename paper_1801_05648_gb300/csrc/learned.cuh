@@ -38,6 +38,7 @@ struct MlpGeom {
   float sig_in[5] = {1, 1, 1, 1, 1};
   float inv_in[5] = {1, 1, 1, 1, 1};   // 1 / sig_in
   float sig_out[5] = {1, 1, 1, 1, 1};
+  int* err = nullptr;                  // set to 1 by the tensor-core MLP when a wait gives up
 };
 
 // The stage as one context holds it.
@@ -50,7 +51,8 @@ struct Learned {
   bool has_weights = false;
   DBuf<double> rp, c, t;       // r', correction, A c (length n)
   DBuf<double> part;           // 2 x kRedBlocks reduction partials
-  DBuf<int> counters;          // [0] accept flag of the current iteration, [1] corrections accepted
+  DBuf<int> counters;          // [0] accept flag of the current iteration, [1] corrections accepted,
+                               // [2] tensor-core MLP error flag (sticky until a solve reports it)
 };
 
 // Validate and upload the node map (host arrays) of a system with n DOFs.
@@ -65,8 +67,12 @@ void learned_load_file(Learned& L, const char* path, cudaStream_t s);
 void learned_save_file(const char* path, const float* sig_in, const float* sig_out, const uint16_t* params);
 MlpGeom learned_geom(const Learned& L, const int64_t off[6]);
 
-// c = MLP(r'), every DOF of c written.
+// c = MLP(r'), every DOF of c written: on the tensor cores (mlp_tc.cu) when the
+// thread's mlp_tensor_cores() knob is set and g.err is given, else on the CUDA cores.
 void mlp_apply(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, cudaStream_t s);
+// The tensor-core form: tcgen05.mma (kind::tf32) with the activations split into
+// two TF32 terms, FP32 accumulation; *err = 1 if a wait for the MMAs gave up.
+void mlp_apply_tc(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, int* err, cudaStream_t s);
 // Feature rows (node-major [n_nodes][53]) and rho of r'.
 void mlp_features(const MlpGeom& g, const double* rp, float* F, float* rho, cudaStream_t s);
 

@@ -856,8 +856,17 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
     ++C.last_cycles;
   }
   FSI_CUDA(cudaStreamSynchronize(C.s));
-  if (C.prm.flags & LEARNED)
-    FSI_CUDA(cudaMemcpy(&C.last_accepted, C.learned.counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (C.learned.counters.p) {
+    int cnt[3] = {0, 0, 0};
+    FSI_CUDA(cudaMemcpy(cnt, C.learned.counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
+    if (C.prm.flags & LEARNED) C.last_accepted = cnt[1];
+    if (cnt[2] != 0) {
+      FSI_CUDA(cudaMemset(C.learned.counters.p + 2, 0, sizeof(int)));
+      C.last_status = ECUDA_;
+      C.solve_s = secs(t0, clk::now());
+      throw Error(ECUDA_, "a wait of the tensor-core MLP timed out; its corrections are not valid");
+    }
+  }
   if (C.prm.flags & GRID_COARSE) {
     bool failed = false;
     for (auto& H : C.H) failed = coarse_failed(H, C.s) || failed;

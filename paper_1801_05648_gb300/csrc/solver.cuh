@@ -29,7 +29,7 @@ struct SolverParams {
 };
 
 enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8, LEARNED = 16, NO_PDL = 32,
-             GRID_COARSE = 64, FLUID_GMRES = 128 };
+             GRID_COARSE = 64, FLUID_GMRES = 128, MLP_CUDA_CORES = 256 };
 
 constexpr int kFluidGmresMax = 32;
 

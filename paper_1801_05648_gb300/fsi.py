@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libfsi.so")
 FSI_OK, FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA, FSI_ENOTCONV, FSI_EBREAKDOWN, FSI_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 FSI_FP64, FSI_FP32_AMG = 0, 1
 FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_LEARNED, FSI_NO_PDL = 1, 2, 4, 8, 16, 32
-FSI_GRID_COARSE, FSI_FLUID_GMRES = 64, 128
+FSI_GRID_COARSE, FSI_FLUID_GMRES, FSI_MLP_CUDA_CORES = 64, 128, 256
 FSI_PRECOND_LDU, FSI_PRECOND_LOWER, FSI_PRECOND_UPPER, FSI_PRECOND_DIAG = 0, 1, 2, 3
 FSI_MLP_PARAMS, FSI_MLP_INPUTS = 7941, 53
 STATUS_NAMES = {0: "FSI_OK", -1: "FSI_EINVAL", -2: "FSI_ENOMEM", -3: "FSI_ECUDA", -4: "FSI_ENOTCONV",

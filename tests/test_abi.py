@@ -62,7 +62,7 @@ def test_default_params(lib):
     assert p2.mass_ratio == 8.0 and p3.mass_ratio == 20.0
     assert p2.strength_theta == 0.08 and p2.dt_theta == 0.01
     assert (p2.cheb_degree_coarse, p2.spmv_prefetch, p2.cluster_max_bytes) == (2, 1, 6.0e6)
-    assert p2.fluid_gmres_iters == 4 and P.FSI_FLUID_GMRES == 128
+    assert p2.fluid_gmres_iters == 4 and P.FSI_FLUID_GMRES == 128 and P.FSI_MLP_CUDA_CORES == 256
     assert p2.precond_variant == P.FSI_PRECOND_LDU == 0
 
 
@@ -121,7 +121,7 @@ def test_rejects_bad_params(lib):
     for k in (0, 33):
         rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, fluid_gmres_iters=k))
         assert rc == -1 and "fluid_gmres_iters" in msg
-    rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, flags=256))
+    rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, flags=512))
     assert rc == -1 and "flag" in msg
     for v in (-1, 4):
         rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, precond_variant=v))

@@ -130,28 +130,71 @@ def test_features_match_oracle(name, torch_cuda):
     assert np.abs(F.cpu().numpy() - Fo).max() <= 2e-6 * np.sqrt(45)
 
 
+def check_correction(s, nd, pt, g, torch, rp, si, so, bits):
+    c = torch.full((s.n,), np.nan, dtype=torch.float64, device="cuda")
+    g.learned_apply(torch.tensor(rp, device="cuda"), c)
+    cg = c.cpu().numpy()
+    co = L.correction(rp, nd, pt, s.offsets, bits, si.astype(np.float64), so.astype(np.float64))
+    assert np.all(np.isfinite(cg)), "every DOF of c must be written"
+    assert np.all(cg[s.fixed] == 0.0)
+    cls = L.dof_class(np.arange(s.n), s.offsets)
+    for k in range(5):
+        sel = cls == k
+        if sel.any() and np.abs(co[sel]).max() > 0:
+            assert np.abs(cg[sel] - co[sel]).max() <= 5e-5 * np.abs(co[sel]).max(), k
+    return cg
+
+
+# the MLP on the tensor cores (tcgen05, the default) and on the CUDA cores
+UNITS = {"tensor_cores": 0, "cuda_cores": 256}
+
+
+@pytest.mark.parametrize("unit", list(UNITS))
 @pytest.mark.parametrize("name", list(CASES))
-def test_correction_matches_oracle(name, torch_cuda):
+def test_correction_matches_oracle(name, unit, torch_cuda):
+    """Several 128-node tiles and a ragged last one (1,089 and 2,925 nodes)."""
     torch = torch_cuda
     s, pb, nd, pt, g = case(name, torch)
     rng = np.random.default_rng(22)
     rp = rng.standard_normal(s.n)
     si = np.array([1.0, 2.0, 0.5, 4.0, 0.25], np.float32)
     so = np.array([3.0, 0.5, 0.25, 2.0, 1.5], np.float32)
-    for seed in (2, 3):
-        bits = random_bits(seed)
-        g.learned_set_weights(si, so, bits)
-        c = torch.full((s.n,), np.nan, dtype=torch.float64, device="cuda")
-        g.learned_apply(torch.tensor(rp, device="cuda"), c)
-        cg = c.cpu().numpy()
-        co = L.correction(rp, nd, pt, s.offsets, bits, si.astype(np.float64), so.astype(np.float64))
-        assert np.all(np.isfinite(cg)), "every DOF of c must be written"
-        assert np.all(cg[s.fixed] == 0.0)
-        cls = L.dof_class(np.arange(s.n), s.offsets)
-        for k in range(5):
-            sel = cls == k
-            if sel.any() and np.abs(co[sel]).max() > 0:
-                assert np.abs(cg[sel] - co[sel]).max() <= 5e-5 * np.abs(co[sel]).max(), (seed, k)
+    g.set_flags(UNITS[unit])
+    try:
+        for seed in (2, 3):
+            bits = random_bits(seed)
+            g.learned_set_weights(si, so, bits)
+            check_correction(s, nd, pt, g, torch, rp, si, so, bits)
+    finally:
+        g.set_flags(0)
+
+
+def test_correction_2d_256x128_both_units(torch_cuda):
+    """131,841 nodes: 1,031 tiles, several per CTA of the tensor-core kernel (its
+    barrier phases alternate across tiles); both units against the oracle and
+    against each other, with the committed trained weights."""
+    torch = torch_cuda
+    import os
+    import paper_1801_05648_gb300 as P
+    cfg = fsigen.CONFIGS["2d_mid"]
+    s = fsigen.make_system(cfg)
+    nd, pt = fsigen.get_problem(cfg).node_map()
+    g = P.FSISolver.from_system(s, params=P.default_params(2))
+    try:
+        g.learned_setup(nd, pt)
+        path = os.path.join(os.path.dirname(P.__file__), "weights", "mlp_fsi2d_256x128.bin")
+        bits, si, so = L.read_weights(path)
+        g.learned_set_weights(np.asarray(si, np.float32), np.asarray(so, np.float32), bits)
+        rp = np.random.default_rng(24).standard_normal(s.n) * np.exp(np.random.default_rng(25).uniform(-2, 2, s.n))
+        out = {}
+        for unit, fl in UNITS.items():
+            g.set_flags(fl)
+            out[unit] = check_correction(s, nd, pt, g, torch, rp, np.asarray(si, np.float32),
+                                         np.asarray(so, np.float32), bits)
+        a, b = out["tensor_cores"], out["cuda_cores"]
+        assert np.abs(a - b).max() <= 5e-5 * np.abs(b).max()
+    finally:
+        g.close()
 
 
 def test_scaled_identity_network_closed_form(torch_cuda):
