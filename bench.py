@@ -70,6 +70,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--spmv-prefetch", type=int, default=None, choices=[0, 1, 2],
                     help="SpMV L2 prefetch mode (fsi_params.spmv_prefetch; default: the library's)")
+    ap.add_argument("--spmv-unroll", type=int, default=None, choices=[4, 8],
+                    help="SpMV blocks in flight per lane (fsi_params.spmv_unroll; default: the library's)")
+    ap.add_argument("--spmv-lane-shift", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="FP32 SpMV lanes per block row / 2^shift (fsi_params.spmv_lane_shift; default: the library's)")
     ap.add_argument("--kernel-only", choices=["spmv", "solve", "mlp", "cheb"], default=None,
                     help="small programs for ncu captures: 'spmv' runs the outer SpMV 6 times, 'cheb' 6 level-0 "
                          "Chebyshev steps of the mesh hierarchy, 'mlp' 6 learned-stage applications; 'solve' runs "
@@ -418,7 +422,8 @@ def bench_ours(args):
     dev = torch.device("cuda", local)
     bs = torch.cuda.Stream(device=dev)       # every solver runs on this stream
     flags = (0 if args.no_graphs else P.FSI_USE_GRAPHS) | (P.FSI_NO_PDL if args.no_pdl else 0)
-    knobs = {} if args.spmv_prefetch is None else {"spmv_prefetch": args.spmv_prefetch}
+    knobs = {k: v for k, v in (("spmv_prefetch", args.spmv_prefetch), ("spmv_unroll", args.spmv_unroll),
+                               ("spmv_lane_shift", args.spmv_lane_shift)) if v is not None}
     n_states = args.states or DEFAULT_STATES.get(args.workload, 1)
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
@@ -690,6 +695,8 @@ def bench_ours(args):
                    "form": "FP32-AMG" if args.precision == "fp32" else "FP64", "rtol": 1e-8, "restart": 100,
                    "states": S, "graphs": not args.no_graphs, "pdl": not args.no_pdl,
                    "spmv_prefetch": int(P.default_params(W.dim, **knobs).spmv_prefetch),
+                   "spmv_unroll": int(P.default_params(W.dim, **knobs).spmv_unroll),
+                   "spmv_lane_shift": int(P.default_params(W.dim, **knobs).spmv_lane_shift),
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": f"inputs larger than L2: each solve streams {bytes_per_iter / 1e9:.2f} GB of matrices and "
                          f"vectors per FGMRES iteration ({S} resident Jacobian(s); L2 is 0.13 GB)"},

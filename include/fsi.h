@@ -131,6 +131,10 @@ typedef struct fsi_params {
      D = diag(M, S, F), L (C_sm dropped) / U the strict block triangles; the same
      approximate inverses in every variant */
   int precond_variant;
+  /* FP32 SpMV launches: lanes per block row = the automatic count (see spmv_unroll)
+     divided by 2^spmv_lane_shift, at least 1 (0..4; 0).  Fewer lanes per row put
+     more rows, and more blocks per lane, into each pass of a warp */
+  int spmv_lane_shift;
 } fsi_params;
 
 enum { FSI_PRECOND_LDU = 0, FSI_PRECOND_LOWER = 1, FSI_PRECOND_UPPER = 2, FSI_PRECOND_DIAG = 3 };

@@ -187,6 +187,7 @@ struct SpmvTuning {
   int unroll = 4;      // blocks each lane loads before multiplying: 4 or 8 (8 only for small blocks)
   int prefetch = 1;    // 0 none, 1 L2 bulk prefetch of each CTA's matrix slice, 2 also persistent CTAs
   int ctas_per_sm = 5; // persistent grid size per SM (prefetch 2)
+  int lane_shift = 0;  // FP32 launches: lanes per block row divided by 2^lane_shift (at least 1)
   int setup_depth = 0; // > 0 while matrices are being built: no reads before the dependency wait
 };
 inline SpmvTuning& spmv_tuning() {

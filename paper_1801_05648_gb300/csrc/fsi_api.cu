@@ -32,6 +32,7 @@ struct KnobScope {
         coarse_bytes(fsi::coarse_max_bytes()) {
     fsi::spmv_tuning().unroll = p.spmv_unroll;
     fsi::spmv_tuning().prefetch = p.spmv_prefetch;
+    fsi::spmv_tuning().lane_shift = p.spmv_lane_shift;
     fsi::pdl_enabled() = (p.flags & FSI_NO_PDL) == 0;
     fsi::mlp_tensor_cores() = (p.flags & FSI_MLP_CUDA_CORES) == 0;
     fsi::coarse_max_bytes() = p.cluster_max_bytes;
@@ -100,6 +101,7 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.cluster_max_bytes = p.cluster_max_bytes;
   s.fluid_gmres_iters = p.fluid_gmres_iters;
   s.precond_variant = p.precond_variant;
+  s.spmv_lane_shift = p.spmv_lane_shift;
 }
 
 void validate_params(const fsi::SolverParams& s) {
@@ -125,6 +127,7 @@ void validate_params(const fsi::SolverParams& s) {
   require(s.fluid_gmres_iters >= 1 && s.fluid_gmres_iters <= fsi::kFluidGmresMax, "fluid_gmres_iters must be in [1, 32]");
   require(s.precond_variant >= FSI_PRECOND_LDU && s.precond_variant <= FSI_PRECOND_DIAG,
           "precond_variant must be FSI_PRECOND_LDU, _LOWER, _UPPER or _DIAG");
+  require(s.spmv_lane_shift >= 0 && s.spmv_lane_shift <= 4, "spmv_lane_shift must be in [0, 4]");
 }
 
 void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -191,6 +194,7 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->cheb_degree_coarse = 2;
   p->fluid_gmres_iters = 4;
   p->precond_variant = FSI_PRECOND_LDU;
+  p->spmv_lane_shift = 0;
 }
 
 int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,

@@ -8,9 +8,8 @@
 // 32-lane quarters of the tensor memory, so thread t's node is accumulator row t.
 // Each layer is a chain of tcgen05.mma.kind::tf32 (M = 128, N = 64 / 64 / 16,
 // K = 8 per instruction) from shared memory into tensor memory:
-//   layer 1  K = 48 (the 45 dense inputs, zero-padded); the one-hot lattice
-//            parity and the four node flags select rows of W1 that the epilogue
-//            adds with b1 (they are exact 0/1 inputs)
+//   layer 1  K = 56: the 53 inputs (45 patch values, the one-hot lattice parity,
+//            the four node flags), a constant 1 whose weight row is b1, two zeros
 //   layer 2  K = 64
 //   layer 3  K = 64, N = 16 (5 outputs, zero-padded columns)
 // Operand precision.  The weights are bfloat16, exact in TF32.  Each activation
@@ -34,7 +33,7 @@ namespace fsi {
 namespace {
 
 constexpr int kTcRows = 128;           // nodes per tile = MMA M = threads per CTA
-constexpr int kTcK1 = 48;              // layer-1 K (45 inputs, zero-padded to a multiple of 8)
+constexpr int kTcK1 = 56;              // layer-1 K: 53 inputs, the bias column, zero padding
 constexpr int kTcN3 = 16;              // layer-3 N (5 outputs, zero-padded)
 constexpr uint32_t kLbo = 128;         // bytes between core matrices along K
 constexpr uint32_t kSbo = 2048;        // bytes between 8-row groups (64 fp32 columns of capacity)
@@ -42,9 +41,7 @@ constexpr uint32_t kTmemCols = 128;    // D1 / D3 in columns [0, 64), D2 in [64,
 
 // dynamic shared memory map (bytes)
 constexpr uint32_t kOffAhi = 0, kOffAlo = 32768, kOffB1 = 65536, kOffB2 = 81920, kOffB3 = 98304;
-constexpr uint32_t kOffRows = 102400;                    // W1 rows 45..52 (8 x 64 floats)
-constexpr uint32_t kOffB1v = kOffRows + 8 * 64 * 4;      // b1 (64)
-constexpr uint32_t kOffB2v = kOffB1v + 64 * 4;           // b2 (64)
+constexpr uint32_t kOffB2v = 102400;                     // b2 (64)
 constexpr uint32_t kOffB3v = kOffB2v + 64 * 4;           // b3 (16, padded)
 constexpr uint32_t kOffBar = kOffB3v + 16 * 4;           // mbarrier (8 bytes)
 constexpr uint32_t kOffTmem = kOffBar + 8;               // tensor-memory base written by tcgen05.alloc
@@ -152,22 +149,19 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* _
   const int t = threadIdx.x, warp = t >> 5;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
   const uint32_t bar = sbase + kOffBar;
-  // ---- weights (independent of earlier kernels): B operands N x K, K-major, zero-padded
+  // ---- weights (independent of earlier kernels): B operands N x K, K-major, zero-padded;
+  // row 53 of the layer-1 operand is b1 (its input column is the constant 1)
   for (int i = t; i < 64 * 64; i += blockDim.x) {
     const int n = i >> 6, k = i & 63;
     float w1 = 0.f;
-    if (k < kMlpPatch) w1 = bf16f(w16[kW1 + k * kMlpHidden + n]);
+    if (k < kMlpIn) w1 = bf16f(w16[kW1 + k * kMlpHidden + n]);
+    else if (k == kMlpIn) w1 = bf16f(w16[kB1 + n]);
     *reinterpret_cast<float*>(sm + kOffB1 + core_off(n, k)) = w1;
     *reinterpret_cast<float*>(sm + kOffB2 + core_off(n, k)) = bf16f(w16[kW2 + k * kMlpHidden + n]);
     if (n < kTcN3)
       *reinterpret_cast<float*>(sm + kOffB3 + core_off(n, k)) = n < kMlpOut ? bf16f(w16[kW3 + k * kMlpOut + n]) : 0.f;
   }
-  for (int i = t; i < 8 * 64; i += blockDim.x)
-    reinterpret_cast<float*>(sm + kOffRows)[i] = bf16f(w16[kW1 + (kMlpPatch + i / 64) * kMlpHidden + (i & 63)]);
-  for (int i = t; i < 64; i += blockDim.x) {
-    reinterpret_cast<float*>(sm + kOffB1v)[i] = bf16f(w16[kB1 + i]);
-    reinterpret_cast<float*>(sm + kOffB2v)[i] = bf16f(w16[kB2 + i]);
-  }
+  for (int i = t; i < 64; i += blockDim.x) reinterpret_cast<float*>(sm + kOffB2v)[i] = bf16f(w16[kB2 + i]);
   if (t < 16) reinterpret_cast<float*>(sm + kOffB3v)[t] = t < kMlpOut ? bf16f(w16[kB3 + t]) : 0.f;
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -184,8 +178,6 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* _
   tc_fence_after();
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + kOffTmem);
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lane quarter
-  const float* rows = reinterpret_cast<const float*>(sm + kOffRows);
-  const float* b1 = reinterpret_cast<const float*>(sm + kOffB1v);
   const float* b2 = reinterpret_cast<const float*>(sm + kOffB2v);
   const float* b3 = reinterpret_cast<const float*>(sm + kOffB3v);
   dep_wait();
@@ -222,35 +214,33 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* _
     const float inv_rho = live ? 1.0f / rho : 0.f;
     const int fl = me.w;
     const int par = ((fl >> 4) & 1) | (((fl >> 5) & 1) << 1);
-    // columns 45..47 (zero) pad layer 1's K to 48; the hidden layers overwrite them
+    // columns 45..55: one-hot parity, flags (bits 0..3), the bias input 1, zeros (all
+    // exact in TF32, so their low terms are 0); the hidden layers overwrite them
 #pragma unroll
     for (int k = 0; k < kMlpPatch - 1; k += 4)
       put4(sm, t, k, x[k] * inv_rho, x[k + 1] * inv_rho, x[k + 2] * inv_rho, x[k + 3] * inv_rho);
-    put4(sm, t, kMlpPatch - 1, x[kMlpPatch - 1] * inv_rho, 0.f, 0.f, 0.f);
+    const float oh[4] = {par == 0 ? 1.f : 0.f, par == 1 ? 1.f : 0.f, par == 2 ? 1.f : 0.f, par == 3 ? 1.f : 0.f};
+    const float fb[4] = {(float)(fl & 1), (float)((fl >> 1) & 1), (float)((fl >> 2) & 1), (float)((fl >> 3) & 1)};
+    put4(sm, t, 44, x[kMlpPatch - 1] * inv_rho, oh[0], oh[1], oh[2]);
+    put4(sm, t, 48, oh[3], fb[0], fb[1], fb[2]);
+    put4(sm, t, 52, fb[3], 1.f, 0.f, 0.f);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (t == 0) issue_layer(sbase, kOffB1, tmem, 0, kTcK1 / 8, kMlpHidden, bar);
-    // ---- layer 1 epilogue: bias, one-hot and flag rows, gelu -> layer-2 operand
+    // ---- layer 1 epilogue: gelu -> layer-2 operand
     bool ok = bar_wait(bar, phase);
     if (__syncthreads_or(!ok)) { failed = true; break; }
     phase ^= 1u;
     tc_fence_after();
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < kMlpHidden / 16; ++q) {
       float h[16];
       tc_ld16(trow + 16u * q, h);
       tc_wait_ld();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int j = 16 * q + i;
-        float v = h[i] + b1[j] + rows[par * 64 + j];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if ((fl >> k) & 1) v += rows[(4 + k) * 64 + j];
-        h[i] = tc_gelu(v);
-      }
+      for (int i = 0; i < 16; ++i) h[i] = tc_gelu(h[i]);
 #pragma unroll
       for (int i = 0; i < 16; i += 4) put4(sm, t, 16 * q + i, h[i], h[i + 1], h[i + 2], h[i + 3]);
     }
@@ -264,7 +254,7 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* _
     if (__syncthreads_or(!ok)) { failed = true; break; }
     phase ^= 1u;
     tc_fence_after();
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < kMlpHidden / 16; ++q) {
       float h[16];
       tc_ld16(trow + 64u + 16u * q, h);

@@ -13,10 +13,11 @@ namespace {
 template <class T, int BR, int BC1, int BC2, class Epi, class G1, bool ALLOW16 = false>
 void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi& epi, cudaStream_t s) {
   if (A1.nbr == 0) return;
-  const int tpr = sizeof(T) == 8 ? A1.tpr64 : A1.tpr;
+  const SpmvTuning& tu = spmv_tuning();
+  int tpr = sizeof(T) == 8 ? A1.tpr64 : A1.tpr;
+  if (sizeof(T) == 4) tpr = (tpr >> tu.lane_shift) > 0 ? (tpr >> tu.lane_shift) : 1;
   const int threads = 256;
   const int per_pass = threads / tpr;
-  const SpmvTuning& tu = spmv_tuning();
   int rows_per_cta = per_pass;
   int blocks = div_up(A1.nbr, per_pass);
   if (tu.prefetch >= 2 && blocks > device_sms() * tu.ctas_per_sm) {
@@ -32,9 +33,14 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
   const int pf = tu.prefetch > 0 ? 1 : 0;
   if constexpr (ALLOW16 && sizeof(T) == 4 && BC2 == 0) {
     if (A1.cd16.p) {
-      launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4, int16_t>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf,
-               pre_wait, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2,
-               epi);
+      if (tu.unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
+        launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8, int16_t>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta,
+                 pf, pre_wait, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2,
+                 x2, epi);
+      else
+        launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4, int16_t>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta,
+                 pf, pre_wait, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2,
+                 x2, epi);
       return;
     }
   }

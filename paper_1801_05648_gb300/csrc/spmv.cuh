@@ -299,14 +299,19 @@ __device__ __forceinline__ void row_accumulate(const CI* __restrict__ ci, int ba
 }
 
 // L2 prefetch of the 16-byte-aligned interior of [p, p + bytes) (one bulk
-// prefetch per 64 KB; the unaligned edges are left to the ordinary loads).
+// prefetch per 64 KB; the unaligned edges are left to the ordinary loads).  The
+// lines come in with the evict-first policy, like the streaming loads that read
+// them, so they do not push the gathered vector out of L2.
 __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
   const uintptr_t a0 = ((uintptr_t)p + 15) & ~(uintptr_t)15;
   const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  uint64_t policy;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
   for (uintptr_t a = a0; a < e; a += 65536) {
     const uint32_t n = (uint32_t)(e - a < 65536 ? e - a : 65536);
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(a), "r"(n), "l"(policy)
+                 : "memory");
   }
 #endif
 }
