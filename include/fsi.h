@@ -153,6 +153,7 @@ typedef struct fsi_stats {
   int hist_len;
   int64_t kernel_launches;  /* CUDA kernels the solve executed (graph replays counted per kernel node) */
   int learned_accepted;     /* FSI_LEARNED: iterations whose learned correction was taken */
+  int reorth_passes;        /* Arnoldi steps that took a second Gram-Schmidt pass (see fsi_solve) */
 } fsi_stats;
 
 typedef struct fsi_ctx fsi_ctx;

@@ -281,6 +281,7 @@ int fsi_solve(fsi_ctx* ctx, const double* rhs_dev, double* x_dev, double rtol, f
     out->hist_len = (int)C.hist.size();
     out->kernel_launches = C.last_launches;
     out->learned_accepted = C.last_accepted;
+    out->reorth_passes = C.last_reorth;
   }
   if (rc != FSI_OK) return rc;
   if (status == fsi::ENOTCONV_) C.err = "FGMRES reached maxit before rtol";

@@ -76,24 +76,25 @@ __global__ void k_col_out(int64_t n, const T* __restrict__ in, double* __restric
     dst[i] = v;
   }
 }
-// V_{j+1} = w / h  (left zero when h == 0)
+// V_{j+1} = sign * w / h  (left zero when h == 0)
 __global__ void k_scale_col(int64_t n, const double* __restrict__ w, const double* __restrict__ h,
-                            double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev) {
+                            double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev, double sign) {
   dep_wait();
   const double hv = *h;
   double* dst = V + (size_t)(*jdev + 1) * ldv;
-  const double inv = hv > 0.0 ? 1.0 / hv : 0.0;
+  const double inv = hv > 0.0 ? sign / hv : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = w[i] * inv;
 }
 
-// Hessenberg column j = h1 + h2 (CGS2), h_{j+1,j} = ||w||; apply the previous
-// rotations, form the new one, update g.  Writes |g_{j+1}|/||b|| and a
+// Hessenberg column j = h1 + h2 (two Gram-Schmidt passes on w), or, with defect != 0,
+// e_j - (h1 + h2) (the passes ran on the defect v_j - w), h_{j+1,j} = ||w||; apply the
+// previous rotations, form the new one, update g.  Writes |g_{j+1}|/||b|| and a
 // breakdown flag to host-mapped memory.  One thread.
 __global__ void k_givens(int ldh, const int* __restrict__ jdev, const double* __restrict__ h1,
                          const double* __restrict__ h2, const double* __restrict__ hnorm, double* __restrict__ H,
                          double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
-                         const double* __restrict__ inv_bnorm_p, double* __restrict__ out) {
+                         const double* __restrict__ inv_bnorm_p, double* __restrict__ out, int defect) {
   dep_wait();
   const double inv_bnorm = *inv_bnorm_p;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -101,7 +102,7 @@ __global__ void k_givens(int ldh, const int* __restrict__ jdev, const double* __
   double* col = H + (size_t)j * ldh;
   double w0 = 0.0;
   for (int i = 0; i <= j; ++i) {
-    col[i] = h1[i] + h2[i];
+    col[i] = defect ? (i == j ? 1.0 : 0.0) - (h1[i] + h2[i]) : h1[i] + h2[i];
     w0 += col[i] * col[i];
   }
   const double hn = *hnorm;
@@ -709,6 +710,7 @@ void ensure_krylov(Context& C) {
   C.npart.alloc(kRedBlocks);
   C.zfix.alloc(n); C.wfix.alloc(n); C.rvec.alloc(n);
   C.jdev.alloc(1); C.kdev.alloc(1);
+  C.dpart.alloc(kRedBlocks); C.reorth.alloc(2);
   if (!C.pinned) {
     FSI_CUDA(cudaHostAlloc(&C.pinned, 8 * sizeof(double), cudaHostAllocMapped));
     FSI_CUDA(cudaHostGetDevicePointer(&C.pinned_dev, C.pinned, 0));
@@ -719,7 +721,11 @@ void ensure_krylov(Context& C) {
 }
 
 // One FGMRES iteration for the index held in C.jdev: Z_j = P^-1 V_j,
-// w = A Z_j, CGS2 against V_0..V_j, Givens update, V_{j+1} = w / ||w||.
+// w = A Z_j, Gram-Schmidt against V_0..V_j, Givens update, V_{j+1} = w / ||w||.
+// Second-pass threshold of the Arnoldi Gram-Schmidt: one pass leaves the new
+// vector orthogonal to about u ||d|| / ||d'|| (u the unit roundoff), so a pass that
+// keeps at least 1% of the norm leaves it within ~1e-14.
+constexpr double kReorthEta = 1e-2;
 template <class T>
 void iteration_body(Context& C) {
   const int64_t n = C.n;
@@ -741,14 +747,19 @@ void iteration_body(Context& C) {
     learned_decide(n, L.rp.p, L.t.p, C.prm.learned_accept, L.part.p, L.counters.p, C.s);
     learned_commit(n, L.counters.p, L.c.p, L.t.p, C.Z.p, C.ldv, C.jdev.p, C.wfix.p, C.s);
   }
+  // Arnoldi step on the defect d = v_j - w (classical Gram-Schmidt, a second pass
+  // only when the first kept less than kReorthEta of ||d||): h = e_j - V^T d,
+  // w - V h = -(d - V V^T d), so v_{j+1} = -d' / ||d'||.
+  arnoldi_defect(n, C.V.p, C.ldv, C.jdev.p, C.wfix.p, C.dpart.p, C.s);
   mdot(n, C.V.p, C.ldv, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h1.p, m + 1, C.s);
-  maxpy(n, C.V.p, C.ldv, C.jdev.p, 1, C.h1.p, 1.0, C.wfix.p, nullptr, m + 1, C.s);
-  mdot(n, C.V.p, C.ldv, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h2.p, m + 1, C.s);
-  maxpy(n, C.V.p, C.ldv, C.jdev.p, 1, C.h2.p, 1.0, C.wfix.p, C.npart.p, m + 1, C.s);
+  maxpy(n, C.V.p, C.ldv, C.jdev.p, 1, C.h1.p, 1.0, C.wfix.p, C.npart.p, m + 1, C.s);
+  reorth_flag(C.npart.p, C.dpart.p, kReorthEta, C.reorth.p, C.s);
+  mdot(n, C.V.p, C.ldv, C.jdev.p, 1, C.wfix.p, C.partials.p, C.h2.p, m + 1, C.s, C.reorth.p);
+  maxpy(n, C.V.p, C.ldv, C.jdev.p, 1, C.h2.p, 1.0, C.wfix.p, C.npart.p, m + 1, C.s, C.reorth.p);
   finish_norm(C.npart.p, C.scal.p, C.s);
   launch_k(k_givens, 1, 32, 0, C.s, m + 1, C.jdev.p, C.h1.p, C.h2.p, C.scal.p, C.Hh.p, C.cs.p, C.sn.p, C.g.p,
-           C.scal.p + 5, C.pinned_dev);
-  launch_k(k_scale_col, grid_n(n), 256, 0, C.s, n, C.wfix.p, C.scal.p, C.V.p, C.ldv, C.jdev.p);
+           C.scal.p + 5, C.pinned_dev, 1);
+  launch_k(k_scale_col, grid_n(n), 256, 0, C.s, n, C.wfix.p, C.scal.p, C.V.p, C.ldv, C.jdev.p, -1.0);
 }
 
 void run_iteration(Context& C) {
@@ -798,7 +809,9 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
   ensure_krylov(C);
   ensure_fluid_gmres(C);
   C.last_accepted = 0;
+  C.last_reorth = 0;
   if (C.prm.flags & LEARNED) FSI_CUDA(cudaMemsetAsync(C.learned.counters.p, 0, 2 * sizeof(int), C.s));
+  FSI_CUDA(cudaMemsetAsync(C.reorth.p, 0, 2 * sizeof(int), C.s));
   const int64_t n = C.n;
   const int m = C.prm.restart;
   C.hist.clear();
@@ -856,6 +869,7 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
     ++C.last_cycles;
   }
   FSI_CUDA(cudaStreamSynchronize(C.s));
+  FSI_CUDA(cudaMemcpy(&C.last_reorth, C.reorth.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
   if (C.learned.counters.p) {
     int cnt[3] = {0, 0, 0};
     FSI_CUDA(cudaMemcpy(cnt, C.learned.counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));

@@ -93,11 +93,14 @@ struct Context {
   double* harvest = nullptr;  // device, harvest_n x n: V_j - A z_j of the first iterations
   int harvest_n = 0;
   int last_accepted = 0;      // learned corrections taken in the last solve
+  int last_reorth = 0;        // Arnoldi steps of the last solve with a second Gram-Schmidt pass
   // FGMRES storage; basis columns V_i, Z_i at stride ldv (n rounded up to 32: 16-byte aligned columns)
   int m_alloc = 0;
   int64_t ldv = 0;
   DBuf<double> V, Z, Hh, cs, sn, g, y, h1, h2, scal, partials, npart, zfix, wfix, rvec;
   DBuf<int> jdev, kdev;
+  DBuf<double> dpart;         // per-block sums of squares of the Arnoldi defect
+  DBuf<int> reorth;           // [0] second-pass flag of the current step, [1] second passes in this solve
   double* pinned = nullptr;   // host-mapped: [0] |g_{j+1}|/|b|, [1] breakdown flag, [2] h_{j+1,j}
   double* pinned_dev = nullptr;
   int* pinned_j = nullptr;    // pinned host staging for the iteration index

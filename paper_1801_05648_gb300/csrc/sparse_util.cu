@@ -380,66 +380,114 @@ __global__ void k_to_dense(int nbr, int br, int bc, int ncols, const int* __rest
         D[((int64_t)row * br + i) * ncols + (int64_t)ci[k] * bc + j] = va[((int64_t)k * br + i) * bc + j];
 }
 
-// Gauss-Jordan on [M | I], one block of 1024 threads; M is destroyed.
-__global__ void __launch_bounds__(1024) k_gauss_jordan(int n, double* __restrict__ M, double* __restrict__ X,
-                                                       int* __restrict__ fail) {
-  __shared__ double bval[32];
-  __shared__ int bidx[32];
-  __shared__ int piv_s;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  // zero rows -> identity rows; X = I
-  for (int r = tid; r < n; r += nt) {
-    bool zero = true;
-    for (int c = 0; c < n; ++c) if (M[(int64_t)r * n + c] != 0.0) { zero = false; break; }
-    if (zero) M[(int64_t)r * n + r] = 1.0;
+// Gauss-Jordan elimination with partial pivoting on [M | I] (M is destroyed, X
+// becomes M^-1), one launch per pivot column over the whole GPU.  Before step p,
+// row p holds the pivot row (swapped in and scaled to a unit pivot) and f holds
+// column p; step p eliminates column p from every other row.  The CTA that
+// finishes a step last (an atomic ticket taken after a memory fence: nothing
+// waits) prepares pivot p + 1.
+constexpr int kGjThreads = 256;
+
+// Rows that are entirely zero become identity rows; X = I.
+__global__ void k_gj_init(int n, double* __restrict__ M, double* __restrict__ X) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    bool nz = false;
+    for (int c = lane; c < n; c += 32) nz |= M[r * n + c] != 0.0;
+    nz = __any_sync(0xffffffffu, nz);
+    if (!nz && lane == 0) M[r * n + r] = 1.0;
+    for (int c = lane; c < n; c += 32) X[r * n + c] = c == r ? 1.0 : 0.0;
   }
-  for (int64_t t = tid; t < (int64_t)n * n; t += nt) X[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
+// Pivot p: the largest |M[r][p]|, r >= p (ties to the lowest row), swapped into
+// row p of M and X, row p scaled by 1 / M[p][p], f = column p.  One CTA; the loads
+// bypass L1 (other CTAs wrote the data in the same launch).
+__device__ void gj_prepare(int n, int p, double* __restrict__ M, double* __restrict__ X, double* __restrict__ f,
+                           int* __restrict__ fail) {
+  __shared__ double bval[kGjThreads / 32];
+  __shared__ int bidx[kGjThreads / 32];
+  __shared__ int piv;
+  __shared__ double inv;
+  const int tid = threadIdx.x;
+  double best = -1.0;
+  int bi = p;
+  for (int r = p + tid; r < n; r += blockDim.x) {
+    const double v = fabs(__ldcg(M + (int64_t)r * n + p));
+    if (v > best) { best = v; bi = r; }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  if ((tid & 31) == 0) { bval[tid >> 5] = best; bidx[tid >> 5] = bi; }
   __syncthreads();
-  for (int p = 0; p < n; ++p) {
-    // pivot search over rows p..n-1 of column p
-    double best = -1.0; int bi = p;
-    for (int r = p + tid; r < n; r += nt) {
-      double v = fabs(M[(int64_t)r * n + p]);
-      if (v > best) { best = v; bi = r; }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, best, off);
-      int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((tid & 31) == 0) { bval[tid >> 5] = best; bidx[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double b = -1.0; int i = p;
-      for (int w = 0; w < (nt >> 5); ++w)
-        if (bval[w] > b || (bval[w] == b && bidx[w] < i)) { b = bval[w]; i = bidx[w]; }
-      piv_s = i;
-      if (!(b > 0.0)) *fail = 1;
-    }
-    __syncthreads();
-    const int pr = piv_s;
-    if (pr != p)
-      for (int c = tid; c < n; c += nt) {
-        double t = M[(int64_t)p * n + c]; M[(int64_t)p * n + c] = M[(int64_t)pr * n + c]; M[(int64_t)pr * n + c] = t;
-        t = X[(int64_t)p * n + c]; X[(int64_t)p * n + c] = X[(int64_t)pr * n + c]; X[(int64_t)pr * n + c] = t;
-      }
-    __syncthreads();
-    const double inv = 1.0 / M[(int64_t)p * n + p];
-    __syncthreads();
-    for (int c = tid; c < n; c += nt) { M[(int64_t)p * n + c] *= inv; X[(int64_t)p * n + c] *= inv; }
-    __syncthreads();
-    for (int64_t t = tid; t < (int64_t)n * n; t += nt) {
-      const int r = (int)(t / n), c = (int)(t % n);
-      if (r == p) continue;
-      const double f = M[(int64_t)r * n + p];
-      if (f == 0.0) continue;
-      if (c != p) M[(int64_t)r * n + c] -= f * M[(int64_t)p * n + c];
-      X[(int64_t)r * n + c] -= f * X[(int64_t)p * n + c];
-    }
-    __syncthreads();
-    for (int r = tid; r < n; r += nt) if (r != p) M[(int64_t)r * n + p] = 0.0;
-    __syncthreads();
+  if (tid == 0) {
+    double b = -1.0;
+    int i = p;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (bval[w] > b || (bval[w] == b && bidx[w] < i)) { b = bval[w]; i = bidx[w]; }
+    piv = i;
+    if (!(b > 0.0)) *fail = 1;
   }
+  __syncthreads();
+  const int pr = piv;
+  if (pr != p)
+    for (int c = tid; c < n; c += blockDim.x) {
+      double* a = M + (int64_t)p * n + c;
+      double* b = M + (int64_t)pr * n + c;
+      const double t = __ldcg(a); *a = __ldcg(b); *b = t;
+      double* xa = X + (int64_t)p * n + c;
+      double* xb = X + (int64_t)pr * n + c;
+      const double u = __ldcg(xa); *xa = __ldcg(xb); *xb = u;
+    }
+  __syncthreads();
+  if (tid == 0) inv = 1.0 / __ldcg(M + (int64_t)p * n + p);
+  __syncthreads();
+  const double s = inv;
+  for (int c = tid; c < n; c += blockDim.x) {
+    M[(int64_t)p * n + c] = __dmul_rn(__ldcg(M + (int64_t)p * n + c), s);
+    X[(int64_t)p * n + c] = __dmul_rn(__ldcg(X + (int64_t)p * n + c), s);
+  }
+  for (int r = tid; r < n; r += blockDim.x) f[r] = r == p ? 0.0 : __ldcg(M + (int64_t)r * n + p);
+}
+
+__global__ void __launch_bounds__(kGjThreads) k_gj_first(int n, double* M, double* X, double* f, int* fail) {
+  gj_prepare(n, 0, M, X, f, fail);
+}
+
+// Step p: row r != p of [M | X] -= f[r] * row p; column p of M becomes e_p.
+__global__ void __launch_bounds__(kGjThreads) k_gj_step(int n, int p, double* __restrict__ M,
+                                                        double* __restrict__ X, double* __restrict__ f,
+                                                        unsigned* __restrict__ ticket, int* __restrict__ fail) {
+  __shared__ bool last;
+  const int64_t w = 2 * (int64_t)n;
+  const int64_t total = (int64_t)n * w;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / w);
+    const int c = (int)(t - (int64_t)r * w);
+    if (r == p) continue;
+    const double fr = f[r];
+    if (c < n) {
+      double* m = M + (int64_t)r * n + c;
+      if (c == p) *m = 0.0;
+      else if (fr != 0.0) *m = __fma_rn(-fr, M[(int64_t)p * n + c], *m);
+    } else if (fr != 0.0) {
+      double* x = X + (int64_t)r * n + (c - n);
+      *x = __fma_rn(-fr, X[(int64_t)p * n + (c - n)], *x);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (p + 1 < n) gj_prepare(n, p + 1, M, X, f, fail);
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 template <class F>
@@ -656,14 +704,25 @@ void bsr_to_dense(const Bsr& A, double* dense, cudaStream_t s) {
 bool dense_inverse(int n, double* M, double* Minv, cudaStream_t s) {
   DBuf<int> fail(1);
   FSI_CUDA(cudaMemsetAsync(fail.p, 0, sizeof(int), s));
+  DBuf<double> f(n > 0 ? n : 1);      // released after the synchronisation below
+  DBuf<unsigned> ticket(1);
   if (n > 0) {
-    k_gauss_jordan<<<1, 1024, 0, s>>>(n, M, Minv, fail.p);
+    FSI_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s));
+    const int sms = device_sms();
+    k_gj_init<<<std::min(div_up(n, kGjThreads / 32), 4 * sms), kGjThreads, 0, s>>>(n, M, Minv);
     FSI_CHECK_LAUNCH();
+    k_gj_first<<<1, kGjThreads, 0, s>>>(n, M, Minv, f.p, fail.p);
+    FSI_CHECK_LAUNCH();
+    const int grid = std::min(div_up(2 * (int64_t)n * n, kGjThreads), 2 * sms);
+    for (int p = 0; p < n; ++p) {
+      k_gj_step<<<grid, kGjThreads, 0, s>>>(n, p, M, Minv, f.p, ticket.p, fail.p);
+      FSI_CHECK_LAUNCH();
+    }
   }
-  int f = 0;
-  FSI_CUDA(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int failed = 0;
+  FSI_CUDA(cudaMemcpyAsync(&failed, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   FSI_CUDA(cudaStreamSynchronize(s));
-  return f == 0;
+  return failed == 0;
 }
 
 }  // namespace fsi

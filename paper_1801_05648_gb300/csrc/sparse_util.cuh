@@ -69,9 +69,9 @@ bool bsr_make_delta16(Bsr& A, cudaStream_t s);
 // Dense row-major copy (n = nbr*br rows, nbc*bc cols) of a BSR matrix.
 void bsr_to_dense(const Bsr& A, double* dense, cudaStream_t s);
 
-// In-place inverse of an n x n row-major dense matrix (Gauss-Jordan with partial
-// pivoting, one thread block); all-zero rows are first replaced by identity rows.
-// Returns false when a pivot vanishes.
+// Inverse of an n x n row-major dense matrix M into Minv (Gauss-Jordan with partial
+// pivoting, one launch per pivot over the whole GPU; M is destroyed); all-zero rows
+// are first replaced by identity rows.  Returns false when a pivot vanishes.
 bool dense_inverse(int n, double* M, double* Minv, cudaStream_t s);
 
 }  // namespace fsi

@@ -80,13 +80,19 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_partial(int64_t n, const T*
 }
 
 // out[c] = (sqrt?) sum_k partials[c * np + k], one block per column c
+// (out[c] = 0 instead when *skip != 0)
 __global__ void __launch_bounds__(kRedThreads) k_reduce_cols(const double* __restrict__ partials, int np,
-                                                             const int* jcount, int joff, double* out, int take_sqrt) {
+                                                             const int* jcount, int joff, double* out, int take_sqrt,
+                                                             const int* skip) {
   dep_wait();
   __shared__ double sh[32];
   const int c = blockIdx.x;
   const int J = jcount ? (*jcount + joff) : joff;
   if (c >= J) return;
+  if (skip && *skip) {
+    if (threadIdx.x == 0) out[c] = 0.0;
+    return;
+  }
   double acc = 0.0;
   for (int k = threadIdx.x; k < np; k += blockDim.x) acc += partials[(size_t)c * np + k];
   acc = block_sum(acc, sh);
@@ -98,8 +104,10 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_cols(const double* __res
 __global__ void __launch_bounds__(kRedThreads) k_mdot_partial(int64_t n, const double* __restrict__ V, int64_t ldv,
                                                               const int* __restrict__ jcount, int joff,
                                                               const double* __restrict__ w,
-                                                              double* __restrict__ partials) {
+                                                              double* __restrict__ partials,
+                                                              const int* __restrict__ skip) {
   dep_wait();
+  if (skip && *skip) return;
   __shared__ double sh[32];
   const int J = *jcount + joff;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -128,8 +136,10 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot_partial(int64_t n, const d
 __global__ void __launch_bounds__(kRedThreads) k_maxpy(int64_t n, const double* __restrict__ V, int64_t ldv,
                                                        const int* __restrict__ jcount, int joff,
                                                        const double* __restrict__ h, double sign,
-                                                       double* __restrict__ w, double* __restrict__ nrm_partials) {
+                                                       double* __restrict__ w, double* __restrict__ nrm_partials,
+                                                       const int* __restrict__ skip) {
   dep_wait();
+  if (skip && *skip) return;
   __shared__ double hs[256];
   __shared__ double sh[32];
   const int J = *jcount + joff;
@@ -175,8 +185,10 @@ __device__ __forceinline__ void chunk_of(int64_t n, int64_t& lo, int64_t& hi) {
 __global__ void __launch_bounds__(kRedThreads, 4) k_mdot_partial_v2(int64_t n, const double* __restrict__ V,
                                                                  int64_t ldv, const int* __restrict__ jcount,
                                                                  int joff, const double* __restrict__ w,
-                                                                 double* __restrict__ partials) {
+                                                                 double* __restrict__ partials,
+                                                                 const int* __restrict__ skip) {
   dep_wait();
+  if (skip && *skip) return;
   __shared__ double sh[kDotCols][kRedThreads / 32];
   const int J = *jcount + joff;
   int64_t lo, hi;
@@ -225,8 +237,10 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_mdot_partial_v2(int64_t n, c
 __global__ void __launch_bounds__(kRedThreads) k_maxpy_v2(int64_t n, const double* __restrict__ V, int64_t ldv,
                                                           const int* __restrict__ jcount, int joff,
                                                           const double* __restrict__ h, double sign,
-                                                          double* __restrict__ w, double* __restrict__ nrm_partials) {
+                                                          double* __restrict__ w, double* __restrict__ nrm_partials,
+                                                          const int* __restrict__ skip) {
   dep_wait();
+  if (skip && *skip) return;
   extern __shared__ double hs[];
   __shared__ double sh[32];
   const int J = *jcount + joff;
@@ -257,6 +271,45 @@ __global__ void __launch_bounds__(kRedThreads) k_maxpy_v2(int64_t n, const doubl
   if (nrm_partials) {
     nacc = block_sum(nacc, sh);
     if (threadIdx.x == 0) nrm_partials[blockIdx.x] = nacc;
+  }
+}
+
+// Arnoldi defect: w = V_j - w over the block's chunk (j = *jcount), per-block sums of w^2.
+__global__ void __launch_bounds__(kRedThreads) k_defect(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                                        const int* __restrict__ jcount, double* __restrict__ w,
+                                                        double* __restrict__ partials) {
+  dep_wait();
+  __shared__ double sh[32];
+  const double* vj = V + (size_t)(*jcount) * ldv;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double acc = 0.0;
+  for (int64_t r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+    const double d = vj[r] - w[r];
+    w[r] = d;
+    acc = fma(d, d, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// A second Gram-Schmidt pass is needed when the first kept less than eta of the
+// vector's norm (a: its partial sums of squares after the pass, b: before):
+// flag[0] = 1 when it is not (the skip flag of the second pass), flag[1] += passes needed
+__global__ void __launch_bounds__(kRedThreads) k_reorth_flag(const double* __restrict__ pa,
+                                                             const double* __restrict__ pb, int np, double eta2,
+                                                             int* __restrict__ flag) {
+  dep_wait();
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) { a += pa[k]; b += pb[k]; }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    const int need = (a < eta2 * b) ? 1 : 0;
+    flag[0] = 1 - need;
+    flag[1] += need;
   }
 }
 
@@ -292,7 +345,8 @@ void cast(int64_t n, const Ti* x, To* y, cudaStream_t s) {
 template <class T>
 void dot_dev(int64_t n, const T* x, const T* y, double* partials, double* out, cudaStream_t s) {
   launch_k(k_dot_partial<T>, kRedBlocks, kRedThreads, 0, s, n, x, y, partials);
-  launch_k(k_reduce_cols, 1, kRedThreads, 0, s, partials, kRedBlocks, (const int*)nullptr, 1, out, 0);
+  launch_k(k_reduce_cols, 1, kRedThreads, 0, s, partials, kRedBlocks, (const int*)nullptr, 1, out, 0,
+           (const int*)nullptr);
 }
 template <class T>
 double dot_host(int64_t n, const T* x, const T* y, double* partials, double* out, cudaStream_t s) {
@@ -304,25 +358,35 @@ double dot_host(int64_t n, const T* x, const T* y, double* partials, double* out
 }
 
 void mdot(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* w, double* partials,
-          double* h, int maxcols, cudaStream_t s) {
+          double* h, int maxcols, cudaStream_t s, const int* skip) {
   if (ldv % 2 == 0 && aligned16(V) && aligned16(w))
-    launch_k(k_mdot_partial_v2, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, w, partials);
+    launch_k(k_mdot_partial_v2, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, w, partials, skip);
   else
-    launch_k(k_mdot_partial, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, w, partials);
-  launch_k(k_reduce_cols, maxcols, kRedThreads, 0, s, partials, kRedBlocks, jcount, joff, h, 0);
+    launch_k(k_mdot_partial, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, w, partials, skip);
+  launch_k(k_reduce_cols, maxcols, kRedThreads, 0, s, partials, kRedBlocks, jcount, joff, h, 0, skip);
 }
 
 void maxpy(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* h, double sign,
-           double* w, double* nrm_partials, int maxcols, cudaStream_t s) {
+           double* w, double* nrm_partials, int maxcols, cudaStream_t s, const int* skip) {
   if (maxcols > 0 && ldv % 2 == 0 && aligned16(V) && aligned16(w))
     launch_k(k_maxpy_v2, kRedBlocks, kRedThreads, sizeof(double) * maxcols, s, n, V, ldv, jcount, joff, h, sign, w,
-             nrm_partials);
+             nrm_partials, skip);
   else
-    launch_k(k_maxpy, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, h, sign, w, nrm_partials);
+    launch_k(k_maxpy, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, joff, h, sign, w, nrm_partials, skip);
 }
 
 void finish_norm(const double* partials, double* out, cudaStream_t s) {
-  launch_k(k_reduce_cols, 1, kRedThreads, 0, s, partials, kRedBlocks, (const int*)nullptr, 1, out, 1);
+  launch_k(k_reduce_cols, 1, kRedThreads, 0, s, partials, kRedBlocks, (const int*)nullptr, 1, out, 1,
+           (const int*)nullptr);
+}
+
+void arnoldi_defect(int64_t n, const double* V, int64_t ldv, const int* jcount, double* w, double* partials,
+                    cudaStream_t s) {
+  launch_k(k_defect, kRedBlocks, kRedThreads, 0, s, n, V, ldv, jcount, w, partials);
+}
+
+void reorth_flag(const double* after, const double* before, double eta, int* flag, cudaStream_t s) {
+  launch_k(k_reorth_flag, 1, kRedThreads, 0, s, after, before, kRedBlocks, eta * eta, flag);
 }
 
 template void axpby<double>(int64_t, double, const double*, double, double*, cudaStream_t);

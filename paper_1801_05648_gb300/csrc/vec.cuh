@@ -30,16 +30,25 @@ template <class T> double dot_host(int64_t n, const T* x, const T* y, double* pa
 // Gram-Schmidt pieces.  V holds basis vectors of length n with leading dimension
 // ldv (vector i at V + i*ldv); the number of active vectors is read on the
 // device from *jcount (+ joff), so a captured graph can be replayed for every j.
-// h[i] = <V_i, w>, i < *jcount + joff
+// h[i] = <V_i, w>, i < *jcount + joff.  With skip != nullptr and *skip != 0 (read on
+// the device) the products are not formed and h[i] = 0.
 void mdot(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* w, double* partials,
-          double* h, int maxcols, cudaStream_t s);
-// w -= sum_i h[i] V_i; if nrm_partials != nullptr also writes per-block sums of w^2.
+          double* h, int maxcols, cudaStream_t s, const int* skip = nullptr);
+// w -= sign * sum_i h[i] V_i; if nrm_partials != nullptr also writes per-block sums of w^2.
 // maxcols bounds the number of vectors (*jcount + joff) for the shared-memory copy
 // of h (0: unknown, the unvectorised kernel runs).  Both multi-products use 16-byte
-// loads when V's columns and w are 16-byte aligned (ldv even).
+// loads when V's columns and w are 16-byte aligned (ldv even).  With *skip != 0
+// nothing is written (w and the partial sums keep their values).
 void maxpy(int64_t n, const double* V, int64_t ldv, const int* jcount, int joff, const double* h, double sign,
-           double* w, double* nrm_partials, int maxcols, cudaStream_t s);
+           double* w, double* nrm_partials, int maxcols, cudaStream_t s, const int* skip = nullptr);
 // out = sqrt(sum partials)
 void finish_norm(const double* partials, double* out, cudaStream_t s);
+// Arnoldi defect: w = V_j - w (j = *jcount), partials = per-block sums of w^2.
+void arnoldi_defect(int64_t n, const double* V, int64_t ldv, const int* jcount, double* w, double* partials,
+                    cudaStream_t s);
+// Second-pass test of Gram-Schmidt (kRedBlocks partial sums of squares of the vector
+// after and before one pass): flag[0] = 0 when sum(after) < eta^2 sum(before) (a second
+// pass is needed), else 1 (the skip flag of that pass); flag[1] += 1 - flag[0].
+void reorth_flag(const double* after, const double* before, double eta, int* flag, cudaStream_t s);
 
 }  // namespace fsi

@@ -78,7 +78,8 @@ class Stats(ctypes.Structure):
                 ("precond_build_s", ctypes.c_double), ("solve_s", ctypes.c_double),
                 ("operator_bytes", ctypes.c_double), ("precond_bytes", ctypes.c_double),
                 ("relres_hist", ctypes.POINTER(ctypes.c_double)), ("hist_len", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int64), ("learned_accepted", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int64), ("learned_accepted", ctypes.c_int),
+                ("reorth_passes", ctypes.c_int)]
 
 
 class TrainParams(ctypes.Structure):
@@ -102,6 +103,7 @@ class SolveStats:
     history: list
     kernel_launches: int
     learned_accepted: int = 0
+    reorth_passes: int = 0
 
 
 _lib = None
@@ -284,7 +286,7 @@ class FSISolver:
         hist = [st.relres_hist[i] for i in range(st.hist_len)] if st.hist_len else []
         out = SolveStats(st.iters, st.cycles, st.status, st.true_relres, st.setup_s, st.precond_build_s,
                          st.solve_s, st.operator_bytes, st.precond_bytes, hist, st.kernel_launches,
-                         st.learned_accepted)
+                         st.learned_accepted, st.reorth_passes)
         if rc != FSI_OK and raise_on_error:
             raise FSIError(rc, self._lib.fsi_last_error(self._h).decode())
         return out
