@@ -113,9 +113,9 @@ typedef struct fsi_params {
   /* learned stage: take the correction only when ||r' - A c|| < learned_accept * ||r'||
      (0.1; at 0.3 and above the trained stage's accepted corrections stall FGMRES) */
   double learned_accept;
-  /* SpMV L2 prefetch: 0 none, 1 each CTA bulk-prefetches its slice of the matrix arrays
-     into L2 before waiting for the previous kernel, 2 the same with at most 5 persistent
-     CTAs per SM walking longer slices (1) */
+  /* SpMV L2 prefetch: 0 none, 1 each CTA bulk-prefetches the head of its slice of the
+     matrix arrays (at most 32 KB per matrix) into L2 before waiting for the previous
+     kernel, 2 the same with at most 5 persistent CTAs per SM walking longer slices (1) */
   int spmv_prefetch;
   /* FSI_CLUSTER_COARSE / FSI_GRID_COARSE: levels whose matrix values take at most this
      many bytes run in the single coarse launch (6e6) */

@@ -8,6 +8,9 @@ namespace fsi {
 
 namespace {
 
+// L2 prefetch per CTA and matrix: at most this many bytes from the head of its slice.
+constexpr int kPrefetchCap = 32768;
+
 // ALLOW16: the first matrix's 16-bit column offsets are read when present (FP32
 // Chebyshev steps on the square level matrices).
 template <class T, int BR, int BC1, int BC2, class Epi, class G1, bool ALLOW16 = false>
@@ -30,7 +33,7 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
   int64_t nnzb2 = 0;
   if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; nnzb2 = A2->nnzb; }
   const int pre_wait = tu.setup_depth == 0 ? 1 : 0;
-  const int pf = tu.prefetch > 0 ? 1 : 0;
+  const int pf = tu.prefetch > 0 ? kPrefetchCap : 0;
   if constexpr (ALLOW16 && sizeof(T) == 4 && BC2 == 0) {
     if (A1.cd16.p) {
       if (tu.unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)

@@ -329,10 +329,13 @@ __device__ __forceinline__ void prefetch_blocks(const T* v, int64_t nnzb, int a,
 }
 
 // One CTA handles the contiguous block rows [blockIdx.x * rows_per_cta, + rows_per_cta),
-// blockDim.x / tpr rows per pass, tpr lanes per row.  With prefetch, thread 0 first
-// asks L2 for the CTA's slice of the (constant) matrix arrays, before waiting for the
-// previous kernel (programmatic dependent launch), so the slice streams in while
-// that kernel drains and while the CTA works through its first rows.  Reading the
+// blockDim.x / tpr rows per pass, tpr lanes per row.  With prefetch (> 0, a byte cap),
+// thread 0 first asks L2 for the head of the CTA's slice of the (constant) matrix
+// arrays, at most `prefetch` bytes of each matrix, before waiting for the previous
+// kernel (programmatic dependent launch), so the head streams in while that kernel
+// drains and while the CTA works through its first rows.  The cap keeps the lines in
+// flight for all resident CTAs well inside L2: a whole 80 KB FP64 slice per CTA
+// (about 60 MB for the resident CTAs) was evicted before use and read twice.  Reading the
 // row pointers before the wait is only allowed once the matrices are built
 // (pre_wait != 0); during set-up the previous kernel may still be writing them.
 template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4, class CI1 = int>
@@ -345,11 +348,15 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
   const int r1 = r0 + rows_per_cta < nbr ? r0 + rows_per_cta : nbr;
   if (!pre_wait) dep_wait();
   if (prefetch && threadIdx.x == 0 && r0 < r1) {
-    const int a = rp1[r0], b = rp1[r1];
+    const int a = rp1[r0];
+    const int cap1 = prefetch / (int)(BR * BC1 * sizeof(T) + sizeof(CI1));
+    const int b = rp1[r1] - a < cap1 ? rp1[r1] : a + cap1;
     prefetch_blocks<T, BR, BC1>(v1, nnzb1, a, b);
     prefetch_l2(ci1 + a, sizeof(CI1) * (size_t)(b - a));
     if constexpr (BC2 > 0) {
-      const int a2 = rp2[r0], b2 = rp2[r1];
+      const int a2 = rp2[r0];
+      const int cap2 = prefetch / (int)(BR * BC2 * sizeof(T) + sizeof(int));
+      const int b2 = rp2[r1] - a2 < cap2 ? rp2[r1] : a2 + cap2;
       prefetch_blocks<T, BR, BC2>(v2, nnzb2, a2, b2);
       prefetch_l2(ci2 + a2, sizeof(int) * (size_t)(b2 - a2));
     }
