@@ -642,12 +642,14 @@ void apply_block(Context& C, int which, const T* in, T* out) {
 }
 
 void apply_operator(Context& C, const double* x, double* y) {
+  OuterOperatorScope outer;
   const int64_t nv = C.off[4];
   spmv2_axpby<double>(C.AVV, x, &C.AVP, x + nv, 1.0, 0.0, y, C.s);
   spmv2_axpby<double>(C.APV, x, &C.APP, x + nv, 1.0, 0.0, y + nv, C.s);
 }
 
 static void operator_resid(Context& C, const double* x, const double* b, double* r) {
+  OuterOperatorScope outer;
   const int64_t nv = C.off[4];
   spmv2_resid<double>(C.AVV, x, &C.AVP, x + nv, b, r, C.s);
   spmv2_resid<double>(C.APV, x, &C.APP, x + nv, b + nv, r + nv, C.s);

@@ -74,6 +74,33 @@ __device__ __forceinline__ void load_gather(const T* __restrict__ p, T* out) {
   }
 }
 
+// FP64 gathers with the L2 evict-last policy: the gathered vector (71 MB in FP64 on
+// the 1024x512 system) then outlives the evict-first matrix stream in L2.  FP64
+// launches use them unless the caller turns them off (OuterOperatorScope).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+template <int N>
+__device__ __forceinline__ void load_gather_keep(const double* __restrict__ p, double* out) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
+  const uint64_t pol = l2_evict_last_policy();
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i)
+      asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+          : "=d"(out[2 * i]), "=d"(out[2 * i + 1])
+          : "l"(p + 2 * i), "l"(pol));
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(out[i]) : "l"(p + i), "l"(pol));
+  }
+#else
+  for (int i = 0; i < N; ++i) out[i] = p[i];
+#endif
+}
+
 // FP32 copies of 3 x 3-block matrices are stored planar (bsr_make_fp32): values
 // 0-3 of every block, then values 4-7 of every block, then value 8 of every block,
 // so that the lanes of a row group, which read consecutive blocks, issue two
@@ -106,7 +133,15 @@ __device__ __forceinline__ void load_block(const T* __restrict__ v, int64_t nnzb
 template <class T, int BC>
 struct GatherX {
   const T* x;
-  __device__ __forceinline__ void operator()(int c, T* out) const { load_gather<T, BC>(x + (size_t)c * BC, out); }
+  int keep = 0;   // FP64: gather with the L2 evict-last policy
+  __device__ __forceinline__ void operator()(int c, T* out) const {
+    if constexpr (sizeof(T) == 8) {
+      if (keep) load_gather_keep<BC>(x + (size_t)c * BC, out);
+      else load_gather<T, BC>(x + (size_t)c * BC, out);
+    } else {
+      load_gather<T, BC>(x + (size_t)c * BC, out);
+    }
+  }
 };
 // (dinv * b * s)[c] segment: the first Chebyshev iterate from x = 0, formed on the fly.
 template <class T, int BC>
@@ -340,6 +375,7 @@ __device__ __forceinline__ void prefetch_blocks(const T* v, int64_t nnzb, int a,
 // (pre_wait != 0); during set-up the previous kernel may still be writing them.
 template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4, class CI1 = int>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per_cta, int prefetch, int pre_wait,
+    int keep_x2,
     const int* __restrict__ rp1, const CI1* __restrict__ ci1, const T* __restrict__ v1, int64_t nnzb1, G1 g1,
     const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, int64_t nnzb2,
     const T* __restrict__ x2,
@@ -376,8 +412,8 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
       row_accumulate<T, BR, BC1, UREQ, G1, CI1>(ci1, sizeof(CI1) == 4 ? 0 : row, v1, nnzb1, g1, rp1[row],
                                                 rp1[row + 1], lane, tpr, acc);
       if constexpr (BC2 > 0)
-        row_accumulate<T, BR, BC2, UREQ>(ci2, 0, v2, nnzb2, GatherX<T, BC2>{x2}, rp2[row], rp2[row + 1], lane, tpr,
-                                         acc);
+        row_accumulate<T, BR, BC2, UREQ>(ci2, 0, v2, nnzb2, GatherX<T, BC2>{x2, keep_x2}, rp2[row], rp2[row + 1],
+                                         lane, tpr, acc);
     }
     for (int off = tpr >> 1; off > 0; off >>= 1)
 #pragma unroll
