@@ -135,6 +135,11 @@ typedef struct fsi_params {
      divided by 2^spmv_lane_shift, at least 1 (0..4; 0).  Fewer lanes per row put
      more rows, and more blocks per lane, into each pass of a warp */
   int spmv_lane_shift;
+  /* 2 x 2 FP32 Chebyshev steps on large matrices by persistent CTAs that have the TMA
+     engine (cp.async.bulk) copy each chunk's 16-bit column offsets into shared memory
+     one chunk ahead: 1 on, 0 off (0).  Bit-identical to the default kernel, and measured
+     slower on the GB300 (116 vs 104 us per 1024x512 level-0 step) */
+  int spmv_stage;
 } fsi_params;
 
 enum { FSI_PRECOND_LDU = 0, FSI_PRECOND_LOWER = 1, FSI_PRECOND_UPPER = 2, FSI_PRECOND_DIAG = 3 };

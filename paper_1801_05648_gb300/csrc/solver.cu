@@ -883,6 +883,11 @@ int fgmres_solve(Context& C, const double* b, double* x, double tol) {
       throw Error(ECUDA_, "a wait of the tensor-core MLP timed out; its corrections are not valid");
     }
   }
+  if (spmv_stage_failed(C.s)) {
+    C.last_status = ECUDA_;
+    C.solve_s = secs(t0, clk::now());
+    throw Error(ECUDA_, "a staged Chebyshev step timed out waiting for its copies; the result is not valid");
+  }
   if (C.prm.flags & GRID_COARSE) {
     bool failed = false;
     for (auto& H : C.H) failed = coarse_failed(H, C.s) || failed;

@@ -678,19 +678,45 @@ void bsr_make_fp32(Bsr& A, cudaStream_t s) {
   }
 }
 
+// Largest slice (in blocks, counted from the 8-entry boundary below it) of the CTAs
+// that take R consecutive block rows each: the shared-memory size of the staged
+// Chebyshev kernel.
+__global__ void k_stage_max(int nbr, const int* __restrict__ rp, int R, int* __restrict__ out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t r0 = c * R;
+  if (r0 >= nbr) return;
+  const int64_t r1 = r0 + R < nbr ? r0 + R : nbr;
+  atomicMax(out, rp[r1] - (rp[r0] & ~7));
+}
+
 bool bsr_make_delta16(Bsr& A, cudaStream_t s) {
   A.cd16.release();
+  A.stage_rows = A.stage_max = 0;
   if (A.nbr == 0 || A.nbr != A.nbc || A.nnzb == 0) return false;
-  DBuf<int> of(1);
-  FSI_CUDA(cudaMemsetAsync(of.p, 0, sizeof(int), s));
-  A.cd16.alloc(A.nnzb);
+  DBuf<int> of(2);
+  FSI_CUDA(cudaMemsetAsync(of.p, 0, 2 * sizeof(int), s));
+  // 8 spare entries: the staged kernel copies whole 16-byte groups of offsets
+  A.cd16.alloc(A.nnzb + 8);
+  FSI_CUDA(cudaMemsetAsync(A.cd16.p + A.nnzb, 0, 8 * sizeof(int16_t), s));
   k_delta16<<<div_up(A.nbr, 128), 128, 0, s>>>(A.nbr, A.rowptr.p, A.colind.p, A.cd16.p, of.p);
   FSI_CHECK_LAUNCH();
-  int h = 0;
-  FSI_CUDA(cudaMemcpyAsync(&h, of.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  const int R = A.br == 2 && A.bc == 2 ? 256 / A.tpr : 0;
+  if (R > 0) {
+    k_stage_max<<<div_up(div_up(A.nbr, R), 128), 128, 0, s>>>(A.nbr, A.rowptr.p, R, of.p + 1);
+    FSI_CHECK_LAUNCH();
+  }
+  int h[2] = {0, 0};
+  FSI_CUDA(cudaMemcpyAsync(h, of.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   FSI_CUDA(cudaStreamSynchronize(s));
-  if (h) A.cd16.release();
-  return !h;
+  if (h[0]) {
+    A.cd16.release();
+    return false;
+  }
+  if (R > 0) {
+    A.stage_rows = R;
+    A.stage_max = h[1];
+  }
+  return true;
 }
 
 void bsr_to_dense(const Bsr& A, double* dense, cudaStream_t s) {

@@ -11,6 +11,42 @@ namespace {
 // L2 prefetch per CTA and matrix: at most this many bytes from the head of its slice.
 constexpr int kPrefetchCap = 32768;
 
+// Staged 2 x 2 Chebyshev steps: at most this much dynamic shared memory per CTA.
+constexpr int kStageSmemMax = 100 * 1024;
+
+// Set by a staged kernel whose wait for its copies gave up (see spmv_stage_failed).
+__device__ int g_stage_err = 0;
+
+int* stage_err_ptr() {
+  static int* p = nullptr;   // the symbol's address, looked up once
+  if (!p) FSI_CUDA(cudaGetSymbolAddress((void**)&p, g_stage_err));
+  return p;
+}
+
+// Persistent grid of the staged kernel: up to eight 256-thread CTAs per SM (its
+// register limit), fewer if shared memory runs out.
+inline int staged_grid(int nchunks, int smax) {
+  const size_t per_cta = staged_smem_bytes(smax) + 1024;
+  int c = (int)((200 * 1024) / per_cta);
+  c = c < 1 ? 1 : (c > 8 ? 8 : c);
+  const int g = device_sms() * c;
+  return nchunks < g ? nchunks : g;
+}
+
+template <class Epi, class G1, int UREQ>
+void launch_staged(const Bsr& A1, const G1& g1, const Epi& epi, int tpr, int rows_per_cta, int nchunks, int grid,
+                   int pre_wait, cudaStream_t s) {
+  static bool attr = false;   // the opt-in above 48 KB, set once per instantiation
+  if (!attr) {
+    FSI_CUDA(cudaFuncSetAttribute(k_bsr_cheb_staged<Epi, G1, UREQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kStageSmemMax));
+    attr = true;
+  }
+  launch_k(k_bsr_cheb_staged<Epi, G1, UREQ>, grid, 256, staged_smem_bytes(A1.stage_max), s, A1.nbr, tpr,
+           rows_per_cta, nchunks, pre_wait, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<float>(), g1, epi,
+           A1.stage_max, stage_err_ptr());
+}
+
 // ALLOW16: the first matrix's 16-bit column offsets are read when present (FP32
 // Chebyshev steps on the square level matrices).
 template <class T, int BR, int BC1, int BC2, class Epi, class G1, bool ALLOW16 = false>
@@ -36,6 +72,17 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
   const int pf = tu.prefetch > 0 ? kPrefetchCap : 0;
   const int keep = (sizeof(T) == 8 && tu.keep_x64) ? 1 : 0;
   if constexpr (ALLOW16 && sizeof(T) == 4 && BC2 == 0) {
+    if constexpr (BR == 2 && BC1 == 2) {
+      // staged for matrices with at least two chunks per CTA of the persistent grid
+      if (A1.cd16.p && tu.stage && A1.stage_rows == rows_per_cta && A1.stage_max > 0 &&
+          staged_smem_bytes(A1.stage_max) <= (size_t)kStageSmemMax) {
+        const int grid = staged_grid(blocks, A1.stage_max);
+        if (blocks >= 2 * grid) {
+          launch_staged<Epi, G1, 4>(A1, g1, epi, tpr, rows_per_cta, blocks, grid, pre_wait, s);
+          return;
+        }
+      }
+    }
     if (A1.cd16.p) {
       if (tu.unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
         launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8, int16_t>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta,
@@ -81,6 +128,14 @@ inline void check_pair(const Bsr& A1, const Bsr* A2) {
 }
 
 }  // namespace
+
+bool spmv_stage_failed(cudaStream_t s) {
+  int h = 0;
+  FSI_CUDA(cudaMemcpyAsync(&h, stage_err_ptr(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  if (h) FSI_CUDA(cudaMemsetAsync(stage_err_ptr(), 0, sizeof(int), s));
+  return h != 0;
+}
 
 template <class T>
 void spmv_axpby(const Bsr& A, const T* x, T alpha, T beta, T* y, cudaStream_t s) {

@@ -422,6 +422,151 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
   }
 }
 
+// ------------------------------------------------------------------ staged 2 x 2 FP32 steps
+// Chebyshev steps (EpiCheb, EpiChebFromZero) on 2 x 2 FP32 blocks with 16-bit column
+// offsets, with the offsets staged one chunk ahead.  In k_bsr_spmv a warp's pass makes
+// two dependent memory round trips: column offsets (with the blocks), then the x they
+// index.  Here a persistent CTA walks chunks of R consecutive block rows (chunk c,
+// c + gridDim.x, ...; R = 256 / tpr, one k_bsr_spmv CTA's rows).  While it computes
+// chunk i, the TMA engine copies the column offsets of chunk i + 2 into a two-stage
+// shared-memory ring (cp.async.bulk from the 8-entry boundary below the chunk's first
+// block, 16-byte aligned, completing on the stage's mbarrier), and the chunk's block
+// values are bulk-prefetched into L2.  A pass then issues its x gathers and its block
+// loads together: one round trip.  Each lane visits the same blocks in the same order
+// and rounds the same way as k_bsr_spmv, so the results are bit-identical.  smax bounds
+// every chunk's offsets, counted from that 8-entry boundary (bsr_make_delta16).  Every
+// wait is bounded (about a second of clock); on a timeout the CTA sets *err, waits
+// (bounded) for the copy still in flight and returns.
+constexpr int kStageDepth = 2;
+
+__device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000ll) return false;
+  }
+}
+
+// bytes of one ring stage (column offsets) for chunks of at most smax blocks
+__host__ __device__ constexpr size_t stage_bytes(int smax) { return (2 * ((size_t)smax + 8) + 15) & ~(size_t)15; }
+// dynamic shared memory of the staged kernel: the ring, then one mbarrier per stage
+__host__ __device__ constexpr size_t staged_smem_bytes(int smax) {
+  return kStageDepth * stage_bytes(smax) + 8 * kStageDepth;
+}
+
+// Thread 0: the column offsets of chunk c into ring stage st, and an L2 prefetch of
+// its block values (no-op past the last chunk).
+__device__ __forceinline__ void stage_issue(int c, int nchunks, int R, int nbr, int st, uint32_t sbase, int smax,
+                                            const int* __restrict__ rp, const int16_t* __restrict__ ci,
+                                            const float* __restrict__ v, int* s_a8) {
+  if (c >= nchunks) return;
+  const int r0 = c * R;
+  const int r1 = r0 + R < nbr ? r0 + R : nbr;
+  const int a = rp[r0], b = rp[r1];
+  const int a8 = a & ~7, b8 = (b + 7) & ~7;
+  s_a8[st] = a8;
+  const uint32_t cbytes = 2u * (uint32_t)(b8 - a8);
+  const uint32_t buf = sbase + (uint32_t)(st * stage_bytes(smax));
+  const uint32_t bar = sbase + (uint32_t)(kStageDepth * stage_bytes(smax)) + 8u * st;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(cbytes) : "memory");
+  if (cbytes)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(buf),
+                 "l"(ci + a8), "r"(cbytes), "r"(bar)
+                 : "memory");
+  prefetch_l2(v + 4 * (size_t)a, 16 * (size_t)(b - a));
+}
+
+template <class Epi, class G1, int UREQ>
+__global__ void __launch_bounds__(256) k_bsr_cheb_staged(int nbr, int tpr, int R, int nchunks, int pre_wait,
+                                                         const int* __restrict__ rp, const int16_t* __restrict__ ci,
+                                                         const float* __restrict__ v, G1 g1, Epi epi, int smax,
+                                                         int* __restrict__ err) {
+  constexpr int BR = 2, BC = 2;
+  constexpr int U = unroll_for<float, BR, BC, UREQ>();
+  extern __shared__ __align__(16) unsigned char stage_sm[];
+  __shared__ int s_a8[kStageDepth];
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage_sm);
+  const uint32_t bar0 = sbase + (uint32_t)(kStageDepth * stage_bytes(smax));
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStageDepth; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * st) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (!pre_wait) dep_wait();
+  if (threadIdx.x == 0)
+    for (int st = 0; st < kStageDepth; ++st)
+      stage_issue(blockIdx.x + st * gridDim.x, nchunks, R, nbr, st, sbase, smax, rp, ci, v, s_a8);
+  __syncthreads();
+  if (pre_wait) dep_wait();
+  const int lane = threadIdx.x & (tpr - 1);
+  for (int i = 0;; ++i) {
+    const int c = blockIdx.x + i * gridDim.x;
+    if (c >= nchunks) break;
+    const int st = i % kStageDepth;
+    const int r0 = c * R;
+    const int r1 = r0 + R < nbr ? r0 + R : nbr;
+    const int row = r0 + threadIdx.x / tpr;     // R = blockDim.x / tpr: one row per lane group
+    const bool valid = row < r1;
+    typename Epi::Pre pre;
+    if (valid && lane == 0) pre = epi.load(row);
+    int kb = 0, ke = 0;
+    if (valid) { kb = rp[row]; ke = rp[row + 1]; }
+    const bool ok = stage_wait(bar0 + 8u * st, (uint32_t)(i / kStageDepth) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      // the copies still in flight: this stage's and the other stage's next chunk
+      stage_wait(bar0 + 8u * st, (uint32_t)(i / kStageDepth) & 1u);
+      if (c + (int)gridDim.x < nchunks)
+        stage_wait(bar0 + 8u * ((i + 1) % kStageDepth), (uint32_t)((i + 1) / kStageDepth) & 1u);
+      return;
+    }
+    const int16_t* sc = reinterpret_cast<const int16_t*>(stage_sm + st * stage_bytes(smax));
+    const int a8 = s_a8[st];
+    float acc[BR] = {0.f, 0.f};
+    for (int k0 = kb + lane; k0 < ke; k0 += tpr * U) {
+      float4 q[U];
+      float xv[U][BC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + u * tpr;
+        if (k < ke) {
+          q[u] = __ldcs(reinterpret_cast<const float4*>(v) + k);
+          g1(row + (int)sc[k - a8], xv[u]);
+        } else {
+          q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          xv[u][0] = 0.f;
+          xv[u][1] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        acc[0] = fma_rn(q[u].x, xv[u][0], acc[0]);
+        acc[0] = fma_rn(q[u].y, xv[u][1], acc[0]);
+        acc[1] = fma_rn(q[u].z, xv[u][0], acc[1]);
+        acc[1] = fma_rn(q[u].w, xv[u][1], acc[1]);
+      }
+    }
+    for (int off = tpr >> 1; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < BR; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off, tpr);
+    if (valid && lane == 0) epi.store(row, acc, pre);
+    __syncthreads();   // every lane is done with this stage: refill it
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      stage_issue(c + kStageDepth * (int)gridDim.x, nchunks, R, nbr, st, sbase, smax, rp, ci, v, s_a8);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host API
 // y = alpha * A x + beta * y
 template <class T> void spmv_axpby(const Bsr& A, const T* x, T alpha, T beta, T* y, cudaStream_t s);
@@ -437,6 +582,9 @@ template <class T> void spmv_restrict(const Bsr& R, const T* b, const Bsr& RAn, 
 template <class T> void spmv_cheb(const Bsr& A, const T* x, const T* b, const T* dinv, T* d, T* xo, T c1, T c2, cudaStream_t s);
 // y = dinv * (A x)
 template <class T> void spmv_dinv(const Bsr& A, const T* x, const T* dinv, T* y, cudaStream_t s);
+// True (and the flag cleared) if a staged Chebyshev step gave up waiting for its copies
+// since the last call; the results of that step are then not valid.
+bool spmv_stage_failed(cudaStream_t s);
 // Chebyshev steps 1 and 2 from x = 0 in one pass (see EpiChebFromZero)
 template <class T> void spmv_cheb_from_zero(const Bsr& A, const T* b, const T* dinv, T* d, T* xo, T inv_theta, T c1,
                                             T c2, cudaStream_t s);

@@ -63,7 +63,7 @@ def test_default_params(lib):
     assert p2.strength_theta == 0.08 and p2.dt_theta == 0.01
     assert (p2.cheb_degree_coarse, p2.spmv_prefetch, p2.cluster_max_bytes) == (2, 1, 6.0e6)
     assert p2.fluid_gmres_iters == 4 and P.FSI_FLUID_GMRES == 128 and P.FSI_MLP_CUDA_CORES == 256
-    assert p2.precond_variant == P.FSI_PRECOND_LDU == 0 and p2.spmv_lane_shift == 0
+    assert p2.precond_variant == P.FSI_PRECOND_LDU == 0 and p2.spmv_lane_shift == 0 and p2.spmv_stage == 0
 
 
 def _setup(lib, dim, n, rowptr, colind, vals, off, params=None):
@@ -129,6 +129,8 @@ def test_rejects_bad_params(lib):
     for v in (-1, 5):
         rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, spmv_lane_shift=v))
         assert rc == -1 and "spmv_lane_shift" in msg
+    rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, spmv_stage=2))
+    assert rc == -1 and "spmv_stage" in msg
 
 
 def test_null_context_calls(lib):

@@ -183,7 +183,7 @@ def test_graph_replay_is_bit_identical(torch_cuda):
 def test_launch_modes_are_bit_identical(torch_cuda):
     """Programmatic dependent launch on/off and the SpMV prefetch modes change only
     launch attributes and the assignment of rows to CTAs: every solve is bit-identical.
-    (Both knobs belong to the context: each call applies its own context's values.)"""
+    (The knobs belong to the context: each call applies its own context's values.)"""
     torch = torch_cuda
     import paper_1801_05648_gb300 as P
     s, o, ref, _, mr = case("2d_64x32", torch)
@@ -203,6 +203,28 @@ def test_launch_modes_are_bit_identical(torch_cuda):
                 first = (x, st.iters)
             else:
                 assert torch.equal(x, first[0]) and st.iters == first[1], (prec, kw)
+
+
+def test_staged_chebyshev_is_bit_identical(torch_cuda):
+    """The opt-in staged 2 x 2 FP32 Chebyshev kernel (persistent CTAs, column offsets
+    copied into shared memory by the TMA engine one chunk ahead) visits every block in
+    the order of the default kernel: FP32-AMG solves on 512x256 (level 0 of the mesh and
+    fluid hierarchies: 6,150 chunks, enough for the persistent grid) are bit-identical."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    s = fsigen.make_system(fsigen.CONFIGS["2d_512x256"])
+    b = torch.tensor(s.rhs, device="cuda")
+    out = []
+    for stage in (0, 1):
+        g = P.FSISolver.from_system(s, params=P.default_params(2, flags=P.FSI_USE_GRAPHS, spmv_stage=stage))
+        g.precond_build("fp32")
+        x = torch.zeros_like(b)
+        st = g.solve(b, x, 1e-8)
+        g.close()
+        assert st.status == 0
+        out.append((x, st.iters, st.history))
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert torch.equal(out[0][0], out[1][0])
 
 
 @pytest.mark.parametrize("deg", [0, 1, 3])
