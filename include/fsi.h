@@ -446,6 +446,29 @@ int fsi_set_flags(fsi_ctx* ctx, int flags);
 int fsi_set_harvest(fsi_ctx* ctx, double* buf_dev, int nvec);
 
 /*
+ * fsi_check_device_errors - wait for the context's stream, then report whether a
+ * bounded wait inside a kernel gave up since the last check (or the last fsi_solve,
+ * which checks by itself): the grid barrier of the FSI_GRID_COARSE kernel, the
+ * staged Chebyshev step (spmv_stage), the tensor-core MLP.  Such a wait gives up
+ * after about a second, sets a flag and lets the kernel end, so the context stays
+ * usable; the results of the calls since the last check are then not valid.
+ * Returns FSI_OK, or FSI_ECUDA with the message naming the waits (flags cleared).
+ * The asynchronous entry points (fsi_apply_block, fsi_apply_operator,
+ * fsi_learned_apply, fsi_smoother_step) leave this check to the caller.
+ */
+int fsi_check_device_errors(fsi_ctx* ctx);
+
+/*
+ * fsi_debug_inject - fault injection for tests of the bounded waits (0: none, the
+ * default).  Bit 1: the grid barrier of the FSI_GRID_COARSE kernel waits for one CTA
+ * more than its launch has; bit 2: the tensor-core MLP does not commit its first
+ * layer's MMAs to the barrier it then waits on.  The waits then run out (about a
+ * second each) and fsi_check_device_errors / fsi_solve report FSI_ECUDA.  Applies to
+ * the context's later launches; FSI_EINVAL for other bits.
+ */
+int fsi_debug_inject(fsi_ctx* ctx, int mask);
+
+/*
  * Training of the stage on residuals r' of one or more contexts.  Loss per
  * residual: L = ||r' - A c(r')||^2 / ||r'||^2 (A of the context given), i.e. the
  * error e - c of the pair (r', e = A^-1 r') in the residual norm that the accept

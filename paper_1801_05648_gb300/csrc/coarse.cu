@@ -156,11 +156,11 @@ __device__ void pass_any(const CoarseMat& M, const T* x, int kind, const T* b, c
 
 template <class T, bool GRID>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_vcycle(const CoarsePlan* __restrict__ plan, const T* b0,
-                                                                  T* x0, unsigned* bar, int* err) {
+                                                                  T* x0, unsigned* bar, int* err, int extra) {
   __shared__ int s_ok;
   int nblk, rank;
   if constexpr (GRID) {
-    nblk = (int)gridDim.x;
+    nblk = (int)gridDim.x + extra;   // extra > 0 only under fault injection (tests)
     rank = (int)blockIdx.x;
   } else {
     cg::cluster_group cluster = cg::this_cluster();
@@ -320,10 +320,11 @@ void launch(const CoarseRun<T>& run, const T* b0, T* x0, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (run.mode == COARSE_GRID)
-    FSI_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_vcycle<T, true>, run.plan.p, b0, x0, run.bar.p, run.err.p));
+    FSI_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_vcycle<T, true>, run.plan.p, b0, x0, run.bar.p, run.err.p,
+                                (fault_inject() & kInjectCoarseBarrier) ? 1 : 0));
   else
     FSI_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_vcycle<T, false>, run.plan.p, b0, x0, (unsigned*)nullptr,
-                                (int*)nullptr));
+                                (int*)nullptr, 0));
   ++g_kernel_launches;
 }
 

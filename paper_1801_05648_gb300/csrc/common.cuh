@@ -65,6 +65,15 @@ inline bool& mlp_tensor_cores() {
   thread_local bool on = true;
   return on;
 }
+// Host-side fault injection for the tests of the bounded waits (0 in normal use):
+// kInjectCoarseBarrier: the coarse V-cycle's grid barrier waits for one CTA more than
+// the launch has; kInjectMlpCommit: the tensor-core MLP does not commit its first
+// layer's MMAs to the barrier it then waits on.  Either wait then runs out.
+enum { kInjectCoarseBarrier = 1, kInjectMlpCommit = 2 };
+inline int& fault_inject() {
+  thread_local int v = 0;
+  return v;
+}
 
 // Streaming multiprocessors of the current device (looked up once per device).
 inline int device_sms() {

@@ -1,6 +1,7 @@
 // C ABI of the solver (declarations and contract in include/fsi.h).
 #include "../../include/fsi.h"
 #include "solver.cuh"
+#include "spmv.cuh"
 #include "vec.cuh"
 
 #include <cmath>
@@ -26,10 +27,12 @@ thread_local std::string g_setup_error;
 struct KnobScope {
   fsi::SpmvTuning tuning;
   bool pdl, mlp_tc;
+  int inject;
   double coarse_bytes;
   explicit KnobScope(const fsi::SolverParams& p)
       : tuning(fsi::spmv_tuning()), pdl(fsi::pdl_enabled()), mlp_tc(fsi::mlp_tensor_cores()),
-        coarse_bytes(fsi::coarse_max_bytes()) {
+        inject(fsi::fault_inject()), coarse_bytes(fsi::coarse_max_bytes()) {
+    fsi::fault_inject() = p.inject;
     fsi::spmv_tuning().unroll = p.spmv_unroll;
     fsi::spmv_tuning().prefetch = p.spmv_prefetch;
     fsi::spmv_tuning().lane_shift = p.spmv_lane_shift;
@@ -44,6 +47,7 @@ struct KnobScope {
     fsi::spmv_tuning().setup_depth = depth;
     fsi::pdl_enabled() = pdl;
     fsi::mlp_tensor_cores() = mlp_tc;
+    fsi::fault_inject() = inject;
     fsi::coarse_max_bytes() = coarse_bytes;
   }
   KnobScope(const KnobScope&) = delete;
@@ -456,6 +460,40 @@ int fsi_set_flags(fsi_ctx* ctx, int flags) {
     fsi::require((flags & fixed) == (ctx->C.prm.flags & fixed),
                  "FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_GRID_COARSE and FSI_NO_PDL are fixed at fsi_setup");
     ctx->C.prm.flags = flags;
+  });
+}
+
+int fsi_debug_inject(fsi_ctx* ctx, int mask) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::require((mask & ~(fsi::kInjectCoarseBarrier | fsi::kInjectMlpCommit)) == 0, "unknown injection bits");
+    drop_graph(ctx->C);   // the captured iteration holds the launch arguments of its capture
+    ctx->C.prm.inject = mask;
+  });
+}
+
+int fsi_check_device_errors(fsi_ctx* ctx) {
+  if (!ctx) return FSI_EINVAL;
+  return guarded(ctx, [&] {
+    fsi::Context& C = ctx->C;
+    FSI_CUDA(cudaStreamSynchronize(C.s));
+    std::string what;
+    if (C.built && (C.prm.flags & FSI_GRID_COARSE)) {
+      bool failed = false;
+      for (auto& H : C.H) failed = fsi::coarse_failed(H, C.s) || failed;
+      if (failed) what += " a grid barrier of the coarse-level kernel;";
+    }
+    if (fsi::spmv_stage_failed(C.s)) what += " a staged Chebyshev step;";
+    if (C.learned.counters.p) {
+      int e = 0;
+      FSI_CUDA(cudaMemcpy(&e, C.learned.counters.p + 2, sizeof(int), cudaMemcpyDeviceToHost));
+      if (e) {
+        FSI_CUDA(cudaMemset(C.learned.counters.p + 2, 0, sizeof(int)));
+        what += " the tensor-core MLP;";
+      }
+    }
+    if (!what.empty())
+      throw fsi::Error(fsi::ECUDA_, "bounded waits timed out in" + what + " those results are not valid");
   });
 }
 

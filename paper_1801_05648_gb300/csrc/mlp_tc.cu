@@ -131,20 +131,21 @@ __device__ __forceinline__ void put4(unsigned char* sm, int row, int col, float 
 }
 
 // one layer's MMA chain on (A_hi, A_lo) x B into the accumulator at dcol; issued by one thread
+// (commit = false only under fault injection: the wait on the barrier then runs out)
 __device__ __forceinline__ void issue_layer(uint32_t sbase, uint32_t boff, uint32_t tmem, uint32_t dcol, int ksteps,
-                                            int n, uint32_t bar) {
+                                            int n, uint32_t bar, bool commit = true) {
   const uint32_t id = idesc_tf32(n);
   for (int s = 0; s < ksteps; ++s)
     tc_mma(tmem + dcol, smem_desc(sbase + kOffAhi + 2u * kLbo * s), smem_desc(sbase + boff + 2u * kLbo * s), id,
            s > 0);
   for (int s = 0; s < ksteps; ++s)
     tc_mma(tmem + dcol, smem_desc(sbase + kOffAlo + 2u * kLbo * s), smem_desc(sbase + boff + 2u * kLbo * s), id, 1);
-  tc_commit(bar);
+  if (commit) tc_commit(bar);
 }
 
 __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* __restrict__ w16,
                                                     const double* __restrict__ rp, double* __restrict__ c,
-                                                    int* __restrict__ err) {
+                                                    int* __restrict__ err, int no_commit) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int t = threadIdx.x, warp = t >> 5;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* _
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (t == 0) issue_layer(sbase, kOffB1, tmem, 0, kTcK1 / 8, kMlpHidden, bar);
+    if (t == 0) issue_layer(sbase, kOffB1, tmem, 0, kTcK1 / 8, kMlpHidden, bar, !no_commit);
     // ---- layer 1 epilogue: gelu -> layer-2 operand
     bool ok = bar_wait(bar, phase);
     if (__syncthreads_or(!ok)) { failed = true; break; }
@@ -318,7 +319,8 @@ void mlp_apply_tc(const MlpGeom& g, const uint16_t* w16, const double* rp, doubl
   const int64_t tiles = (g.n_nodes + kTcRows - 1) / kTcRows;
   int64_t grid = (int64_t)device_sms() * 2;   // two 103-KB CTAs per SM
   if (grid > tiles) grid = tiles;
-  launch_k(k_mlp_tc, (int)grid, kTcRows, kTcSmem, s, g, w16, rp, c, err);
+  launch_k(k_mlp_tc, (int)grid, kTcRows, kTcSmem, s, g, w16, rp, c, err,
+           (fault_inject() & kInjectMlpCommit) ? 1 : 0);
 }
 
 }  // namespace fsi

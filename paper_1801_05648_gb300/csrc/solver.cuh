@@ -28,6 +28,7 @@ struct SolverParams {
   int precond_variant = 0;       // 0 Alg. 2 (LDU), 1 (D + L)^-1, 2 (D + U)^-1, 3 D^-1
   int spmv_lane_shift = 0;       // FP32 SpMV lanes per block row divided by 2^shift
   int spmv_stage = 0;            // staged 2 x 2 FP32 Chebyshev steps (opt-in)
+  int inject = 0;                // fault injection for the bounded-wait tests (fsi_debug_inject)
 };
 
 enum Flags { X0_GIVEN = 1, USE_GRAPHS = 2, NO_RIGID_MODES = 4, CLUSTER_COARSE = 8, LEARNED = 16, NO_PDL = 32,

@@ -34,7 +34,11 @@ EXPORTED = ["fsi_default_params", "fsi_setup", "fsi_precond_build", "fsi_solve",
             "fsi_trainer_create", "fsi_trainer_step", "fsi_trainer_loss", "fsi_trainer_update",
             "fsi_trainer_set_master", "fsi_trainer_get", "fsi_trainer_save", "fsi_trainer_free", "fsi_set_flags",
             "fsi_set_learned_accept", "fsi_update_values", "fsi_asm_create", "fsi_asm_residual",
-            "fsi_asm_jacobian", "fsi_asm_axpy", "fsi_asm_last_error", "fsi_asm_free"]
+            "fsi_asm_jacobian", "fsi_asm_axpy", "fsi_asm_last_error", "fsi_asm_free", "fsi_check_device_errors",
+            "fsi_debug_inject"]
+
+# fault-injection bits of fsi_debug_inject (tests of the bounded waits)
+FSI_INJECT_COARSE_BARRIER, FSI_INJECT_MLP_COMMIT = 1, 2
 
 
 class FSIError(RuntimeError):
@@ -158,6 +162,10 @@ def load_library(path: str = LIB_PATH):
     lib.fsi_trainer_loss.argtypes = [vp, vp, vp, f64p]
     lib.fsi_trainer_update.argtypes = [vp, vp, ctypes.c_double]
     lib.fsi_set_flags.argtypes = [vp, ctypes.c_int]
+    lib.fsi_check_device_errors.argtypes = [vp]
+    lib.fsi_check_device_errors.restype = ctypes.c_int
+    lib.fsi_debug_inject.argtypes = [vp, ctypes.c_int]
+    lib.fsi_debug_inject.restype = ctypes.c_int
     lib.fsi_set_learned_accept.argtypes = [vp, ctypes.c_double]
     lib.fsi_trainer_set_master.argtypes = [vp, f32p]
     lib.fsi_trainer_get.argtypes = [vp, f32p, u16p, f32p]
@@ -425,6 +433,15 @@ class FSISolver:
                                                    _dev_ptr(rho, nn, torch.float32)))
         if sync:
             self._sync()
+
+    def check_device_errors(self):
+        """Wait for the context's stream; raise FSIError (FSI_ECUDA) if a bounded wait in a
+        kernel gave up since the last check or solve."""
+        self._check(self._lib.fsi_check_device_errors(self._h))
+
+    def debug_inject(self, mask: int):
+        """Fault injection for tests of the bounded waits (FSI_INJECT_*; 0 = none)."""
+        self._check(self._lib.fsi_debug_inject(self._h, int(mask)))
 
     def set_harvest(self, buf=None, nvec=0):
         """Store r'_j = v_j - A P^-1 v_j of the first nvec iterations of later solves into buf [nvec, n]."""
