@@ -130,22 +130,21 @@ __device__ __forceinline__ void load_block(const T* __restrict__ v, int64_t nnzb
 
 // ------------------------------------------------------------------ gathers
 // x[c] segment of the vector the matrix multiplies.
-template <class T, int BC>
+// KEEP (FP64 only): gather with the L2 evict-last policy.  A template parameter, so
+// that kernels without it carry no code (and no registers) for it.
+template <class T, int BC, bool KEEP = false>
 struct GatherX {
+  static constexpr bool kKeep = KEEP;
   const T* x;
-  int keep = 0;   // FP64: gather with the L2 evict-last policy
   __device__ __forceinline__ void operator()(int c, T* out) const {
-    if constexpr (sizeof(T) == 8) {
-      if (keep) load_gather_keep<BC>(x + (size_t)c * BC, out);
-      else load_gather<T, BC>(x + (size_t)c * BC, out);
-    } else {
-      load_gather<T, BC>(x + (size_t)c * BC, out);
-    }
+    if constexpr (sizeof(T) == 8 && KEEP) load_gather_keep<BC>(x + (size_t)c * BC, out);
+    else load_gather<T, BC>(x + (size_t)c * BC, out);
   }
 };
 // (dinv * b * s)[c] segment: the first Chebyshev iterate from x = 0, formed on the fly.
 template <class T, int BC>
 struct GatherScaled {
+  static constexpr bool kKeep = false;
   const T* b; const T* dinv; T s;
   __device__ __forceinline__ void operator()(int c, T* out) const {
     T bv[BC], dv[BC];
@@ -334,19 +333,16 @@ __device__ __forceinline__ void row_accumulate(const CI* __restrict__ ci, int ba
 }
 
 // L2 prefetch of the 16-byte-aligned interior of [p, p + bytes) (one bulk
-// prefetch per 64 KB; the unaligned edges are left to the ordinary loads).  The
-// lines come in with the evict-first policy, like the streaming loads that read
-// them, so they do not push the gathered vector out of L2.
+// prefetch per 64 KB; the unaligned edges are left to the ordinary loads).  (An
+// evict-first policy on these prefetches changed no DRAM traffic and cost the 3 x 3
+// Chebyshev kernel 6 registers, one CTA per SM.)
 __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
   const uintptr_t a0 = ((uintptr_t)p + 15) & ~(uintptr_t)15;
   const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
-  uint64_t policy;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
   for (uintptr_t a = a0; a < e; a += 65536) {
     const uint32_t n = (uint32_t)(e - a < 65536 ? e - a : 65536);
-    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(a), "r"(n), "l"(policy)
-                 : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
   }
 #endif
 }
@@ -375,7 +371,6 @@ __device__ __forceinline__ void prefetch_blocks(const T* v, int64_t nnzb, int a,
 // (pre_wait != 0); during set-up the previous kernel may still be writing them.
 template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4, class CI1 = int>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per_cta, int prefetch, int pre_wait,
-    int keep_x2,
     const int* __restrict__ rp1, const CI1* __restrict__ ci1, const T* __restrict__ v1, int64_t nnzb1, G1 g1,
     const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, int64_t nnzb2,
     const T* __restrict__ x2,
@@ -412,7 +407,7 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
       row_accumulate<T, BR, BC1, UREQ, G1, CI1>(ci1, sizeof(CI1) == 4 ? 0 : row, v1, nnzb1, g1, rp1[row],
                                                 rp1[row + 1], lane, tpr, acc);
       if constexpr (BC2 > 0)
-        row_accumulate<T, BR, BC2, UREQ>(ci2, 0, v2, nnzb2, GatherX<T, BC2>{x2, keep_x2}, rp2[row], rp2[row + 1],
+        row_accumulate<T, BR, BC2, UREQ>(ci2, 0, v2, nnzb2, GatherX<T, BC2, G1::kKeep>{x2}, rp2[row], rp2[row + 1],
                                          lane, tpr, acc);
     }
     for (int off = tpr >> 1; off > 0; off >>= 1)
