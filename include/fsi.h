@@ -92,7 +92,7 @@ typedef struct fsi_params {
   double dt_theta;          /* c = dt*theta of the solid Schur complement S_hat = A_vv + c A_vu (0.01) */
   /* smoothed-aggregation AMG */
   double strength_theta;    /* strength threshold on node-block Frobenius norms (0.08) */
-  int coarse_max;           /* coarsen until <= this many scalar rows (500) */
+  int coarse_max;           /* coarsen until <= this many scalar rows (1500) */
   int max_levels;           /* (10) */
   int cheb_degree;          /* Chebyshev smoother degree (4) */
   double cheb_ratio;        /* smoothing interval [lambda/ratio, upper*lambda] (30) */

@@ -42,7 +42,7 @@ STATE_SHIFT = 59       # key = state << 59 | priority << 27 | index
 @dataclass
 class AMGParams:
     theta: float = 0.08
-    coarse_max: int = 500        # stop coarsening at <= this many scalar rows
+    coarse_max: int = 1500       # stop coarsening at <= this many scalar rows
     max_levels: int = 10
     cheb_degree: int = 4
     cheb_ratio: float = 30.0

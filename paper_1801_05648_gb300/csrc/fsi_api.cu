@@ -179,7 +179,7 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->flags = 0;
   p->dt_theta = 0.01;
   p->strength_theta = 0.08;
-  p->coarse_max = 500;
+  p->coarse_max = 1500;
   p->max_levels = 10;
   p->cheb_degree = 4;
   p->cheb_ratio = 30.0;

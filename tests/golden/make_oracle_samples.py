@@ -20,11 +20,14 @@ import fsigen  # noqa: E402
 import oracle  # noqa: E402
 
 N_SAMPLES = 4000
+# AMG coarse size of the stored solution (the parity test passes the same value)
+COARSE_MAX = 500
 
 
 def main(workload):
     s = fsigen.make_system(fsigen.CONFIGS[workload].with_(state_seed=0))
-    o = oracle.OracleSolver.from_system(s, params=oracle.PrecondParams(mass_ratio=8.0 if s.dim == 2 else 20.0))
+    o = oracle.OracleSolver.from_system(s, params=oracle.PrecondParams(
+        mass_ratio=8.0 if s.dim == 2 else 20.0, amg=oracle.AMGParams(coarse_max=COARSE_MAX)))
     r = o.solve(s.rhs, tol=1e-8)
     idx = np.sort(np.random.default_rng(1234).choice(s.n, N_SAMPLES, replace=False))
     path = os.path.join(HERE, f"oracle_{workload}_samples.txt")

@@ -61,6 +61,8 @@ def test_default_params(lib):
     assert (p2.restart, p2.maxit, p2.cheb_degree, p2.vcycles_solid, p2.mass_degree) == (100, 1000, 4, 2, 12)
     assert p2.mass_ratio == 8.0 and p3.mass_ratio == 20.0
     assert p2.strength_theta == 0.08 and p2.dt_theta == 0.01
+    import oracle
+    assert p2.coarse_max == oracle.AMGParams().coarse_max == 1500     # the oracle's default is the library's
     assert (p2.cheb_degree_coarse, p2.spmv_prefetch, p2.cluster_max_bytes) == (2, 1, 6.0e6)
     assert p2.fluid_gmres_iters == 4 and P.FSI_FLUID_GMRES == 128 and P.FSI_MLP_CUDA_CORES == 256
     assert p2.precond_variant == P.FSI_PRECOND_LDU == 0 and p2.spmv_lane_shift == 0 and p2.spmv_stage == 0

@@ -637,14 +637,15 @@ def _read_oracle_samples(workload):
 def test_2d_large_fp64_matches_sampled_oracle(torch_cuda):
     """The 8.9M-DOF Jacobian (1024x512): the FP64 GPU solve against the FP64 oracle's
     own full solve of it, stored at 4000 seeded indices with the solution's 2-norm by
-    tests/golden/make_oracle_samples.py (the oracle takes minutes at this size):
-    iteration count within +-1, sampled entries and the 2-norm within 1e-8."""
+    tests/golden/make_oracle_samples.py (the oracle takes minutes at this size; AMG
+    coarse size 500, passed here too): iteration count within +-1, sampled entries and
+    the 2-norm within 1e-8."""
     torch = torch_cuda
     import paper_1801_05648_gb300 as P
     head, idx, ref = _read_oracle_samples("2d_large")
     s = fsigen.make_system("2d_large")
     assert s.n == int(head["n"])
-    g = P.FSISolver.from_system(s, params=P.default_params(2, mass_ratio=8.0, flags=P.FSI_USE_GRAPHS))
+    g = P.FSISolver.from_system(s, params=P.default_params(2, mass_ratio=8.0, flags=P.FSI_USE_GRAPHS, coarse_max=500))
     g.precond_build("fp64")
     b = torch.tensor(s.rhs, device="cuda")
     x = torch.zeros_like(b)

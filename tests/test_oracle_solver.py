@@ -237,8 +237,10 @@ def test_fluid_inner_gmres_improves_the_velocity_solve(dim):
     # 16x16 in 2D: A_ff needs more than one AMG level, so the V-cycle is not exact
     s = fsigen.make_system(fsigen.CONFIGS["2d_tiny"]) if dim == 2 else tiny(3)
     mr = 8.0 if dim == 2 else 20.0
-    base = oracle.BlockLDU(s.scipy(), s.offsets, dim, params=oracle.PrecondParams(mass_ratio=mr))
-    g4 = oracle.BlockLDU(s.scipy(), s.offsets, dim, params=oracle.PrecondParams(mass_ratio=mr, fluid_gmres_iters=4))
+    amg = oracle.AMGParams(coarse_max=500)     # keeps A_ff multi-level on these small meshes
+    base = oracle.BlockLDU(s.scipy(), s.offsets, dim, params=oracle.PrecondParams(mass_ratio=mr, amg=amg))
+    g4 = oracle.BlockLDU(s.scipy(), s.offsets, dim,
+                         params=oracle.PrecondParams(mass_ratio=mr, fluid_gmres_iters=4, amg=amg))
     A_ff = base.B.A_ff
     r = np.random.default_rng(6).standard_normal(A_ff.shape[0])
     res = lambda x: np.linalg.norm(r - A_ff @ x)
@@ -246,7 +248,7 @@ def test_fluid_inner_gmres_improves_the_velocity_solve(dim):
     r0 = res(base.Aff_inv(r))
     assert r0 > 1e-6 * np.linalg.norm(r)
     assert res(g4.Aff_inv(r)) <= r0 * (1 + 1e-12)
-    o = oracle.OracleSolver.from_system(s, oracle.PrecondParams(mass_ratio=mr, fluid_gmres_iters=4))
+    o = oracle.OracleSolver.from_system(s, oracle.PrecondParams(mass_ratio=mr, fluid_gmres_iters=4, amg=amg))
     rr = o.solve(s.rhs, tol=1e-8)
     assert rr.converged and rr.true_relres <= 1e-8
 
