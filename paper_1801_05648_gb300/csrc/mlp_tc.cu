@@ -4,8 +4,8 @@
 // residuals scaled by the class scales and the patch RMS rho, then
 //   h1 = W1^T f + b1, h2 = W2^T gelu(h1) + b2, y = W3^T gelu(h2) + b3,
 //   c[dof_k(a)] = y_k rho sigma_out[class].
-// A CTA takes 128 nodes at a time, one per thread; its four warps own the four
-// 32-lane quarters of the tensor memory, so thread t's node is accumulator row t.
+// A CTA takes 128 nodes at a time, two threads per node; node row r of the tile is
+// accumulator row r, read by the warps that own its 32-lane quarter of tensor memory.
 // Each layer is a chain of tcgen05.mma.kind::tf32 (M = 128, N = 64 / 64 / 16,
 // K = 8 per instruction) from shared memory into tensor memory:
 //   layer 1  K = 56: the 53 inputs (45 patch values, the one-hot lattice parity,
@@ -32,7 +32,8 @@ namespace fsi {
 
 namespace {
 
-constexpr int kTcRows = 128;           // nodes per tile = MMA M = threads per CTA
+constexpr int kTcRows = 128;           // nodes per tile = MMA M
+constexpr int kTcThreads = 256;        // two threads per node (see k_mlp_tc)
 constexpr int kTcK1 = 56;              // layer-1 K: 53 inputs, the bias column, zero padding
 constexpr int kTcN3 = 16;              // layer-3 N (5 outputs, zero-padded)
 constexpr uint32_t kLbo = 128;         // bytes between core matrices along K
@@ -45,7 +46,8 @@ constexpr uint32_t kOffB2v = 102400;                     // b2 (64)
 constexpr uint32_t kOffB3v = kOffB2v + 64 * 4;           // b3 (16, padded)
 constexpr uint32_t kOffBar = kOffB3v + 16 * 4;           // mbarrier (8 bytes)
 constexpr uint32_t kOffTmem = kOffBar + 8;               // tensor-memory base written by tcgen05.alloc
-constexpr uint32_t kTcSmem = kOffTmem + 16;
+constexpr uint32_t kOffSs = kOffTmem + 8;                // partial sums of squares, 2 x 128 floats
+constexpr uint32_t kTcSmem = kOffSs + 2 * 128 * 4;
 
 __device__ __forceinline__ uint32_t core_off(int r, int k) {
   return (uint32_t)(r >> 3) * kSbo + (uint32_t)(k >> 2) * kLbo + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 3) * 4u;
@@ -143,13 +145,22 @@ __device__ __forceinline__ void issue_layer(uint32_t sbase, uint32_t boff, uint3
   if (commit) tc_commit(bar);
 }
 
-__global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* __restrict__ w16,
-                                                    const double* __restrict__ rp, double* __restrict__ c,
-                                                    int* __restrict__ err, int no_commit) {
+// 256 threads: thread t works on node row t & 127 of the tile; the two halves (t < 128
+// and t >= 128) split every per-node step.  Warp w reads tensor-memory lane quarter
+// w & 3 (warps w and w + 4 share it and take different columns).
+//   gather     half 0: patch slots 0-3 (columns 0-19); half 1: slots 4-8 (20-44), the
+//              one-hot, the flags and the bias column; rho from both halves' partial sums
+//   layers 1-2 half 0: hidden columns 0-31; half 1: 32-63
+//   layer 3    half 0: the outputs and the scatter
+__global__ void __launch_bounds__(kTcThreads, 2) k_mlp_tc(MlpGeom g, const uint16_t* __restrict__ w16,
+                                                          const double* __restrict__ rp, double* __restrict__ c,
+                                                          int* __restrict__ err, int no_commit) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int t = threadIdx.x, warp = t >> 5;
+  const int row = t & (kTcRows - 1), half = t >> 7;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
   const uint32_t bar = sbase + kOffBar;
+  float* ssbuf = reinterpret_cast<float*>(sm + kOffSs);   // [2][128] partial sums of squares
   // ---- weights (independent of earlier kernels): B operands N x K, K-major, zero-padded;
   // row 53 of the layer-1 operand is b1 (its input column is the constant 1)
   for (int i = t; i < 64 * 64; i += blockDim.x) {
@@ -178,24 +189,27 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* _
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + kOffTmem);
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lane quarter
+  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's lane quarter
+  const uint32_t hcol = 32u * (uint32_t)half;                         // this half's hidden columns
   const float* b2 = reinterpret_cast<const float*>(sm + kOffB2v);
   const float* b3 = reinterpret_cast<const float*>(sm + kOffB3v);
   dep_wait();
   uint32_t phase = 0;
   bool failed = false;
   const int64_t ntiles = (g.n_nodes + kTcRows - 1) / kTcRows;
+  // patch slots of this half, and where their values go in the layer-1 operand
+  const int s0 = half ? 4 : 0, ns = half ? kMlpSlots - 4 : 4;
   for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int64_t a = tile * kTcRows + t;
+    const int64_t a = tile * kTcRows + row;
     const bool valid = a < g.n_nodes;
-    // ---- gather and normalise (as k_mlp), write the layer-1 operand
+    // ---- gather this half's slots (as k_mlp), partial sum of squares
     int4 me = make_int4(0, 0, -1, 0);
-    float x[kMlpPatch];
+    float x[25];
     float ss = 0.f;
     if (valid) me = g.node_dof[a];
 #pragma unroll
-    for (int s = 0; s < kMlpSlots; ++s) {
-      const int q = valid ? g.patch[a * kMlpSlots + s] : -1;
+    for (int s = 0; s < 5; ++s) {
+      const int q = (valid && s < ns) ? g.patch[a * kMlpSlots + s0 + s] : -1;
       float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, e4 = 0.f;
       if (q >= 0) {
         const int4 r = g.node_dof[q];
@@ -210,40 +224,48 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* _
       x[5 * s + 0] = e0; x[5 * s + 1] = e1; x[5 * s + 2] = e2; x[5 * s + 3] = e3; x[5 * s + 4] = e4;
       ss += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3 + e4 * e4;
     }
-    const float rho = sqrtf(ss * (1.0f / kMlpPatch));
+    ssbuf[half * kTcRows + row] = ss;
+    __syncthreads();
+    const float rho = sqrtf((ssbuf[row] + ssbuf[kTcRows + row]) * (1.0f / kMlpPatch));
     const bool live = rho > 0.f;
     const float inv_rho = live ? 1.0f / rho : 0.f;
     const int fl = me.w;
-    const int par = ((fl >> 4) & 1) | (((fl >> 5) & 1) << 1);
-    // columns 45..55: one-hot parity, flags (bits 0..3), the bias input 1, zeros (all
-    // exact in TF32, so their low terms are 0); the hidden layers overwrite them
+    if (half == 0) {
 #pragma unroll
-    for (int k = 0; k < kMlpPatch - 1; k += 4)
-      put4(sm, t, k, x[k] * inv_rho, x[k + 1] * inv_rho, x[k + 2] * inv_rho, x[k + 3] * inv_rho);
-    const float oh[4] = {par == 0 ? 1.f : 0.f, par == 1 ? 1.f : 0.f, par == 2 ? 1.f : 0.f, par == 3 ? 1.f : 0.f};
-    const float fb[4] = {(float)(fl & 1), (float)((fl >> 1) & 1), (float)((fl >> 2) & 1), (float)((fl >> 3) & 1)};
-    put4(sm, t, 44, x[kMlpPatch - 1] * inv_rho, oh[0], oh[1], oh[2]);
-    put4(sm, t, 48, oh[3], fb[0], fb[1], fb[2]);
-    put4(sm, t, 52, fb[3], 1.f, 0.f, 0.f);
+      for (int k = 0; k < 20; k += 4)
+        put4(sm, row, k, x[k] * inv_rho, x[k + 1] * inv_rho, x[k + 2] * inv_rho, x[k + 3] * inv_rho);
+    } else {
+      // columns 20..44, then 45..55: one-hot parity, flags (bits 0..3), the bias input 1,
+      // zeros (all exact in TF32, so their low terms are 0); the hidden layers overwrite them
+#pragma unroll
+      for (int k = 0; k < 24; k += 4)
+        put4(sm, row, 20 + k, x[k] * inv_rho, x[k + 1] * inv_rho, x[k + 2] * inv_rho, x[k + 3] * inv_rho);
+      const int par = ((fl >> 4) & 1) | (((fl >> 5) & 1) << 1);
+      const float oh[4] = {par == 0 ? 1.f : 0.f, par == 1 ? 1.f : 0.f, par == 2 ? 1.f : 0.f, par == 3 ? 1.f : 0.f};
+      const float fb[4] = {(float)(fl & 1), (float)((fl >> 1) & 1), (float)((fl >> 2) & 1), (float)((fl >> 3) & 1)};
+      put4(sm, row, 44, x[24] * inv_rho, oh[0], oh[1], oh[2]);
+      put4(sm, row, 48, oh[3], fb[0], fb[1], fb[2]);
+      put4(sm, row, 52, fb[3], 1.f, 0.f, 0.f);
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (t == 0) issue_layer(sbase, kOffB1, tmem, 0, kTcK1 / 8, kMlpHidden, bar, !no_commit);
-    // ---- layer 1 epilogue: gelu -> layer-2 operand
+    // ---- layer 1 epilogue: gelu -> layer-2 operand (this half's 32 columns)
     bool ok = bar_wait(bar, phase);
     if (__syncthreads_or(!ok)) { failed = true; break; }
     phase ^= 1u;
     tc_fence_after();
 #pragma unroll 1
-    for (int q = 0; q < kMlpHidden / 16; ++q) {
+    for (int q = 0; q < 2; ++q) {
       float h[16];
-      tc_ld16(trow + 16u * q, h);
+      tc_ld16(trow + hcol + 16u * q, h);
       tc_wait_ld();
 #pragma unroll
       for (int i = 0; i < 16; ++i) h[i] = tc_gelu(h[i]);
 #pragma unroll
-      for (int i = 0; i < 16; i += 4) put4(sm, t, 16 * q + i, h[i], h[i + 1], h[i + 2], h[i + 3]);
+      for (int i = 0; i < 16; i += 4) put4(sm, row, hcol + 16 * q + i, h[i], h[i + 1], h[i + 2], h[i + 3]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -256,39 +278,41 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(MlpGeom g, const uint16_t* _
     phase ^= 1u;
     tc_fence_after();
 #pragma unroll 1
-    for (int q = 0; q < kMlpHidden / 16; ++q) {
+    for (int q = 0; q < 2; ++q) {
       float h[16];
-      tc_ld16(trow + 64u + 16u * q, h);
+      tc_ld16(trow + 64u + hcol + 16u * q, h);
       tc_wait_ld();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) h[i] = tc_gelu(h[i] + b2[16 * q + i]);
+      for (int i = 0; i < 16; ++i) h[i] = tc_gelu(h[i] + b2[hcol + 16 * q + i]);
 #pragma unroll
-      for (int i = 0; i < 16; i += 4) put4(sm, t, 16 * q + i, h[i], h[i + 1], h[i + 2], h[i + 3]);
+      for (int i = 0; i < 16; i += 4) put4(sm, row, hcol + 16 * q + i, h[i], h[i + 1], h[i + 2], h[i + 3]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (t == 0) issue_layer(sbase, kOffB3, tmem, 0, kMlpHidden / 8, kTcN3, bar);
-    // ---- layer 3 epilogue: outputs, scatter
+    // ---- layer 3 epilogue: outputs, scatter (half 0)
     ok = bar_wait(bar, phase);
     if (__syncthreads_or(!ok)) { failed = true; break; }
     phase ^= 1u;
     tc_fence_after();
-    float y[16];
-    tc_ld16(trow, y);
-    tc_wait_ld();
-    if (valid) {
-      const double rr = (double)rho;
-      const double sv = live && !(fl & NF_VFIX) ? rr * (double)pick(g.sig_out, cls_in(g, me.x)) : 0.0;
-      const double su = live && !(fl & NF_UFIX) ? rr * (double)pick(g.sig_out, cls_in(g, me.y)) : 0.0;
-      c[me.x] = sv != 0.0 ? (double)(y[0] + b3[0]) * sv : 0.0;
-      c[me.x + 1] = sv != 0.0 ? (double)(y[1] + b3[1]) * sv : 0.0;
-      c[me.y] = su != 0.0 ? (double)(y[2] + b3[2]) * su : 0.0;
-      c[me.y + 1] = su != 0.0 ? (double)(y[3] + b3[3]) * su : 0.0;
-      if (me.z >= 0) {
-        const double sp = live && !(fl & NF_PFIX) ? rr * (double)pick(g.sig_out, cls_in(g, me.z)) : 0.0;
-        c[me.z] = sp != 0.0 ? (double)(y[4] + b3[4]) * sp : 0.0;
+    if (half == 0) {
+      float y[16];
+      tc_ld16(trow, y);
+      tc_wait_ld();
+      if (valid) {
+        const double rr = (double)rho;
+        const double sv = live && !(fl & NF_VFIX) ? rr * (double)pick(g.sig_out, cls_in(g, me.x)) : 0.0;
+        const double su = live && !(fl & NF_UFIX) ? rr * (double)pick(g.sig_out, cls_in(g, me.y)) : 0.0;
+        c[me.x] = sv != 0.0 ? (double)(y[0] + b3[0]) * sv : 0.0;
+        c[me.x + 1] = sv != 0.0 ? (double)(y[1] + b3[1]) * sv : 0.0;
+        c[me.y] = su != 0.0 ? (double)(y[2] + b3[2]) * su : 0.0;
+        c[me.y + 1] = su != 0.0 ? (double)(y[3] + b3[3]) * su : 0.0;
+        if (me.z >= 0) {
+          const double sp = live && !(fl & NF_PFIX) ? rr * (double)pick(g.sig_out, cls_in(g, me.z)) : 0.0;
+          c[me.z] = sp != 0.0 ? (double)(y[4] + b3[4]) * sp : 0.0;
+        }
       }
     }
     tc_fence_before();
@@ -319,7 +343,7 @@ void mlp_apply_tc(const MlpGeom& g, const uint16_t* w16, const double* rp, doubl
   const int64_t tiles = (g.n_nodes + kTcRows - 1) / kTcRows;
   int64_t grid = (int64_t)device_sms() * 2;   // two 103-KB CTAs per SM
   if (grid > tiles) grid = tiles;
-  launch_k(k_mlp_tc, (int)grid, kTcRows, kTcSmem, s, g, w16, rp, c, err,
+  launch_k(k_mlp_tc, (int)grid, kTcThreads, kTcSmem, s, g, w16, rp, c, err,
            (fault_inject() & kInjectMlpCommit) ? 1 : 0);
 }
 
