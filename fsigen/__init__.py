@@ -250,16 +250,16 @@ class Problem:
         return R
 
     def node_map(self):
-        """2D only: (node_dof [n_q2, 4] int32, patch [n_q2, 9] int32).  node_dof
-        rows: first v DOF, first u DOF, p DOF or -1, flags (1 solid closure,
-        2 v fixed, 4 u fixed, 8 interface, 16 lattice i odd, 32 lattice j odd,
-        64 p row fixed); patch: the 3x3 lattice neighbourhood
-        of each Q2 node (-1 outside the mesh)."""
+        """(node_dof [n_q2, 4] int32, patch [n_q2, 3^dim] int32).  node_dof rows: first
+        v DOF, first u DOF, p DOF or -1, flags (1 solid closure, 2 v fixed, 4 u fixed,
+        8 interface, 16 lattice i odd, 32 lattice j odd, 64 p row fixed, 128 lattice k
+        odd); patch: the 3x3 (3x3x3) lattice neighbourhood of each Q2 node, direction 0
+        fastest (-1 outside the mesh).  Nodal (Q1) pressure only."""
         nd = np.empty((self.n_q2, 4), np.int32)
-        pt = np.empty((self.n_q2, 9), np.int32)
+        pt = np.empty((self.n_q2, 3 ** self.dim), np.int32)
         rc = _load().fsigen_node_map(self._h, _ptr(nd, ctypes.c_int32), _ptr(pt, ctypes.c_int32))
         if rc != 0:
-            raise ValueError("node_map: 2D problems only")
+            raise ValueError("node_map: nodal (Q1) pressure only")
         return nd, pt
 
     def cell_map(self):

@@ -1024,24 +1024,29 @@ int fsigen_residual(void* h, const double* U, const double* Uold, double* R, dou
 // for 3D problems.
 int fsigen_node_map(void* h, int32_t* node_dof, int32_t* patch) {
   Problem* p = static_cast<Problem*>(h);
-  if (p->dim != 2 || p->pdisc) return -1;   // the stage's patch layout assumes nodal Q1 pressure
-  const int nx = p->nq2[0], ny = p->nq2[1];
+  if (p->pdisc) return -1;   // the stage's patch layout assumes nodal Q1 pressure
+  const int D = p->dim;
+  const int nx = p->nq2[0], ny = p->nq2[1], nz = D == 3 ? p->nq2[2] : 1;
+  const int slots = D == 3 ? 27 : 9;
   for (int64_t a = 0; a < p->n_q2; ++a) {
-    const int i = (int)(a % nx), j = (int)(a / nx);
+    const int i = (int)(a % nx), j = (int)((a / nx) % ny), k = D == 3 ? (int)(a / ((int64_t)nx * ny)) : 0;
     node_dof[a * 4 + 0] = (int32_t)p->dof_v[a];
     node_dof[a * 4 + 1] = (int32_t)p->dof_u[a];
     int32_t pd = -1;
-    if (i % 2 == 0 && j % 2 == 0) pd = (int32_t)p->dof_p[(int64_t)(j / 2) * p->nq1[0] + i / 2];
+    if (i % 2 == 0 && j % 2 == 0 && k % 2 == 0)
+      pd = (int32_t)p->dof_p[((int64_t)(k / 2) * p->nq1[1] + j / 2) * p->nq1[0] + i / 2];
     node_dof[a * 4 + 2] = pd;
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     cells_of_q2(i, p->P.n[0], lo[0], hi[0]);
     cells_of_q2(j, p->P.n[1], lo[1], hi[1]);
+    if (D == 3) cells_of_q2(k, p->P.n[2], lo[2], hi[2]);
     bool fluid_cell = false;
-    for (int cj = lo[1]; cj <= hi[1]; ++cj)
-      for (int ci = lo[0]; ci <= hi[0]; ++ci) {
-        const int c[3] = {ci, cj, 0};
-        if (!p->cell_solid[cell_index(*p, c)]) fluid_cell = true;
-      }
+    for (int ck = lo[2]; ck <= hi[2]; ++ck)
+      for (int cj = lo[1]; cj <= hi[1]; ++cj)
+        for (int ci = lo[0]; ci <= hi[0]; ++ci) {
+          const int c[3] = {ci, cj, ck};
+          if (!p->cell_solid[cell_index(*p, c)]) fluid_cell = true;
+        }
     int32_t flags = 0;
     if (p->node_solid[a]) flags |= 1;
     if (p->node_vdir[a]) flags |= 2;
@@ -1050,13 +1055,16 @@ int fsigen_node_map(void* h, int32_t* node_dof, int32_t* patch) {
     flags |= (i % 2) << 4;
     flags |= (j % 2) << 5;
     if (pd >= 0 && p->row_fixed[pd]) flags |= 64;
+    flags |= (k % 2) << 7;
     node_dof[a * 4 + 3] = flags;
-    for (int dj = -1; dj <= 1; ++dj)
-      for (int di = -1; di <= 1; ++di) {
-        const int ii = i + di, jj = j + dj;
-        const int slot = (dj + 1) * 3 + (di + 1);
-        patch[a * 9 + slot] = (ii >= 0 && ii < nx && jj >= 0 && jj < ny) ? (int32_t)((int64_t)jj * nx + ii) : -1;
-      }
+    for (int dk = (D == 3 ? -1 : 0); dk <= (D == 3 ? 1 : 0); ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          const int ii = i + di, jj = j + dj, kk = k + dk;
+          const int slot = (D == 3 ? (dk + 1) * 9 : 0) + (dj + 1) * 3 + (di + 1);
+          const bool in = ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
+          patch[a * slots + slot] = in ? (int32_t)(((int64_t)kk * ny + jj) * nx + ii) : -1;
+        }
   }
   return 0;
 }

@@ -11,6 +11,10 @@ Per Q2 node a of a 2D mesh, with its 3x3 lattice patch N(a) (slot s = 3*(dj+1) +
   rho_a   = sqrt(sum of the 45 squares / 45)
   f_a     = [x / rho_a (45 values, slot-major), one-hot of the lattice parity
              (i odd) + 2 (j odd) (4), flags solid / v fixed / u fixed / interface (4)]
+
+In 3D the patch is the 3x3x3 neighbourhood (slot s = 9*(dk+1) + 3*(dj+1) + (di+1)),
+k runs over v_x, v_y, v_z, u_x, u_y, u_z, p (189 values), the parity one-hot has 8
+entries ((i odd) + 2 (j odd) + 4 (k odd)), so f_a has 201 inputs and y_a 7 outputs.
   y_a     = W3^T gelu(W2^T gelu(W1^T f_a + b1) + b2) + b3,   gelu(x) = x Phi(x)
   c[dof_k(a)] = y_{a,k} rho_a sigma_out[class(dof)]   (0 on fixed rows, at rho_a = 0
              and for p at a node without p)
@@ -41,14 +45,47 @@ import struct
 import numpy as np
 from scipy.special import erf
 
-N_IN, N_HIDDEN, N_OUT = 53, 64, 5
-N_PATCH = 45
-SHAPES = [("W1", (N_IN, N_HIDDEN)), ("b1", (N_HIDDEN,)), ("W2", (N_HIDDEN, N_HIDDEN)), ("b2", (N_HIDDEN,)),
-          ("W3", (N_HIDDEN, N_OUT)), ("b3", (N_OUT,))]
-N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+N_HIDDEN = 64
+
+
+def layout(dim: int):
+    """(n_in, n_out, n_patch, n_slots, n_comp, n_parity) of the stage in `dim` dimensions."""
+    comp, slots, par = 2 * dim + 1, 3 ** dim, 2 ** dim
+    return slots * comp + par + 4, comp, slots * comp, slots, comp, par
+
+
+def shapes(dim: int):
+    n_in, n_out = layout(dim)[:2]
+    return [("W1", (n_in, N_HIDDEN)), ("b1", (N_HIDDEN,)), ("W2", (N_HIDDEN, N_HIDDEN)), ("b2", (N_HIDDEN,)),
+            ("W3", (N_HIDDEN, n_out)), ("b3", (n_out,))]
+
+
+def n_params(dim: int) -> int:
+    return sum(int(np.prod(s)) for _, s in shapes(dim))
+
+
+N_IN, N_OUT, N_PATCH = layout(2)[:3]
+SHAPES = shapes(2)
+N_PARAMS = n_params(2)
+N_PARAMS_3D = n_params(3)
 MAGIC = b"FSIMLP01"
 
-FLAG_SOLID, FLAG_VFIX, FLAG_UFIX, FLAG_IFACE, FLAG_IODD, FLAG_JODD, FLAG_PFIX = 1, 2, 4, 8, 16, 32, 64
+FLAG_SOLID, FLAG_VFIX, FLAG_UFIX, FLAG_IFACE, FLAG_IODD, FLAG_JODD, FLAG_PFIX, FLAG_KODD = 1, 2, 4, 8, 16, 32, 64, 128
+
+
+def dim_of_params(params) -> int:
+    n = len(np.asarray(params).reshape(-1))
+    for d in (2, 3):
+        if n == n_params(d):
+            return d
+    raise ValueError("parameter count of neither the 2D nor the 3D stage")
+
+
+def dim_of_patch(patch) -> int:
+    w = np.asarray(patch).shape[1]
+    if w not in (9, 27):
+        raise ValueError("patch width must be 9 (2D) or 27 (3D)")
+    return 2 if w == 9 else 3
 
 
 # ------------------------------------------------------------------ bfloat16
@@ -68,7 +105,7 @@ def bf16_value(bits) -> np.ndarray:
 def unflatten(params) -> dict:
     p = np.asarray(params, np.float64)
     out, k = {}, 0
-    for name, shape in SHAPES:
+    for name, shape in shapes(dim_of_params(p)):
         size = int(np.prod(shape))
         out[name] = p[k:k + size].reshape(shape)
         k += size
@@ -76,7 +113,7 @@ def unflatten(params) -> dict:
 
 
 def flatten(d: dict) -> np.ndarray:
-    return np.concatenate([np.asarray(d[name], np.float64).reshape(-1) for name, _ in SHAPES])
+    return np.concatenate([np.asarray(d[name], np.float64).reshape(-1) for name, _ in SHAPES])   # order only
 
 
 # ------------------------------------------------------------------ weights file
@@ -89,10 +126,11 @@ def read_weights(path: str):
     if raw[:8] != MAGIC:
         raise ValueError("not an MLP weights file")
     n_in, n_h, n_out, _ = struct.unpack_from("<4i", raw, 8)
-    if (n_in, n_h, n_out) != (N_IN, N_HIDDEN, N_OUT):
+    dims = {layout(d)[:2]: d for d in (2, 3)}
+    if n_h != N_HIDDEN or (n_in, n_out) not in dims:
         raise ValueError("unexpected MLP shape")
     scales = np.frombuffer(raw, "<f4", 10, 24).astype(np.float64)
-    bits = np.frombuffer(raw, "<u2", N_PARAMS, 64)
+    bits = np.frombuffer(raw, "<u2", n_params(dims[(n_in, n_out)]), 64)
     return bits.copy(), scales[:5].copy(), scales[5:].copy()
 
 
@@ -102,45 +140,51 @@ def dof_class(dofs, offsets) -> np.ndarray:
     return np.searchsorted(np.asarray(offsets[1:5]), np.asarray(dofs), side="right")
 
 
-def node_dofs(node_dof) -> np.ndarray:
-    """[n_nodes, 5] DOF of (v_x, v_y, u_x, u_y, p) at each node, -1 where absent."""
+def node_dofs(node_dof, dim: int = 2) -> np.ndarray:
+    """[n_nodes, 2 dim + 1] DOF of (v components, u components, p) at each node, -1 where absent."""
     nd = np.asarray(node_dof)
-    return np.stack([nd[:, 0], nd[:, 0] + 1, nd[:, 1], nd[:, 1] + 1, nd[:, 2]], axis=1)
+    cols = [nd[:, 0] + i for i in range(dim)] + [nd[:, 1] + i for i in range(dim)] + [nd[:, 2]]
+    return np.stack(cols, axis=1)
 
 
 def features(rp, node_dof, patch, offsets, sigma_in):
-    """(F [n_nodes, 53], rho [n_nodes]) for residual r' (the definition above)."""
+    """(F [n_nodes, n_in], rho [n_nodes]) for residual r' (the definition above); the
+    dimension follows from the patch width."""
+    dim = dim_of_patch(patch)
+    n_in, _, n_patch, n_slots, n_comp, n_par = layout(dim)
     rp = np.asarray(rp, np.float64)
     sig = np.asarray(sigma_in, np.float64)
-    D = node_dofs(node_dof)                                 # [n_nodes, 5]
+    D = node_dofs(node_dof, dim)                            # [n_nodes, n_comp]
     scaled = np.zeros(D.shape)
     ok = D >= 0
     scaled[ok] = rp[D[ok]] / sig[dof_class(D[ok], offsets)]
     pt = np.asarray(patch)
-    X = np.zeros((pt.shape[0], 9, 5))
+    X = np.zeros((pt.shape[0], n_slots, n_comp))
     has = pt >= 0
     X[has] = scaled[pt[has]]
-    X = X.reshape(-1, N_PATCH)
-    rho = np.sqrt(np.sum(X * X, axis=1) / N_PATCH)
-    F = np.zeros((X.shape[0], N_IN))
+    X = X.reshape(-1, n_patch)
+    rho = np.sqrt(np.sum(X * X, axis=1) / n_patch)
+    F = np.zeros((X.shape[0], n_in))
     nz = rho > 0
-    F[nz, :N_PATCH] = X[nz] / rho[nz, None]
+    F[nz, :n_patch] = X[nz] / rho[nz, None]
     fl = np.asarray(node_dof)[:, 3]
     par = ((fl & FLAG_IODD) != 0).astype(int) + 2 * ((fl & FLAG_JODD) != 0).astype(int)
-    F[np.arange(len(par)), N_PATCH + par] = 1.0
+    if dim == 3:
+        par = par + 4 * ((fl & FLAG_KODD) != 0).astype(int)
+    F[np.arange(len(par)), n_patch + par] = 1.0
     for k, bit in enumerate((FLAG_SOLID, FLAG_VFIX, FLAG_UFIX, FLAG_IFACE)):
-        F[:, N_PATCH + 4 + k] = ((fl & bit) != 0).astype(np.float64)
+        F[:, n_patch + n_par + k] = ((fl & bit) != 0).astype(np.float64)
     return F, rho
 
 
-def output_mask(node_dof) -> np.ndarray:
-    """[n_nodes, 5]: 1 where the node's output k is a free DOF."""
+def output_mask(node_dof, dim: int = 2) -> np.ndarray:
+    """[n_nodes, 2 dim + 1]: 1 where the node's output k is a free DOF."""
     nd = np.asarray(node_dof)
     fl = nd[:, 3]
-    M = np.ones((nd.shape[0], N_OUT))
-    M[(fl & FLAG_VFIX) != 0, 0:2] = 0.0
-    M[(fl & FLAG_UFIX) != 0, 2:4] = 0.0
-    M[(nd[:, 2] < 0) | ((fl & FLAG_PFIX) != 0), 4] = 0.0
+    M = np.ones((nd.shape[0], 2 * dim + 1))
+    M[(fl & FLAG_VFIX) != 0, 0:dim] = 0.0
+    M[(fl & FLAG_UFIX) != 0, dim:2 * dim] = 0.0
+    M[(nd[:, 2] < 0) | ((fl & FLAG_PFIX) != 0), 2 * dim] = 0.0
     return M
 
 
@@ -167,10 +211,11 @@ def mlp_forward(params, F, keep=False):
 
 def correction(rp, node_dof, patch, offsets, bits, sigma_in, sigma_out):
     """c = MLP(r') scattered to the monolithic vector (the definition above)."""
+    dim = dim_of_patch(patch)
     F, rho = features(rp, node_dof, patch, offsets, sigma_in)
     y = mlp_forward(bf16_value(bits), F)
-    D = node_dofs(node_dof)
-    M = output_mask(node_dof) * (rho > 0)[:, None]
+    D = node_dofs(node_dof, dim)
+    M = output_mask(node_dof, dim) * (rho > 0)[:, None]
     c = np.zeros(np.asarray(rp).shape[0])
     ok = (M > 0) & (D >= 0)
     sig = np.asarray(sigma_out, np.float64)
@@ -179,11 +224,11 @@ def correction(rp, node_dof, patch, offsets, bits, sigma_in, sigma_out):
     return c
 
 
-def targets(e, node_dof, offsets, rho, sigma_out):
+def targets(e, node_dof, offsets, rho, sigma_out, dim: int = 2):
     """(Y, M): y*_{a,k} = e[dof_k(a)] / (rho_a sigma_out[class]) and its mask."""
     e = np.asarray(e, np.float64)
-    D = node_dofs(node_dof)
-    M = output_mask(node_dof) * (np.asarray(rho) > 0)[:, None]
+    D = node_dofs(node_dof, dim)
+    M = output_mask(node_dof, dim) * (np.asarray(rho) > 0)[:, None]
     Y = np.zeros(D.shape)
     ok = (M > 0) & (D >= 0)
     sig = np.asarray(sigma_out, np.float64)
@@ -194,7 +239,7 @@ def targets(e, node_dof, offsets, rho, sigma_out):
 
 # ------------------------------------------------------------------ training
 def mlp_backward(params, cache, dy) -> np.ndarray:
-    """dL/dparams of the forward pass in `cache` for output gradients dy [n_nodes, 5]."""
+    """dL/dparams of the forward pass in `cache` for output gradients dy [n_nodes, n_out]."""
     P = unflatten(params)
     X, h1, a1, h2, a2 = cache
     g = {"W3": a2.T @ dy, "b3": dy.sum(0)}
@@ -213,10 +258,11 @@ def residual_loss_and_grad(params, rp, A, node_dof, patch, offsets, sigma_in, si
     dL/dy_{a,k} = dL/dc[dof_k(a)] rho_a sigma_out[class] on free outputs, then
     backpropagation through the layers."""
     rp = np.asarray(rp, np.float64)
+    dim = dim_of_patch(patch)
     F, rho = features(rp, node_dof, patch, offsets, sigma_in)
     y, cache = mlp_forward(params, F, keep=True)
-    D = node_dofs(node_dof)
-    M = output_mask(node_dof) * (rho > 0)[:, None]
+    D = node_dofs(node_dof, dim)
+    M = output_mask(node_dof, dim) * (rho > 0)[:, None]
     ok = (M > 0) & (D >= 0)
     sig = np.asarray(sigma_out, np.float64)
     scale = np.zeros(D.shape)
