@@ -382,7 +382,7 @@ const char* fsi_asm_last_error(const fsi_asm* a);
 void fsi_asm_free(fsi_asm* a);
 
 /* ------------------------------------------------------------------------
- * Learned correction stage (2D meshes).  The paper has no such stage: it is an
+ * Learned correction stage (2D and 3D meshes).  The paper has no such stage: it is an
  * extra smoothing step after Alg. 2 inside each FGMRES iteration.  With
  * z_j = P^-1 v_j and q = A z_j:
  *     r' = v_j - q,  c = MLP(r'),  t = A c;
@@ -392,43 +392,51 @@ void fsi_asm_free(fsi_asm* a);
  * so the stage changes the search space of FGMRES but never its answer.  One
  * more FP64 outer SpMV and one MLP pass per iteration.
  *
- * MLP (per Q2 node a, 3x3 lattice patch N(a), slots s = 3 (dj+1) + (di+1)):
- *   x_{s,k} = r'[dof_k(N_s(a))] / sigma_in[class]   k = v_x v_y u_x u_y p
+ * MLP (per Q2 node a of a D-dimensional mesh, 3^D lattice patch N(a), slots
+ * s = 3 (dj+1) + (di+1) in 2D, 9 (dk+1) + 3 (dj+1) + (di+1) in 3D; C = 2D+1
+ * components k = v_x v_y [v_z] u_x u_y [u_z] p per node):
+ *   x_{s,k} = r'[dof_k(N_s(a))] / sigma_in[class]
  *             (0 outside the mesh and for p at a node that carries no p)
- *   rho_a   = sqrt(sum of the 45 squares / 45)
- *   f_a     = [x / rho_a (45), one-hot of (i odd) + 2 (j odd) (4),
- *              flags solid, v fixed, u fixed, interface (4)]              53 inputs
- *   y_a     = W3^T gelu(W2^T gelu(W1^T f_a + b1) + b2) + b3                64, 64, 5
+ *   rho_a   = sqrt(sum of the 3^D C squares / (3^D C))       (45 in 2D, 189 in 3D)
+ *   f_a     = [x / rho_a, one-hot of (i odd) + 2 (j odd) [+ 4 (k odd)] (2^D),
+ *              flags solid, v fixed, u fixed, interface (4)]   53 inputs in 2D, 201 in 3D
+ *   y_a     = W3^T gelu(W2^T gelu(W1^T f_a + b1) + b2) + b3     64, 64, C
  *   c[dof_k(a)] = y_{a,k} rho_a sigma_out[class]  (0 on fixed rows, at rho_a = 0)
  * Classes are m, s_v, s_u, f_v, f_p (0..4).  Weights bfloat16 (round to nearest
- * even), arithmetic FP32, c written in FP64.  The parameter vector (7,941
- * values) is W1 [53][64], b1 [64], W2 [64][64], b2 [64], W3 [64][5], b3 [5],
- * row-major, W_l mapping its layer's input (rows) to output (columns).
- * Weights file: 8 bytes "FSIMLP01", int32 {53, 64, 5, 0}, float32 sigma_in[5],
- * sigma_out[5], then the 7,941 bfloat16 parameters, little endian.
+ * even), arithmetic FP32, c written in FP64.  The parameter vector (7,941 values
+ * in 2D, 17,543 in 3D) is W1 [in][64], b1 [64], W2 [64][64], b2 [64], W3 [64][C],
+ * b3 [C], row-major, W_l mapping its layer's input (rows) to output (columns).
+ * Weights file: 8 bytes "FSIMLP01", int32 {in, 64, C, 0}, float32 sigma_in[5],
+ * sigma_out[5], then the bfloat16 parameters, little endian.  A context takes
+ * only the file of its mesh's dimension.  The tensor-core evaluation
+ * (default) is 2D; 3D meshes use the CUDA-core kernel.
  */
 #define FSI_MLP_PARAMS 7941
 #define FSI_MLP_INPUTS 53
+#define FSI_MLP_PARAMS_3D 17543
+#define FSI_MLP_INPUTS_3D 201
 
 /*
  * fsi_learned_setup - the node map of the context's mesh (host arrays, copied):
  *   n_nodes    Q2 nodes
- *   node_dof   n_nodes x 4 int32: first v DOF (v_y follows), first u DOF (u_y
- *              follows), p DOF or -1, flags (1 solid closure, 2 v fixed, 4 u
- *              fixed, 8 interface, 16 lattice i odd, 32 lattice j odd, 64 p row
- *              fixed)
- *   patch      n_nodes x 9 int32: the 3x3 lattice neighbourhood (row-major, i
- *              fastest), -1 outside the mesh
+ *   node_dof   n_nodes x 4 int32: first v DOF (the other D-1 components
+ *              follow), first u DOF (likewise), p DOF or -1, flags (1 solid
+ *              closure, 2 v fixed, 4 u fixed, 8 interface, 16 lattice i odd,
+ *              32 lattice j odd, 64 p row fixed, 128 lattice k odd)
+ *   patch      n_nodes x 3^D int32: the lattice neighbourhood (slots as above,
+ *              i fastest), -1 outside the mesh
  * Every DOF must belong to exactly one node (FSI_EINVAL otherwise).
  */
 int fsi_learned_setup(fsi_ctx* ctx, int64_t n_nodes, const int32_t* node_dof, const int32_t* patch);
 /* Load the stage's weights from a file (format above). */
 int fsi_learned_load(fsi_ctx* ctx, const char* path);
-/* Set the stage's weights from host memory: sigma_in[5], sigma_out[5] (> 0), params[FSI_MLP_PARAMS] bfloat16. */
+/* Set the stage's weights from host memory: sigma_in[5], sigma_out[5] (> 0), params bfloat16
+ * (FSI_MLP_PARAMS of them on a 2D mesh, FSI_MLP_PARAMS_3D on a 3D one). */
 int fsi_learned_set_weights(fsi_ctx* ctx, const float* sigma_in, const float* sigma_out, const uint16_t* params);
 /* c = MLP(r') (device, n doubles each; every entry of c written).  Enqueued without waiting. */
 int fsi_learned_apply(fsi_ctx* ctx, const double* r_dev, double* c_dev);
-/* Features f_a (device, n_nodes x 53 floats, node-major) and rho_a (n_nodes floats) of r'.  Enqueued. */
+/* Features f_a (device, n_nodes x FSI_MLP_INPUTS[_3D] floats, node-major) and rho_a (n_nodes
+ * floats) of r'.  Enqueued. */
 int fsi_learned_features(fsi_ctx* ctx, const double* r_dev, float* feat_dev, float* rho_dev);
 /* Change fsi_params.learned_accept (in (0, 1]) of a context. */
 int fsi_set_learned_accept(fsi_ctx* ctx, double tau);
@@ -484,6 +492,9 @@ typedef struct fsi_train_params {
   uint64_t seed;
   double init_out_scale;                        /* (0.01) */
   float sigma_in[5], sigma_out[5];              /* class scales, > 0 */
+  int dim;                                      /* mesh dimension trained on, 2 or 3 (2); fixes
+                                                   the parameter count; fsi_trainer_step refuses
+                                                   a context of the other dimension */
 } fsi_train_params;
 typedef struct fsi_trainer fsi_trainer;
 
@@ -497,7 +508,8 @@ int fsi_trainer_loss(fsi_trainer* tr, fsi_ctx* ctx, const double* rprime_dev, do
 /* One AdamW step with the mean of the gradients added since the last update, at
  * learning rate lr (lr <= 0: the fsi_train_params rate), on ctx's stream; waits. */
 int fsi_trainer_update(fsi_trainer* tr, fsi_ctx* ctx, double lr);
-/* Replace the master weights (host, FSI_MLP_PARAMS floats); resets the AdamW moments and gradients. */
+/* Replace the master weights (host, FSI_MLP_PARAMS[_3D] floats by the trainer's dim); resets the
+ * AdamW moments and gradients. */
 int fsi_trainer_set_master(fsi_trainer* tr, const float* params);
 /* Copy out (host, nullable each): master weights (floats), bfloat16 weights, accumulated gradient (floats). */
 int fsi_trainer_get(fsi_trainer* tr, float* master, uint16_t* params_bf16, float* grad);

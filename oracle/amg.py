@@ -186,6 +186,8 @@ def point_dinv(A: sp.csr_matrix) -> np.ndarray:
 def power_lambda(A: sp.csr_matrix, dinv: np.ndarray, iters: int, level: int) -> float:
     """|lambda_max(D^-1 A)| estimate: power iteration from x_i = 1 + u_i (SplitMix64
     stream 256 + level)."""
+    if A.shape[0] == 0:
+        return 0.0            # an empty operator (a block with no DOFs) has no spectrum
     x = 1.0 + unit_uniform(A.shape[0], 256 + level)
     lam = 0.0
     for _ in range(iters):

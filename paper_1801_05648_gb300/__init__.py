@@ -9,7 +9,8 @@ from .fsi import (FSISolver, FSIAssembler, FSIError, Params, SolveStats, Trainer
                   default_train_params, load_library, BLOCKS, EXPORTED, FSI_FP64, FSI_FP32_AMG, FSI_X0_GIVEN,
                   FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_LEARNED, FSI_NO_PDL, FSI_GRID_COARSE,
                   FSI_FLUID_GMRES, FSI_MLP_CUDA_CORES, FSI_PRECOND_LDU, FSI_PRECOND_LOWER, FSI_PRECOND_UPPER,
-                  FSI_PRECOND_DIAG, FSI_MLP_PARAMS, LIB_PATH, probe_fma_rate, FSI_OK, FSI_EINVAL, FSI_ENOMEM,
+                  FSI_PRECOND_DIAG, FSI_MLP_PARAMS, FSI_MLP_PARAMS_3D, mlp_params, mlp_inputs, LIB_PATH,
+                  probe_fma_rate, FSI_OK, FSI_EINVAL, FSI_ENOMEM,
                   FSI_ECUDA, FSI_ENOTCONV, FSI_EBREAKDOWN, FSI_ENONFINITE, FSI_INJECT_COARSE_BARRIER,
                   FSI_INJECT_MLP_COMMIT)
 
@@ -17,6 +18,7 @@ __all__ = ["FSISolver", "FSIAssembler", "FSIError", "Params", "SolveStats", "Tra
            "default_train_params", "load_library", "BLOCKS", "EXPORTED", "FSI_FP64", "FSI_FP32_AMG", "FSI_X0_GIVEN",
            "FSI_USE_GRAPHS", "FSI_NO_RIGID_MODES", "FSI_CLUSTER_COARSE", "FSI_LEARNED", "FSI_NO_PDL",
            "FSI_GRID_COARSE", "FSI_FLUID_GMRES", "FSI_MLP_CUDA_CORES", "FSI_PRECOND_LDU", "FSI_PRECOND_LOWER",
-           "FSI_PRECOND_UPPER", "FSI_PRECOND_DIAG", "FSI_MLP_PARAMS", "LIB_PATH", "probe_fma_rate", "FSI_OK",
+           "FSI_PRECOND_UPPER", "FSI_PRECOND_DIAG", "FSI_MLP_PARAMS", "FSI_MLP_PARAMS_3D", "mlp_params",
+           "mlp_inputs", "LIB_PATH", "probe_fma_rate", "FSI_OK",
            "FSI_EINVAL", "FSI_ENOMEM", "FSI_ECUDA", "FSI_ENOTCONV", "FSI_EBREAKDOWN", "FSI_ENONFINITE",
            "FSI_INJECT_COARSE_BARRIER", "FSI_INJECT_MLP_COMMIT"]

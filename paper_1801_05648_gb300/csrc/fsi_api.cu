@@ -222,6 +222,7 @@ int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const in
     to_solver_params(p ? *p : def, ctx->C.prm);
     validate_params(ctx->C.prm);
     ctx->C.dim = dim;
+    ctx->C.learned.dim = dim;
     ctx->C.n = n;
     for (int k = 0; k < 6; ++k) ctx->C.off[k] = block_offsets[k];
     if (cuda_stream) {
@@ -397,7 +398,6 @@ int fsi_amg_export(fsi_ctx* ctx, int which, int level, int what, void* dst) {
 int fsi_learned_setup(fsi_ctx* ctx, int64_t n_nodes, const int32_t* node_dof, const int32_t* patch) {
   if (!ctx) return FSI_EINVAL;
   return guarded(ctx, [&] {
-    fsi::require(ctx->C.dim == 2, "the learned stage is defined for 2D meshes");
     drop_graph(ctx->C);
     fsi::learned_set_geometry(ctx->C.learned, ctx->C.n, n_nodes, node_dof, patch, ctx->C.s);
   });
@@ -521,6 +521,7 @@ void fsi_default_train_params(fsi_train_params* p) {
   p->weight_decay = 0.0;
   p->seed = 0;
   p->init_out_scale = 0.01;
+  p->dim = 2;
   for (int k = 0; k < 5; ++k) p->sigma_in[k] = p->sigma_out[k] = 1.0f;
 }
 
@@ -540,6 +541,7 @@ int fsi_trainer_create(fsi_trainer** out, const fsi_train_params* p) {
     fsi::TrainParams tp;
     tp.lr = q.lr; tp.beta1 = q.beta1; tp.beta2 = q.beta2; tp.eps = q.eps; tp.weight_decay = q.weight_decay;
     tp.seed = q.seed;
+    tp.dim = q.dim;
     tp.init_out_scale = q.init_out_scale;
     for (int k = 0; k < 5; ++k) { tp.sig_in[k] = q.sigma_in[k]; tp.sig_out[k] = q.sigma_out[k]; }
     fsi::trainer_init(tr->T, tp);
@@ -584,20 +586,20 @@ int fsi_trainer_get(fsi_trainer* tr, float* master, uint16_t* params_bf16, float
   if (!tr) return FSI_EINVAL;
   return guarded(nullptr, [&] {
     FSI_CUDA(cudaDeviceSynchronize());
-    if (master) FSI_CUDA(cudaMemcpy(master, tr->T.master.p, sizeof(float) * fsi::kMlpParams, cudaMemcpyDeviceToHost));
-    if (params_bf16)
-      FSI_CUDA(cudaMemcpy(params_bf16, tr->T.w16.p, sizeof(uint16_t) * fsi::kMlpParams, cudaMemcpyDeviceToHost));
-    if (grad) FSI_CUDA(cudaMemcpy(grad, tr->T.grad.p, sizeof(float) * fsi::kMlpParams, cudaMemcpyDeviceToHost));
+    const size_t np = (size_t)tr->T.n_params();
+    if (master) FSI_CUDA(cudaMemcpy(master, tr->T.master.p, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    if (params_bf16) FSI_CUDA(cudaMemcpy(params_bf16, tr->T.w16.p, sizeof(uint16_t) * np, cudaMemcpyDeviceToHost));
+    if (grad) FSI_CUDA(cudaMemcpy(grad, tr->T.grad.p, sizeof(float) * np, cudaMemcpyDeviceToHost));
   });
 }
 
 int fsi_trainer_save(fsi_trainer* tr, const char* path) {
   if (!tr || !path) return FSI_EINVAL;
   return guarded(nullptr, [&] {
-    std::vector<uint16_t> h(fsi::kMlpParams);
+    std::vector<uint16_t> h((size_t)tr->T.n_params());
     FSI_CUDA(cudaDeviceSynchronize());
-    FSI_CUDA(cudaMemcpy(h.data(), tr->T.w16.p, sizeof(uint16_t) * fsi::kMlpParams, cudaMemcpyDeviceToHost));
-    fsi::learned_save_file(path, tr->T.prm.sig_in, tr->T.prm.sig_out, h.data());
+    FSI_CUDA(cudaMemcpy(h.data(), tr->T.w16.p, sizeof(uint16_t) * h.size(), cudaMemcpyDeviceToHost));
+    fsi::learned_save_file(path, tr->T.prm.dim, tr->T.prm.sig_in, tr->T.prm.sig_out, h.data());
   });
 }
 

@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_mlp_tc(MlpGeom g, const uint1
 }  // namespace
 
 void mlp_apply_tc(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, int* err, cudaStream_t s) {
+  require(g.dim == 2, "the tensor-core MLP takes the 2D layout (3x3 patch, 53 inputs)");
   static thread_local bool attr = false;
   if (!attr) {
     FSI_CUDA(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));

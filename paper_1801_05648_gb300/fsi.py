@@ -21,6 +21,17 @@ FSI_X0_GIVEN, FSI_USE_GRAPHS, FSI_NO_RIGID_MODES, FSI_CLUSTER_COARSE, FSI_LEARNE
 FSI_GRID_COARSE, FSI_FLUID_GMRES, FSI_MLP_CUDA_CORES = 64, 128, 256
 FSI_PRECOND_LDU, FSI_PRECOND_LOWER, FSI_PRECOND_UPPER, FSI_PRECOND_DIAG = 0, 1, 2, 3
 FSI_MLP_PARAMS, FSI_MLP_INPUTS = 7941, 53
+FSI_MLP_PARAMS_3D, FSI_MLP_INPUTS_3D = 17543, 201
+
+
+def mlp_params(dim: int) -> int:
+    """Parameter count of the learned stage's MLP on a mesh of dimension dim."""
+    return FSI_MLP_PARAMS_3D if dim == 3 else FSI_MLP_PARAMS
+
+
+def mlp_inputs(dim: int) -> int:
+    """Input width of the learned stage's MLP on a mesh of dimension dim."""
+    return FSI_MLP_INPUTS_3D if dim == 3 else FSI_MLP_INPUTS
 STATUS_NAMES = {0: "FSI_OK", -1: "FSI_EINVAL", -2: "FSI_ENOMEM", -3: "FSI_ECUDA", -4: "FSI_ENOTCONV",
                 -5: "FSI_EBREAKDOWN", -6: "FSI_ENONFINITE"}
 BLOCKS = {"mesh": 0, "solid_schur": 1, "fluid_velocity": 2, "pressure_schur": 3, "solid_mass": 4,
@@ -90,7 +101,7 @@ class TrainParams(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double), ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("init_out_scale", ctypes.c_double), ("sigma_in", ctypes.c_float * 5),
-                ("sigma_out", ctypes.c_float * 5)]
+                ("sigma_out", ctypes.c_float * 5), ("dim", ctypes.c_int)]
 
 
 @dataclass
@@ -389,11 +400,12 @@ class FSISolver:
 
     # ------------------------------------------------------------ learned stage
     def learned_setup(self, node_dof, patch):
-        """Node map (host int32 arrays [n_nodes, 4] and [n_nodes, 9]) for the learned stage."""
+        """Node map (host int32 arrays [n_nodes, 4] and [n_nodes, 3^dim]) for the learned stage."""
         nd = np.ascontiguousarray(node_dof, np.int32)
         pt = np.ascontiguousarray(patch, np.int32)
-        if nd.ndim != 2 or nd.shape[1] != 4 or pt.shape != (nd.shape[0], 9):
-            raise ValueError("node_dof must be [n_nodes, 4] and patch [n_nodes, 9]")
+        slots = 3 ** self.dim
+        if nd.ndim != 2 or nd.shape[1] != 4 or pt.shape != (nd.shape[0], slots):
+            raise ValueError(f"node_dof must be [n_nodes, 4] and patch [n_nodes, {slots}]")
         self._check(self._lib.fsi_learned_setup(self._h, nd.shape[0], _np_ptr(nd, ctypes.c_int32),
                                                 _np_ptr(pt, ctypes.c_int32)))
         self.n_nodes = int(nd.shape[0])
@@ -405,8 +417,8 @@ class FSISolver:
         si = np.ascontiguousarray(sigma_in, np.float32)
         so = np.ascontiguousarray(sigma_out, np.float32)
         pb = np.ascontiguousarray(params_bf16, np.uint16)
-        if si.shape != (5,) or so.shape != (5,) or pb.shape != (FSI_MLP_PARAMS,):
-            raise ValueError("sigma_in/sigma_out need 5 values and params FSI_MLP_PARAMS bfloat16 words")
+        if si.shape != (5,) or so.shape != (5,) or pb.shape != (mlp_params(self.dim),):
+            raise ValueError(f"sigma_in/sigma_out need 5 values and params {mlp_params(self.dim)} bfloat16 words")
         self._check(self._lib.fsi_learned_set_weights(self._h, _np_ptr(si, ctypes.c_float),
                                                       _np_ptr(so, ctypes.c_float), _np_ptr(pb, ctypes.c_uint16)))
 
@@ -420,16 +432,17 @@ class FSISolver:
             self._sync()
 
     def learned_features(self, r, feat, rho, sync=True):
-        """Features [n_nodes, 53] and rho [n_nodes] (float32 device tensors) of r'."""
+        """Features [n_nodes, 53 (2D) or 201 (3D)] and rho [n_nodes] (float32 device tensors) of r'."""
         import torch
         nn = getattr(self, "n_nodes", None)
         if nn is None:
             raise RuntimeError("learned_setup first")
-        if r.numel() != self.n or feat.numel() < nn * FSI_MLP_INPUTS or rho.numel() < nn:
-            raise ValueError("r needs n entries, feat n_nodes x 53 and rho n_nodes")
+        ni = mlp_inputs(self.dim)
+        if r.numel() != self.n or feat.numel() < nn * ni or rho.numel() < nn:
+            raise ValueError(f"r needs n entries, feat n_nodes x {ni} and rho n_nodes")
         self._order()
         self._check(self._lib.fsi_learned_features(self._h, _dev_ptr(r, self.n),
-                                                   _dev_ptr(feat, nn * FSI_MLP_INPUTS, torch.float32),
+                                                   _dev_ptr(feat, nn * ni, torch.float32),
                                                    _dev_ptr(rho, nn, torch.float32)))
         if sync:
             self._sync()
@@ -604,6 +617,7 @@ class Trainer:
         rc = lib.fsi_trainer_create(ctypes.byref(self._h), ctypes.byref(p))
         if rc != FSI_OK:
             raise FSIError(rc, lib.fsi_last_error(None).decode())
+        self.n_params = mlp_params(p.dim)
 
     def _check_global(self, rc):
         if rc != FSI_OK:
@@ -635,15 +649,15 @@ class Trainer:
 
     def set_master(self, params):
         w = np.ascontiguousarray(params, np.float32)
-        if w.shape != (FSI_MLP_PARAMS,):
-            raise ValueError("params must hold FSI_MLP_PARAMS floats")
+        if w.shape != (self.n_params,):
+            raise ValueError(f"params must hold {self.n_params} floats")
         self._check_global(self._lib.fsi_trainer_set_master(self._h, _np_ptr(w, ctypes.c_float)))
 
     def get(self):
         """(master float32, bfloat16 words, accumulated gradient float32)."""
-        m = np.empty(FSI_MLP_PARAMS, np.float32)
-        b = np.empty(FSI_MLP_PARAMS, np.uint16)
-        g = np.empty(FSI_MLP_PARAMS, np.float32)
+        m = np.empty(self.n_params, np.float32)
+        b = np.empty(self.n_params, np.uint16)
+        g = np.empty(self.n_params, np.float32)
         self._check_global(self._lib.fsi_trainer_get(self._h, _np_ptr(m, ctypes.c_float),
                                                      _np_ptr(b, ctypes.c_uint16), _np_ptr(g, ctypes.c_float)))
         return m, b, g

@@ -158,6 +158,21 @@ def test_learned_defaults_and_validation(lib):
     assert rc == -1 and not h.value and "scales" in lib.fsi_last_error(None).decode()
     rc = lib.fsi_trainer_create(ctypes.byref(h), ctypes.byref(P.default_train_params(beta1=1.0)))
     assert rc == -1 and "AdamW" in lib.fsi_last_error(None).decode()
+    assert tp.dim == 2
+    rc = lib.fsi_trainer_create(ctypes.byref(h), ctypes.byref(P.default_train_params(dim=4)))
+    assert rc == -1 and not h.value and "dim" in lib.fsi_last_error(None).decode()
+
+
+def test_mlp_sizes_agree_with_the_oracle_layout():
+    """The header's parameter and input counts (2D and 3D) against the oracle's layout."""
+    import paper_1801_05648_gb300 as P
+    from oracle import learned as L
+    hdr = open(os.path.join(ROOT, "include", "fsi.h")).read()
+    defs = dict(re.findall(r"#define (FSI_MLP_\w+) (\d+)", hdr))
+    assert int(defs["FSI_MLP_PARAMS"]) == P.FSI_MLP_PARAMS == L.N_PARAMS == P.mlp_params(2)
+    assert int(defs["FSI_MLP_PARAMS_3D"]) == P.FSI_MLP_PARAMS_3D == L.N_PARAMS_3D == P.mlp_params(3)
+    assert int(defs["FSI_MLP_INPUTS"]) == L.layout(2)[0] == P.mlp_inputs(2)
+    assert int(defs["FSI_MLP_INPUTS_3D"]) == L.layout(3)[0] == P.mlp_inputs(3)
 
 
 def test_learned_null_calls(lib):
