@@ -614,6 +614,8 @@ def bench_ours(args):
             msl, _, stl, _ = V.timed("fp32", steps2, 3)
             xl = V.xs[0].cpu().numpy()
             entry["learned"] = form_summary(msl, stl, {"accepted_total": sum(x.learned_accepted for x in stl)})
+        if V.dim == 3 and not args.no_learned and V.systems[0].cfg.pressure == "q1":
+            entry["mlp_3d"] = mlp3d_timing(V, bs, fma32)
         secondary[name] = entry
         if name == "2d_mid" and rank == 0 and not args.no_oracle_error:
             err_oracle = {"workload": "2d_mid", "state": 0, "x64": x64, "x32": x32, "xl": xl,
@@ -751,6 +753,48 @@ def bench_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def bf16_words(w):
+    """float32 -> bfloat16 bit patterns, round to nearest even."""
+    import numpy as np
+    u = np.ascontiguousarray(w, np.float32).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def mlp3d_timing(V, bs, fma32, reps: int = 20):
+    """The learned stage's MLP on a 3D mesh (3x3x3 patch, 201-64-64-7, CUDA cores):
+    seeded random weights (no 3D weights are trained), CUDA events over reps
+    applications to the rhs of the first resident Jacobian."""
+    import numpy as np
+    import torch
+    import fsigen
+    import paper_1801_05648_gb300 as P
+    g = V.solvers[0]
+    nd, pt = fsigen.get_problem(V.systems[0].cfg).node_map()
+    g.learned_setup(nd, pt)
+    w = np.random.default_rng(2024).standard_normal(P.mlp_params(3)) * 0.1
+    g.learned_set_weights(np.ones(5, np.float32), np.full(5, 1e-3, np.float32), bf16_words(w))
+    b = V.rhs[0]
+    c = torch.empty_like(b)
+    for _ in range(3):
+        g.learned_apply(b, c, sync=False)
+    bs.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bs)
+    for _ in range(reps):
+        g.learned_apply(b, c, sync=False)
+    e1.record(bs)
+    bs.synchronize()
+    g.check_device_errors()
+    t = e0.elapsed_time(e1) / reps / 1e3
+    flops = nd.shape[0] * 2.0 * (201 * 64 + 64 * 64 + 64 * 7)
+    peak = 2.0 * fma32 / 1e12
+    return {"kernel": "k_mlp<3, MODE_APPLY>: 3x3x3 patch gather + 201-64-64-7 MLP (FP32 FMA) + scatter",
+            "nodes": int(nd.shape[0]), "launch_us": t * 1e6, "flops_per_launch": flops, "bound": "alu",
+            "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "peak_kind": "measured FP32 FMA rate x 2 (fsi_probe_fma_rate)", "frac": flops / t / 1e12 / peak,
+            "weights": "seeded random (numpy seed 2024, N(0, 0.1^2)); no trained 3D weights"}
+
+
 def newton_timing(name: str):
     """Wall seconds of one quasi-Newton time step (linear solves FP32-AMG to 1e-3,
     stop at 1e-6 of the initial residual) with host and with device assembly."""
@@ -849,6 +893,7 @@ def kernel_only(args):
     'mlp': 6 learned-stage applications.  'solve': set-up and one warm-up solve
     unprofiled, then one solve of the bench form between cudaProfilerStart and
     cudaProfilerStop."""
+    import numpy as np
     import torch
     import fsigen
     from paper_1801_05648_gb300 import build as libbuild
@@ -886,7 +931,11 @@ def kernel_only(args):
         nd, pt = pb.node_map()
         g = P.FSISolver.from_system(s)
         g.learned_setup(nd, pt)
-        g.learned_load(LEARNED_WEIGHTS)
+        if s.dim == 2:
+            g.learned_load(LEARNED_WEIGHTS)
+        else:
+            w = np.random.default_rng(2024).standard_normal(P.mlp_params(3)) * 0.1
+            g.learned_set_weights(np.ones(5, np.float32), np.full(5, 1e-3, np.float32), bf16_words(w))
         b = torch.tensor(s.rhs, device="cuda")
         c = torch.empty_like(b)
         for _ in range(6):

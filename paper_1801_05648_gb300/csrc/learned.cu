@@ -78,19 +78,52 @@ __device__ __forceinline__ int parity_of(int fl) {
 // and pre-activations column-major (row k of node a at [k * ld + a]).
 //
 // Dynamic shared memory: the weights as FP32 (params_padded<D>() floats), then
-// one column per thread (act[k * kNodeThreads + t], max(kPatch, kHidden) rows)
-// holding first the gathered patch, then the hidden activations.  The layers
-// loop over their inputs (read from the thread's column) with the 64
+// one column per thread (act[k * kNodeThreads + t]) holding the hidden
+// activations and, in MODE_FEATURES / MODE_TRAIN, first the gathered patch.  The
+// layers loop over their inputs (read from the thread's column) with the 64
 // accumulators in registers, so the kernel body stays small enough for the
-// instruction cache.  2D: 7.9 K + 8 K floats (64 KB, three CTAs per SM); 3D:
-// 17.5 K + 24.2 K floats (163 KB, one CTA per SM).
-template <int D>
-constexpr int act_rows() { return Net<D>::kPatch > Net<D>::kHidden ? Net<D>::kPatch : Net<D>::kHidden; }
-template <int D>
+// instruction cache.  MODE_APPLY folds the patch into layer 1 as it gathers it
+// (W1^T (x / rho) = (sum_i x_i W1[i]) / rho), so its column is 64 rows: 2D 64 KB
+// (three CTAs per SM), 3D 102 KB (two).  3D training: 163 KB (one).
+template <int D, int MODE>
+constexpr int act_rows() {
+  return MODE != MODE_APPLY && Net<D>::kPatch > Net<D>::kHidden ? Net<D>::kPatch : Net<D>::kHidden;
+}
+template <int D, int MODE>
 constexpr size_t mlp_smem() {
-  return sizeof(float) * ((size_t)params_padded<D>() + (size_t)act_rows<D>() * kNodeThreads);
+  return sizeof(float) * ((size_t)params_padded<D>() + (size_t)act_rows<D, MODE>() * kNodeThreads);
 }
 
+// The node record of patch entry q (q = -1: outside the mesh, no DOFs).
+__device__ __forceinline__ int4 node_rec(const MlpGeom& g, int q) {
+  return q >= 0 ? g.node_dof[q] : make_int4(-1, -1, -1, 0);
+}
+
+// Issue the loads of one patch node's r' values (raw FP64) and class scales.
+template <int D>
+__device__ __forceinline__ void load_node_vals(const MlpGeom& g, const double* __restrict__ rp, int4 r,
+                                               double (&ev)[2 * D + 1], float (&sc)[3]) {
+#pragma unroll
+  for (int k = 0; k < 2 * D + 1; ++k) ev[k] = 0.0;
+  sc[0] = sc[1] = sc[2] = 0.f;
+  if (r.x >= 0) {
+    sc[0] = pick5(g.inv_in, cls_of(g, r.x));
+    sc[1] = pick5(g.inv_in, cls_of(g, r.y));
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      ev[k] = rp[r.x + k];
+      ev[D + k] = rp[r.y + k];
+    }
+    if (r.z >= 0) {
+      sc[2] = pick5(g.inv_in, cls_of(g, r.z));
+      ev[2 * D] = rp[r.z];
+    }
+  }
+}
+
+// (MODE_FEATURES ends each node after the features: the layers below are then
+// unreachable, which the front end would report once per instantiation)
+#pragma nv_diag_suppress 128
 template <int D, int MODE>
 __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t* __restrict__ w16,
                                                       const double* __restrict__ rp, double* __restrict__ c,
@@ -113,61 +146,125 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t*
     if (a >= g.n_nodes) continue;
     const int4 me = g.node_dof[a];
     const int fl = me.w;
-    // gather x (unnormalised) into the thread's column and sum its squares
-    float ss = 0.f;
-#pragma unroll(D == 2 ? 9 : 3)
-    for (int s = 0; s < N::kSlots; ++s) {
-      const int q = g.patch[a * N::kSlots + s];
-      float e[kC];
+    const int par = parity_of<D>(fl);
+    float h[kH];
+    float rho, inv_rho;
+    if constexpr (MODE == MODE_APPLY) {
+      // gather and layer 1 in one pass, software-pipelined: while slot s's kC x 64
+      // FMAs run, the r' values of slot s+1, the node record of slot s+2 and the
+      // patch entry of slot s+3 are in flight
+      const int* pa = g.patch + a * N::kSlots;
 #pragma unroll
-      for (int k = 0; k < kC; ++k) e[k] = 0.f;
-      if (q >= 0) {
-        const int4 r = g.node_dof[q];
-        const float iv = pick5(g.inv_in, cls_of(g, r.x));
-        const float iu = pick5(g.inv_in, cls_of(g, r.y));
+      for (int j = 0; j < kH; ++j) h[j] = 0.f;
+      float ss = 0.f;
+      double ev[kC];
+      float sc[3];
+      load_node_vals<D>(g, rp, node_rec(g, pa[0]), ev, sc);
+      int4 r1 = node_rec(g, pa[1]);
+      int q2 = pa[2];
+#pragma unroll 1
+      for (int s = 0; s < N::kSlots; ++s) {
+        double evn[kC];
+        float scn[3];
+        load_node_vals<D>(g, rp, r1, evn, scn);                 // slot s+1 (r1.x = -1 past the end)
+        const int4 r2 = node_rec(g, q2);                         // slot s+2
+        const int q3 = s + 3 < N::kSlots ? pa[s + 3] : -1;       // slot s+3
+        float e[kC];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          e[k] = (float)rp[r.x + k] * iv;
-          e[D + k] = (float)rp[r.y + k] * iu;
+          e[k] = (float)ev[k] * sc[0];
+          e[D + k] = (float)ev[D + k] * sc[1];
         }
-        if (r.z >= 0) e[2 * D] = (float)rp[r.z] * pick5(g.inv_in, cls_of(g, r.z));
+        e[2 * D] = (float)ev[2 * D] * sc[2];
+        float sl = e[0] * e[0];
+#pragma unroll
+        for (int k = 1; k < kC; ++k) sl += e[k] * e[k];
+        ss += sl;
+        const float4* w4 = reinterpret_cast<const float4*>(W + N::kW1 + kC * s * kH);
+#pragma unroll
+        for (int k = 0; k < kC; ++k) {
+          const float xi = e[k];
+#pragma unroll
+          for (int q = 0; q < kH / 4; ++q) {
+            const float4 w = w4[k * (kH / 4) + q];
+            h[4 * q + 0] += xi * w.x; h[4 * q + 1] += xi * w.y; h[4 * q + 2] += xi * w.z; h[4 * q + 3] += xi * w.w;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kC; ++k) ev[k] = evn[k];
+        sc[0] = scn[0]; sc[1] = scn[1]; sc[2] = scn[2];
+        r1 = r2;
+        q2 = q3;
       }
-      float sl = e[0] * e[0];
+      rho = sqrtf(ss * (1.0f / N::kPatch));
+      inv_rho = rho > 0.f ? 1.0f / rho : 0.f;
+      // h = (sum_i x_i W1[i]) / rho + b1 + the one-hot row + the flag rows
+      const float* wp = W + N::kW1 + (N::kPatch + par) * kH;
 #pragma unroll
-      for (int k = 1; k < kC; ++k) sl += e[k] * e[k];
-      ss += sl;
+      for (int j = 0; j < kH; ++j) h[j] = h[j] * inv_rho + (W[N::kB1 + j] + wp[j]);
+    } else {
+      // gather x (unnormalised) into the thread's column and sum its squares
+      float ss = 0.f;
+#pragma unroll(D == 2 ? 9 : 3)
+      for (int s = 0; s < N::kSlots; ++s) {
+        const int q = g.patch[a * N::kSlots + s];
+        float e[kC];
 #pragma unroll
-      for (int k = 0; k < kC; ++k) act[(kC * s + k) * kNodeThreads + t] = e[k];
-    }
-    const float rho = sqrtf(ss * (1.0f / N::kPatch));
-    const bool live = rho > 0.f;
-    const float inv_rho = live ? 1.0f / rho : 0.f;
-    const int par = parity_of<D>(fl);
-    if (MODE == MODE_FEATURES) {
-      float* row = F + a * N::kIn;
-      for (int k = 0; k < N::kPatch; ++k) row[k] = act[k * kNodeThreads + t] * inv_rho;
+        for (int k = 0; k < kC; ++k) e[k] = 0.f;
+        if (q >= 0) {
+          const int4 r = g.node_dof[q];
+          const float iv = pick5(g.inv_in, cls_of(g, r.x));
+          const float iu = pick5(g.inv_in, cls_of(g, r.y));
 #pragma unroll
-      for (int k = 0; k < N::kPar; ++k) row[N::kPatch + k] = (k == par) ? 1.f : 0.f;
+          for (int k = 0; k < D; ++k) {
+            e[k] = (float)rp[r.x + k] * iv;
+            e[D + k] = (float)rp[r.y + k] * iu;
+          }
+          if (r.z >= 0) e[2 * D] = (float)rp[r.z] * pick5(g.inv_in, cls_of(g, r.z));
+        }
+        float sl = e[0] * e[0];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) row[N::kPatch + N::kPar + k] = ((fl >> k) & 1) ? 1.f : 0.f;
-      rho_out[a] = rho;
-      continue;
-    }
-    if (MODE == MODE_TRAIN) {
+        for (int k = 1; k < kC; ++k) sl += e[k] * e[k];
+        ss += sl;
+#pragma unroll
+        for (int k = 0; k < kC; ++k) act[(kC * s + k) * kNodeThreads + t] = e[k];
+      }
+      rho = sqrtf(ss * (1.0f / N::kPatch));
+      inv_rho = rho > 0.f ? 1.0f / rho : 0.f;
+      if constexpr (MODE == MODE_FEATURES) {
+        float* row = F + a * N::kIn;
+        for (int k = 0; k < N::kPatch; ++k) row[k] = act[k * kNodeThreads + t] * inv_rho;
+#pragma unroll
+        for (int k = 0; k < N::kPar; ++k) row[N::kPatch + k] = (k == par) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) row[N::kPatch + N::kPar + k] = ((fl >> k) & 1) ? 1.f : 0.f;
+        rho_out[a] = rho;
+        continue;
+      }
       for (int k = 0; k < N::kPatch; ++k) F[k * ld + a] = act[k * kNodeThreads + t] * inv_rho;
 #pragma unroll
       for (int k = 0; k < N::kPar; ++k) F[(N::kPatch + k) * ld + a] = (k == par) ? 1.f : 0.f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) F[(N::kPatch + N::kPar + k) * ld + a] = ((fl >> k) & 1) ? 1.f : 0.f;
       rho_out[a] = rho;
-    }
-    // layer 1: h = W1^T f + b1 (the one-hot and flag inputs add their weight rows)
-    float h[kH];
-    {
-      const float* wp = W + N::kW1 + (N::kPatch + par) * kH;
+      // layer 1: h = W1^T f + b1 (the one-hot and flag inputs add their weight rows below)
+      {
+        const float* wp = W + N::kW1 + (N::kPatch + par) * kH;
 #pragma unroll
-      for (int j = 0; j < kH; ++j) h[j] = W[N::kB1 + j] + wp[j];
+        for (int j = 0; j < kH; ++j) h[j] = W[N::kB1 + j] + wp[j];
+      }
+#pragma unroll 1
+      for (int i = 0; i < N::kPatch; ++i) {
+        const float xi = act[i * kNodeThreads + t] * inv_rho;
+        const float4* w4 = reinterpret_cast<const float4*>(W + N::kW1 + i * kH);
+#pragma unroll
+        for (int q = 0; q < kH / 4; ++q) {
+          const float4 w = w4[q];
+          h[4 * q + 0] += xi * w.x; h[4 * q + 1] += xi * w.y; h[4 * q + 2] += xi * w.z; h[4 * q + 3] += xi * w.w;
+        }
+      }
     }
+    const bool live = rho > 0.f;
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
       if ((fl >> k) & 1) {   // flag inputs: NF_SOLID, NF_VFIX, NF_UFIX, NF_IFACE are bits 0..3
@@ -177,16 +274,6 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t*
           const float4 w = w4[q];
           h[4 * q + 0] += w.x; h[4 * q + 1] += w.y; h[4 * q + 2] += w.z; h[4 * q + 3] += w.w;
         }
-      }
-    }
-#pragma unroll 1
-    for (int i = 0; i < N::kPatch; ++i) {
-      const float xi = act[i * kNodeThreads + t] * inv_rho;
-      const float4* w4 = reinterpret_cast<const float4*>(W + N::kW1 + i * kH);
-#pragma unroll
-      for (int q = 0; q < kH / 4; ++q) {
-        const float4 w = w4[q];
-        h[4 * q + 0] += xi * w.x; h[4 * q + 1] += xi * w.y; h[4 * q + 2] += xi * w.z; h[4 * q + 3] += xi * w.w;
       }
     }
 #pragma unroll
@@ -241,10 +328,12 @@ __global__ void __launch_bounds__(kNodeThreads) k_mlp(MlpGeom g, const uint16_t*
   }
 }
 
+#pragma nv_diag_default 128
+
 template <int D, int MODE>
 void launch_mlp(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, float* F, float* rho,
                 float* H1, float* H2, int64_t ld, cudaStream_t s) {
-  constexpr size_t smem = mlp_smem<D>();
+  constexpr size_t smem = mlp_smem<D, MODE>();
   static bool attr = false;   // the opt-in above 48 KB, set once per instantiation
   if (!attr) {
     FSI_CUDA(cudaFuncSetAttribute(k_mlp<D, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
