@@ -76,6 +76,8 @@ def parse_args(argv=None):
                     help="FP32 SpMV lanes per block row / 2^shift (fsi_params.spmv_lane_shift; default: the library's)")
     ap.add_argument("--coarse-max", type=int, default=None,
                     help="AMG: coarsen until <= this many scalar rows (fsi_params.coarse_max; default: the library's)")
+    ap.add_argument("--spmv-order", type=int, default=None, choices=[0, 1],
+                    help="length-ordered rows in the outer operator (fsi_params.spmv_order; default: the library's)")
     ap.add_argument("--spmv-stage", type=int, default=None, choices=[0, 1],
                     help="staged 2 x 2 FP32 Chebyshev steps (fsi_params.spmv_stage; default: the library's)")
     ap.add_argument("--kernel-only", choices=["spmv", "solve", "mlp", "cheb"], default=None,
@@ -428,6 +430,7 @@ def bench_ours(args):
     flags = (0 if args.no_graphs else P.FSI_USE_GRAPHS) | (P.FSI_NO_PDL if args.no_pdl else 0)
     knobs = {k: v for k, v in (("spmv_prefetch", args.spmv_prefetch), ("spmv_unroll", args.spmv_unroll),
                                ("spmv_lane_shift", args.spmv_lane_shift), ("spmv_stage", args.spmv_stage),
+                               ("spmv_order", args.spmv_order),
                                ("coarse_max", args.coarse_max))
              if v is not None}
     n_states = args.states or DEFAULT_STATES.get(args.workload, 1)
@@ -706,6 +709,7 @@ def bench_ours(args):
                    "spmv_unroll": int(P.default_params(W.dim, **knobs).spmv_unroll),
                    "spmv_lane_shift": int(P.default_params(W.dim, **knobs).spmv_lane_shift),
                    "spmv_stage": int(P.default_params(W.dim, **knobs).spmv_stage),
+                   "spmv_order": int(P.default_params(W.dim, **knobs).spmv_order),
                    "coarse_max": int(P.default_params(W.dim, **knobs).coarse_max),
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": f"inputs larger than L2: each solve streams {bytes_per_iter / 1e9:.2f} GB of matrices and "

@@ -140,6 +140,11 @@ typedef struct fsi_params {
      one chunk ahead: 1 on, 0 off (0).  Bit-identical to the default kernel, and measured
      slower on the GB300 (116 vs 104 us per 1024x512 level-0 step) */
   int spmv_stage;
+  /* the outer operator's two-matrix SpMVs (A_VV next to A_VP, A_PV next to A_PP) take
+     each CTA's block rows sorted by length within 32-row windows, so that the rows of a
+     warp have equal length and no FP64 lane idles while a longer row of its warp
+     finishes: 1 on, 0 off (1).  Changes which thread sums a row, not how: bit-identical */
+  int spmv_order;
 } fsi_params;
 
 enum { FSI_PRECOND_LDU = 0, FSI_PRECOND_LOWER = 1, FSI_PRECOND_UPPER = 2, FSI_PRECOND_DIAG = 3 };

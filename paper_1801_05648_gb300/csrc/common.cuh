@@ -157,6 +157,10 @@ struct Bsr {
   DBuf<float> v32;      // optional FP32 copy
   DBuf<int16_t> cd16;   // optional, square matrices: block column minus block row as int16 (read by the
                         // FP32 Chebyshev steps when every offset fits; 2 bytes per block instead of 4)
+  DBuf<int4> ord2;      // optional: the slot table of the two-matrix SpMV with the partner whose row
+  const int* ord2_rp2 = nullptr;   // pointers these are: block rows sorted by (length here, length
+                        // there) within 32-row windows, {row | length << 24, first block, first
+                        // partner block, partner length} per slot (k_pair_order)
   int stage_rows = 0;   // 2 x 2 FP32 with cd16: block rows per CTA the staged Chebyshev kernel was sized for
   int stage_max = 0;    // ... and the largest CTA slice in blocks, from the 8-entry boundary below it
   int tpr = 32;         // threads per block row of the FP32 SpMV, from the mean row length
@@ -201,6 +205,7 @@ struct SpmvTuning {
   int lane_shift = 0;  // FP32 launches: lanes per block row divided by 2^lane_shift (at least 1)
   int keep_x64 = 1;    // FP64 launches gather x with the L2 evict-last policy (see OuterOperatorScope)
   int stage = 0;       // 2 x 2 FP32 Chebyshev steps with the column offsets staged in shared memory
+  int order = 1;       // two-matrix launches take their rows in the order of Bsr::ord2 when it is built
   int setup_depth = 0; // > 0 while matrices are being built: no reads before the dependency wait
 };
 inline SpmvTuning& spmv_tuning() {

@@ -37,6 +37,7 @@ struct KnobScope {
     fsi::spmv_tuning().prefetch = p.spmv_prefetch;
     fsi::spmv_tuning().lane_shift = p.spmv_lane_shift;
     fsi::spmv_tuning().stage = p.spmv_stage;
+    fsi::spmv_tuning().order = p.spmv_order;
     fsi::pdl_enabled() = (p.flags & FSI_NO_PDL) == 0;
     fsi::mlp_tensor_cores() = (p.flags & FSI_MLP_CUDA_CORES) == 0;
     fsi::coarse_max_bytes() = p.cluster_max_bytes;
@@ -108,6 +109,7 @@ void to_solver_params(const fsi_params& p, fsi::SolverParams& s) {
   s.precond_variant = p.precond_variant;
   s.spmv_lane_shift = p.spmv_lane_shift;
   s.spmv_stage = p.spmv_stage;
+  s.spmv_order = p.spmv_order;
 }
 
 void validate_params(const fsi::SolverParams& s) {
@@ -135,6 +137,7 @@ void validate_params(const fsi::SolverParams& s) {
           "precond_variant must be FSI_PRECOND_LDU, _LOWER, _UPPER or _DIAG");
   require(s.spmv_lane_shift >= 0 && s.spmv_lane_shift <= 4, "spmv_lane_shift must be in [0, 4]");
   require(s.spmv_stage == 0 || s.spmv_stage == 1, "spmv_stage must be 0 or 1");
+  require(s.spmv_order == 0 || s.spmv_order == 1, "spmv_order must be 0 or 1");
 }
 
 void validate_csr(int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
@@ -203,6 +206,7 @@ void fsi_default_params(fsi_params* p, int dim) {
   p->precond_variant = FSI_PRECOND_LDU;
   p->spmv_lane_shift = 0;
   p->spmv_stage = 0;
+  p->spmv_order = 1;
 }
 
 int fsi_setup(fsi_ctx** out, int dim, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,

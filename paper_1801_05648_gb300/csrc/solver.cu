@@ -428,6 +428,8 @@ static void extract_blocks(Context& C, const CsrView& A) {
   extract_bsr(A, 0, nV, d, o[4], nP, 1, C.AVP, s);
   extract_bsr(A, o[4], nP, 1, 0, nV, d, C.APV, s);
   extract_bsr(A, o[4], nP, 1, o[4], nP, 1, C.APP, s);
+  bsr_make_pair_order(C.AVV, C.AVP, s);
+  bsr_make_pair_order(C.APV, C.APP, s);
   // preconditioner blocks
   extract_bsr(A, o[0], nm, d, o[0], nm, d, C.Mblk, s);
   extract_bsr(A, o[0], nm, d, o[1], ns, d, C.C_ms, s);

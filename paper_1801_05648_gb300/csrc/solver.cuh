@@ -28,6 +28,7 @@ struct SolverParams {
   int precond_variant = 0;       // 0 Alg. 2 (LDU), 1 (D + L)^-1, 2 (D + U)^-1, 3 D^-1
   int spmv_lane_shift = 0;       // FP32 SpMV lanes per block row divided by 2^shift
   int spmv_stage = 0;            // staged 2 x 2 FP32 Chebyshev steps (opt-in)
+  int spmv_order = 1;            // outer-operator rows in the length order of Bsr::ord2
   int inject = 0;                // fault injection for the bounded-wait tests (fsi_debug_inject)
 };
 

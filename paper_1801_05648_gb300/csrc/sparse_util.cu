@@ -344,6 +344,30 @@ __global__ void k_delta16(int nbr, const int* __restrict__ rp, const int* __rest
     d[k] = (int16_t)off;
   }
 }
+// Slot table of a two-matrix SpMV (block rows of A1 next to those of A2): within
+// each window of 32 block rows, the rows by decreasing A1 length, then decreasing A2
+// length, ties in row order; record {row | len1 << 24, first A1 block, first A2 block,
+// len2}.  One warp per window ranks its rows by counting.  *bad = 1 if an A1 row is
+// longer than 255 blocks (the record cannot hold it).
+__global__ void k_pair_order(int nbr, const int* __restrict__ rp1, const int* __restrict__ rp2,
+                             int4* __restrict__ ord, int* __restrict__ bad) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int kb1 = 0, kb2 = 0, l1 = -1, l2 = -1;     // lanes past the end rank last and write nothing
+  if (row < nbr) {
+    kb1 = rp1[row];
+    l1 = rp1[row + 1] - kb1;
+    kb2 = rp2[row];
+    l2 = rp2[row + 1] - kb2;
+    if (l1 > 255) atomicExch(bad, 1);
+  }
+  int rank = 0;
+  for (int j = 0; j < 32; ++j) {
+    const int a = __shfl_sync(0xffffffffu, l1, j), b = __shfl_sync(0xffffffffu, l2, j);
+    rank += (a > l1 || (a == l1 && (b > l2 || (b == l2 && j < lane)))) ? 1 : 0;
+  }
+  if (row < nbr && l1 <= 255) ord[row - lane + rank] = make_int4((int)row | (l1 << 24), kb1, kb2, l2);
+}
 __global__ void k_point_diag(int nbr, int b, const int* __restrict__ rp, const int* __restrict__ ci,
                              const double* __restrict__ va, double* __restrict__ diag) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -687,6 +711,22 @@ __global__ void k_stage_max(int nbr, const int* __restrict__ rp, int R, int* __r
   if (r0 >= nbr) return;
   const int64_t r1 = r0 + R < nbr ? r0 + R : nbr;
   atomicMax(out, rp[r1] - (rp[r0] & ~7));
+}
+
+void bsr_make_pair_order(Bsr& A1, const Bsr& A2, cudaStream_t s) {
+  A1.ord2.release();
+  A1.ord2_rp2 = nullptr;
+  if (A1.nbr == 0 || A2.nbr != A1.nbr || A1.nbr >= (1 << 24)) return;
+  DBuf<int> bad(1);
+  FSI_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+  A1.ord2.alloc(A1.nbr);
+  k_pair_order<<<div_up(A1.nbr, 256), 256, 0, s>>>(A1.nbr, A1.rowptr.p, A2.rowptr.p, A1.ord2.p, bad.p);
+  FSI_CHECK_LAUNCH();
+  int h = 0;
+  FSI_CUDA(cudaMemcpyAsync(&h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA(cudaStreamSynchronize(s));
+  if (h) A1.ord2.release();
+  else A1.ord2_rp2 = A2.rowptr.p;
 }
 
 bool bsr_make_delta16(Bsr& A, cudaStream_t s) {

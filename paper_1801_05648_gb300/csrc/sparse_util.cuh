@@ -65,6 +65,9 @@ void bsr_make_fp32(Bsr& A, cudaStream_t s);
 // 16-bit column offsets (block column - block row) of a square matrix, kept only
 // when every offset fits in int16; returns whether they were kept.
 bool bsr_make_delta16(Bsr& A, cudaStream_t s);
+// Slot table of the two-matrix SpMV of A1 with A2 (same block rows), held by A1
+// (Bsr::ord2); left empty when a row of A1 has more than 255 blocks.
+void bsr_make_pair_order(Bsr& A1, const Bsr& A2, cudaStream_t s);
 
 // Dense row-major copy (n = nbr*br rows, nbc*bc cols) of a BSR matrix.
 void bsr_to_dense(const Bsr& A, double* dense, cudaStream_t s);

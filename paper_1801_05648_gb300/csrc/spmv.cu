@@ -70,6 +70,7 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
   if (A2) { v2 = A2->vals<T>(); rp2 = A2->rowptr.p; ci2 = A2->colind.p; nnzb2 = A2->nnzb; }
   const int pre_wait = tu.setup_depth == 0 ? 1 : 0;
   const int pf = tu.prefetch > 0 ? kPrefetchCap : 0;
+  const int4* ord2 = BC2 > 0 && tu.order && A2 && A1.ord2.p && A1.ord2_rp2 == A2->rowptr.p ? A1.ord2.p : nullptr;
   if constexpr (ALLOW16 && sizeof(T) == 4 && BC2 == 0) {
     if constexpr (BR == 2 && BC1 == 2) {
       // staged for matrices with at least two chunks per CTA of the persistent grid
@@ -85,21 +86,21 @@ void launch_g(const Bsr& A1, const G1& g1, const Bsr* A2, const T* x2, const Epi
     if (A1.cd16.p) {
       if (tu.unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
         launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8, int16_t>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta,
-                 pf, pre_wait, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2,
+                 pf, pre_wait, ord2, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2,
                  x2, epi);
       else
         launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4, int16_t>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta,
-                 pf, pre_wait, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2,
+                 pf, pre_wait, ord2, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2,
                  x2, epi);
       return;
     }
   }
   if (tu.unroll >= 8 && unroll_for<T, BR, BC1, 8>() == 8)
     launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 8>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf, pre_wait,
-             A1.rowptr.p, A1.colind.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2, epi);
+             ord2, A1.rowptr.p, A1.colind.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2, epi);
   else
     launch_k(k_bsr_spmv<T, BR, BC1, BC2, Epi, G1, 4>, blocks, threads, 0, s, A1.nbr, tpr, rows_per_cta, pf, pre_wait,
-             A1.rowptr.p, A1.colind.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2, epi);
+             ord2, A1.rowptr.p, A1.colind.p, A1.vals<T>(), A1.nnzb, g1, rp2, ci2, v2, nnzb2, x2, epi);
 }
 
 template <class T, int BR, int BC1, int BC2, class Epi, bool ALLOW16 = false>

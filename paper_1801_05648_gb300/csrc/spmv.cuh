@@ -369,8 +369,14 @@ __device__ __forceinline__ void prefetch_blocks(const T* v, int64_t nnzb, int a,
 // (about 60 MB for the resident CTAs) was evicted before use and read twice.  Reading the
 // row pointers before the wait is only allowed once the matrices are built
 // (pre_wait != 0); during set-up the previous kernel may still be writing them.
+// Two-matrix launches may take a slot table (ord2, Bsr::ord2): the CTA's slots
+// [r0, r1) are then its block rows sorted by length within 32-row windows (the same
+// rows when r0 is a multiple of 32, i.e. tpr <= 8), so the rows of a warp have equal
+// length and no lane idles while a longer row in its warp finishes.  A slot's record
+// replaces the four row-pointer loads; each row is summed exactly as without it.
 template <class T, int BR, int BC1, int BC2, class Epi, class G1 = GatherX<T, BC1>, int UREQ = 4, class CI1 = int>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per_cta, int prefetch, int pre_wait,
+    const int4* __restrict__ ord2,
     const int* __restrict__ rp1, const CI1* __restrict__ ci1, const T* __restrict__ v1, int64_t nnzb1, G1 g1,
     const int* __restrict__ rp2, const int* __restrict__ ci2, const T* __restrict__ v2, int64_t nnzb2,
     const T* __restrict__ x2,
@@ -396,19 +402,37 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int nbr, int tpr, int rows_per
   const int per_pass = blockDim.x / tpr;
   const int lane = threadIdx.x & (tpr - 1);
   for (int base = r0; base < r1; base += per_pass) {
-    const int row = base + threadIdx.x / tpr;
-    const bool valid = row < r1;
+    const int slot = base + threadIdx.x / tpr;
+    const bool valid = slot < r1;
+    int row = slot, kb1 = 0, ke1 = 0, kb2 = 0, ke2 = 0;
+    if (valid) {
+      if (BC2 > 0 && ord2) {
+        const int4 o = __ldg(ord2 + slot);
+        row = o.x & 0xFFFFFF;
+        kb1 = o.y;
+        ke1 = kb1 + (int)((unsigned)o.x >> 24);
+        kb2 = o.z;
+        ke2 = kb2 + o.w;
+      } else {
+        kb1 = rp1[row];
+        ke1 = rp1[row + 1];
+        if constexpr (BC2 > 0) {
+          kb2 = rp2[row];
+          ke2 = rp2[row + 1];
+        }
+      }
+    }
     T acc[BR];
 #pragma unroll
     for (int i = 0; i < BR; ++i) acc[i] = T(0);
     typename Epi::Pre pre;
     if (valid && lane == 0) pre = epi.load(row);
     if (valid) {
-      row_accumulate<T, BR, BC1, UREQ, G1, CI1>(ci1, sizeof(CI1) == 4 ? 0 : row, v1, nnzb1, g1, rp1[row],
-                                                rp1[row + 1], lane, tpr, acc);
+      row_accumulate<T, BR, BC1, UREQ, G1, CI1>(ci1, sizeof(CI1) == 4 ? 0 : row, v1, nnzb1, g1, kb1, ke1, lane, tpr,
+                                                acc);
       if constexpr (BC2 > 0)
-        row_accumulate<T, BR, BC2, UREQ>(ci2, 0, v2, nnzb2, GatherX<T, BC2, G1::kKeep>{x2}, rp2[row], rp2[row + 1],
-                                         lane, tpr, acc);
+        row_accumulate<T, BR, BC2, UREQ>(ci2, 0, v2, nnzb2, GatherX<T, BC2, G1::kKeep>{x2}, kb2, ke2, lane, tpr,
+                                         acc);
     }
     for (int off = tpr >> 1; off > 0; off >>= 1)
 #pragma unroll

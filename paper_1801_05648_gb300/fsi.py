@@ -70,7 +70,8 @@ class Params(ctypes.Structure):
                 ("learned_accept", ctypes.c_double), ("spmv_prefetch", ctypes.c_int),
                 ("cluster_max_bytes", ctypes.c_double), ("cheb_degree_coarse", ctypes.c_int),
                 ("fluid_gmres_iters", ctypes.c_int), ("precond_variant", ctypes.c_int),
-                ("spmv_lane_shift", ctypes.c_int), ("spmv_stage", ctypes.c_int)]
+                ("spmv_lane_shift", ctypes.c_int), ("spmv_stage", ctypes.c_int),
+                ("spmv_order", ctypes.c_int)]
 
 
 class AsmMesh(ctypes.Structure):

@@ -133,6 +133,9 @@ def test_rejects_bad_params(lib):
         assert rc == -1 and "spmv_lane_shift" in msg
     rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, spmv_stage=2))
     assert rc == -1 and "spmv_stage" in msg
+    assert P.default_params(2).spmv_order == 1
+    rc, _, msg = _setup(lib, 2, 4, rp, ci, va, off, P.default_params(2, spmv_order=2))
+    assert rc == -1 and "spmv_order" in msg
 
 
 def test_null_context_calls(lib):

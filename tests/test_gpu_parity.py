@@ -227,6 +227,38 @@ def test_staged_chebyshev_is_bit_identical(torch_cuda):
     assert torch.equal(out[0][0], out[1][0])
 
 
+@pytest.mark.parametrize("name", ["2d_37x19_ragged", "3d_8x4x4", "2d_512x256"])
+def test_length_ordered_rows_are_bit_identical(name, torch_cuda):
+    """spmv_order only changes which thread sums a block row of the outer operator
+    (rows sorted by length within 32-row windows, ragged last windows included), never
+    the order of a row's sum: the operator, its residual and whole FP64 and FP32-AMG
+    solves with and without it are bit-identical (2D and 3D)."""
+    torch = torch_cuda
+    import paper_1801_05648_gb300 as P
+    cfg = fsigen.CONFIGS["2d_512x256"] if name == "2d_512x256" else CASES[name][0]
+    s = fsigen.make_system(cfg)
+    b = torch.tensor(s.rhs, device="cuda")
+    xr = torch.tensor(np.random.default_rng(7).standard_normal(s.n), device="cuda")
+    for prec in ("fp64", "fp32"):
+        out = []
+        for order in (0, 1):
+            g = P.FSISolver.from_system(s, params=P.default_params(s.dim, flags=P.FSI_USE_GRAPHS, spmv_order=order))
+            g.precond_build(prec)
+            y = torch.empty_like(b)
+            g.apply_operator(xr, y)
+            x = torch.zeros_like(b)
+            st = g.solve(b, x, 1e-8)
+            g.close()
+            assert st.status == 0
+            out.append((x, st.iters, st.history, y))
+        assert out[0][1] == out[1][1] and out[0][2] == out[1][2], prec
+        assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][3], out[1][3]), prec
+        if prec == "fp64":
+            A = s.scipy()
+            want = A @ xr.cpu().numpy()
+            assert np.abs(out[1][3].cpu().numpy() - want).max() <= 1e-12 * np.abs(want).max()
+
+
 @pytest.mark.parametrize("deg", [0, 1, 3])
 def test_coarse_chebyshev_degree_parity(deg, torch_cuda):
     """The coarse-level Chebyshev degree (0: the level-0 degree everywhere) is the
