@@ -328,24 +328,42 @@ void launch(const CoarseRun<T>& run, const T* b0, T* x0, cudaStream_t s) {
   ++g_kernel_launches;
 }
 
-// Cooperative grid: half of the CTAs the whole GPU holds at once (0 when none fit).
+// Cooperative grid: half of the CTAs the whole GPU holds at once (0 when none fit);
+// found once per device.
 template <class T>
 int choose_grid() {
-  static int cached = -1;
-  if (cached >= 0) return cached;
-  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  static std::atomic<int> cached[64];
+  static std::atomic<unsigned long long> done{0};
+  once_per_device(done, [](int dev) {
+    int nsm = 0, per_sm = 0, coop = 0;
+    FSI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FSI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    FSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_vcycle<T, true>, kCoarseThreads, 0));
+    cached[dev].store(coop ? (per_sm * nsm) / 2 : 0, std::memory_order_relaxed);
+  });
+  int dev = 0;
   FSI_CUDA(cudaGetDevice(&dev));
-  FSI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  FSI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  FSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_vcycle<T, true>, kCoarseThreads, 0));
-  cached = coop ? (per_sm * nsm) / 2 : 0;
-  return cached;
+  return cached[dev].load(std::memory_order_relaxed);
 }
 
 template <class T>
+int find_cluster();
+
+// Cluster size of the one-launch coarse V-cycle: 16 (non-portable, which the kernel
+// then allows on this device) or 8 when a cluster of that size fits, else 0; found
+// once per device.
+template <class T>
 int choose_cluster() {
-  static int cached = -1;
-  if (cached >= 0) return cached;
+  static std::atomic<int> cached[64];
+  static std::atomic<unsigned long long> done{0};
+  once_per_device(done, [](int dev) { cached[dev].store(find_cluster<T>(), std::memory_order_relaxed); });
+  int dev = 0;
+  FSI_CUDA(cudaGetDevice(&dev));
+  return cached[dev].load(std::memory_order_relaxed);
+}
+
+template <class T>
+int find_cluster() {
   int best = 0;
   for (int c : {16, 8}) {
     if (c == 16 && cudaFuncSetAttribute(k_coarse_vcycle<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
@@ -370,7 +388,6 @@ int choose_cluster() {
     }
     cudaGetLastError();
   }
-  cached = best;
   return best;
 }
 

@@ -2,6 +2,7 @@
 // device buffers, the block-sparse-row (BSR) matrix type and small helpers.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -117,6 +118,22 @@ struct DeviceGuard {
   DeviceGuard(const DeviceGuard&) = delete;
   DeviceGuard& operator=(const DeviceGuard&) = delete;
 };
+
+// Runs setup(dev) once per device dev, on the current one: a kernel's function attributes
+// and a __device__ variable's address belong to the copy of the module that each
+// device loads, so what was set up on one device does not hold on another.  `done`
+// is the call site's set of devices already set up (bit d for device d).  Two
+// threads may both run it for the same device; it must be idempotent.
+template <class F>
+void once_per_device(std::atomic<unsigned long long>& done, F&& setup) {
+  int dev = 0;
+  FSI_CUDA(cudaGetDevice(&dev));
+  require(dev >= 0 && dev < 64, "device ordinal above 63");
+  const unsigned long long bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return;
+  setup(dev);
+  done.fetch_or(bit, std::memory_order_release);
+}
 
 // Owning device buffer.
 template <class T>

@@ -334,11 +334,10 @@ template <int D, int MODE>
 void launch_mlp(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, float* F, float* rho,
                 float* H1, float* H2, int64_t ld, cudaStream_t s) {
   constexpr size_t smem = mlp_smem<D, MODE>();
-  static bool attr = false;   // the opt-in above 48 KB, set once per instantiation
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};   // the opt-in above 48 KB, per instantiation and device
+  once_per_device(attr, [](int) {
     FSI_CUDA(cudaFuncSetAttribute(k_mlp<D, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  });
   // one wave of the CTAs that fit an SM (228 KB of shared memory, 1 KB reserved
   // per CTA): the weights are loaded once per CTA
   constexpr int per_sm = (int)((228u * 1024u) / (smem + 1024u)) < 1 ? 1 : (int)((228u * 1024u) / (smem + 1024u));

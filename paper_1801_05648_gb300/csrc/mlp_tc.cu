@@ -335,11 +335,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_mlp_tc(MlpGeom g, const uint1
 
 void mlp_apply_tc(const MlpGeom& g, const uint16_t* w16, const double* rp, double* c, int* err, cudaStream_t s) {
   require(g.dim == 2, "the tensor-core MLP takes the 2D layout (3x3 patch, 53 inputs)");
-  static thread_local bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};   // the opt-in above 48 KB, per device
+  once_per_device(attr, [](int) {
     FSI_CUDA(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-    attr = true;
-  }
+  });
   if (g.n_nodes <= 0) return;
   const int64_t tiles = (g.n_nodes + kTcRows - 1) / kTcRows;
   int64_t grid = (int64_t)device_sms() * 2;   // two 103-KB CTAs per SM

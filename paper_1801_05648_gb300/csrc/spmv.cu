@@ -17,10 +17,18 @@ constexpr int kStageSmemMax = 100 * 1024;
 // Set by a staged kernel whose wait for its copies gave up (see spmv_stage_failed).
 __device__ int g_stage_err = 0;
 
+// The flag's device address on the current device (looked up once per device).
 int* stage_err_ptr() {
-  static int* p = nullptr;   // the symbol's address, looked up once
-  if (!p) FSI_CUDA(cudaGetSymbolAddress((void**)&p, g_stage_err));
-  return p;
+  static std::atomic<int*> addr[64];
+  static std::atomic<unsigned long long> done{0};
+  once_per_device(done, [](int dev) {
+    int* a = nullptr;
+    FSI_CUDA(cudaGetSymbolAddress((void**)&a, g_stage_err));
+    addr[dev].store(a, std::memory_order_relaxed);
+  });
+  int dev = 0;
+  FSI_CUDA(cudaGetDevice(&dev));
+  return addr[dev].load(std::memory_order_relaxed);
 }
 
 // Persistent grid of the staged kernel: up to eight 256-thread CTAs per SM (its
@@ -36,12 +44,11 @@ inline int staged_grid(int nchunks, int smax) {
 template <class Epi, class G1, int UREQ>
 void launch_staged(const Bsr& A1, const G1& g1, const Epi& epi, int tpr, int rows_per_cta, int nchunks, int grid,
                    int pre_wait, cudaStream_t s) {
-  static bool attr = false;   // the opt-in above 48 KB, set once per instantiation
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};   // the opt-in above 48 KB, per instantiation and device
+  once_per_device(attr, [](int) {
     FSI_CUDA(cudaFuncSetAttribute(k_bsr_cheb_staged<Epi, G1, UREQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kStageSmemMax));
-    attr = true;
-  }
+  });
   launch_k(k_bsr_cheb_staged<Epi, G1, UREQ>, grid, 256, staged_smem_bytes(A1.stage_max), s, A1.nbr, tpr,
            rows_per_cta, nchunks, pre_wait, A1.rowptr.p, (const int16_t*)A1.cd16.p, A1.vals<float>(), g1, epi,
            A1.stage_max, stage_err_ptr());
